@@ -1,0 +1,10 @@
+"""GB300-native evaluation of HMatrix-matrix products Y = K~ W (MatRox, arXiv 1812.07152).
+
+The compute path is libhmat.so (hand-written sm_103a CUDA behind a C ABI, see
+include/hmat.h); this package only builds it and marshals arguments to it.
+"""
+from .hmat import (  # noqa: F401
+    HmatError, HMAT_OK, HMAT_EINVAL, HMAT_ENOMEM, HMAT_ECUDA, HMAT_ETIMEOUT, HMAT_EUNSUPPORTED,
+    HMAT_EDEVICE, HMAT_MODE_FP64, DeviceHMatrix, hmat_load, hmat_eval, hmat_reserve,
+    hmat_status_poll, hmat_info, hmat_free, hmat_strerror, library, exported_symbols,
+)

@@ -1,0 +1,87 @@
+"""Builds libhmat.so in-tree for sm_103a with nvcc (one -gencode, TUs in parallel)."""
+from __future__ import annotations
+
+import hashlib
+import os
+import shutil
+import subprocess
+import sys
+from typing import List
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+LIBDIR = os.path.join(PKG, "lib")
+BUILDDIR = os.path.join(ROOT, "_build")
+LIB = os.path.join(LIBDIR, "libhmat.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", "-I" + os.path.join(ROOT, "include")]
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libhmat")
+
+
+def _sources() -> List[str]:
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
+
+
+def _digest(files: List[str], flags: List[str]) -> str:
+    h = hashlib.sha256()
+    for f in sorted(files + [os.path.join(CSRC, x) for x in os.listdir(CSRC) if x.endswith(".h")]
+                    + [os.path.join(ROOT, "include", x) for x in os.listdir(os.path.join(ROOT, "include"))]):
+        h.update(f.encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(flags).encode())
+    return h.hexdigest()
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every CUDA/C++ source of the library and link lib/libhmat.so; returns its path."""
+    srcs = _sources()
+    flags = ARCH + CFLAGS
+    stamp = os.path.join(LIBDIR, "libhmat.stamp")
+    digest = _digest(srcs, flags)
+    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+        with open(stamp) as f:
+            if f.read().strip() == digest:
+                return LIB
+    os.makedirs(LIBDIR, exist_ok=True)
+    os.makedirs(BUILDDIR, exist_ok=True)
+    nvcc = _nvcc()
+    procs = []
+    objs = []
+    for s in srcs:
+        o = os.path.join(BUILDDIR, os.path.basename(s) + ".o")
+        objs.append(o)
+        cmd = [nvcc] + flags + (["-x", "cu"] if s.endswith(".cu") else []) + ["-c", s, "-o", o]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append((s, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+    errors = []
+    for s, p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            errors.append(f"{s}:\n{out}")
+        elif verbose and out.strip():
+            print(out, file=sys.stderr)
+    if errors:
+        raise RuntimeError("libhmat build failed:\n" + "\n".join(errors))
+    tmp = LIB + ".tmp"
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("libhmat link failed:\n" + r.stdout)
+    os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(digest)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

@@ -1,0 +1,511 @@
+// libhmat C ABI: validation and level-packed upload of an HMatrix (hmat_load),
+// the evaluation driver (hmat_eval) and the handle's lifetime.
+//
+// The phases follow the evaluation of Section 2.1: the near-field reduction over
+// D, the bottom-up tree loop over the bases, the far-field reduction over B and
+// the top-down tree loop. Every phase is one grouped-GEMM launch over a work list
+// built here once per handle; the gather of W into tree order and the scatter of
+// Y back to the caller's order are folded into the row indexing of the first and
+// last phases (perm maps a tree-order row to the caller's row).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <numeric>
+
+#include "hmat_internal.h"
+
+using namespace hmat;
+
+namespace {
+
+constexpr int64_t kAlignValues = 16;  // every packed block starts on a 128-byte boundary
+constexpr int kTileRows = 64;         // rows per CTA tile of the FP64 kernels
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct Validated {
+  int64_t n_nodes, n_leaves, first_leaf, n_near, n_far;
+};
+
+int level_of(int64_t a) {
+  int l = 0;
+  while (((int64_t)2 << l) - 1 <= a) ++l;
+  return l;
+}
+
+hmat_status validate(const hmat_desc* d, Validated* v) {
+  if (!d || d->levels < 0 || d->levels > 24 || d->n_points < 0) return HMAT_EINVAL;
+  const int64_t n_nodes = ((int64_t)2 << d->levels) - 1;
+  const int64_t n_leaves = (int64_t)1 << d->levels;
+  const int64_t first_leaf = n_leaves - 1;
+  if (!d->node_begin || !d->node_size || !d->rank || !d->near_ptr || !d->far_ptr) return HMAT_EINVAL;
+  if (d->n_points > 0 && !d->perm) return HMAT_EINVAL;
+  if (d->node_begin[0] != 0 || d->node_size[0] != d->n_points) return HMAT_EINVAL;
+  for (int64_t a = 0; a < n_nodes; ++a) {
+    if (d->node_size[a] < 0 || d->rank[a] < 0 || d->rank[a] > (1 << 20)) return HMAT_EINVAL;
+    if (d->node_size[a] > INT32_MAX) return HMAT_EINVAL;
+    if (a < first_leaf) {
+      const int64_t l = 2 * a + 1, r = 2 * a + 2;
+      if (d->node_begin[l] != d->node_begin[a]) return HMAT_EINVAL;
+      if (d->node_size[l] + d->node_size[r] != d->node_size[a]) return HMAT_EINVAL;
+      if (d->node_begin[r] != d->node_begin[a] + d->node_size[l]) return HMAT_EINVAL;
+    }
+  }
+  // perm: a bijection of 0..n_points-1
+  if (d->n_points > 0) {
+    std::vector<uint8_t> seen((size_t)d->n_points, 0);
+    for (int64_t k = 0; k < d->n_points; ++k) {
+      const int64_t p = d->perm[k];
+      if (p < 0 || p >= d->n_points || seen[(size_t)p]) return HMAT_EINVAL;
+      seen[(size_t)p] = 1;
+    }
+  }
+  // near CSR over leaves
+  if (d->near_ptr[0] != 0) return HMAT_EINVAL;
+  for (int64_t i = 0; i < n_leaves; ++i)
+    if (d->near_ptr[i + 1] < d->near_ptr[i]) return HMAT_EINVAL;
+  const int64_t n_near = d->near_ptr[n_leaves];
+  if (n_near > INT32_MAX) return HMAT_EINVAL;
+  if (n_near > 0 && (!d->near_idx || !d->near)) return HMAT_EINVAL;
+  for (int64_t e = 0; e < n_near; ++e) {
+    if (d->near_idx[e] < 0 || d->near_idx[e] >= n_leaves) return HMAT_EINVAL;
+  }
+  for (int64_t i = 0; i < n_leaves; ++i)
+    for (int64_t e = d->near_ptr[i]; e < d->near_ptr[i + 1]; ++e) {
+      const int64_t j = d->near_idx[e];
+      if (d->node_size[first_leaf + i] * d->node_size[first_leaf + j] > 0 && !d->near[e]) return HMAT_EINVAL;
+    }
+  // far CSR over nodes
+  if (d->far_ptr[0] != 0) return HMAT_EINVAL;
+  for (int64_t a = 0; a < n_nodes; ++a)
+    if (d->far_ptr[a + 1] < d->far_ptr[a]) return HMAT_EINVAL;
+  const int64_t n_far = d->far_ptr[n_nodes];
+  if (n_far > INT32_MAX) return HMAT_EINVAL;
+  if (n_far > 0 && (!d->far_idx || !d->coupling)) return HMAT_EINVAL;
+  for (int64_t a = 0; a < n_nodes; ++a)
+    for (int64_t e = d->far_ptr[a]; e < d->far_ptr[a + 1]; ++e) {
+      const int64_t b = d->far_idx[e];
+      if (b < 0 || b >= n_nodes || b == a || level_of(a) != level_of(b)) return HMAT_EINVAL;
+      if ((int64_t)d->rank[a] * d->rank[b] > 0 && !d->coupling[e]) return HMAT_EINVAL;
+    }
+  // bases
+  for (int64_t a = 0; a < n_nodes; ++a) {
+    if (d->rank[a] == 0) continue;
+    if (!d->basis) return HMAT_EINVAL;
+    const int64_t rows = a >= first_leaf ? d->node_size[a] : (int64_t)d->rank[2 * a + 1] + d->rank[2 * a + 2];
+    if (rows > 0 && !d->basis[a]) return HMAT_EINVAL;
+  }
+  v->n_nodes = n_nodes;
+  v->n_leaves = n_leaves;
+  v->first_leaf = first_leaf;
+  v->n_near = n_near;
+  v->n_far = n_far;
+  return HMAT_OK;
+}
+
+// Streams host blocks into a device arena through two pinned staging buffers.
+class Uploader {
+ public:
+  Uploader() = default;
+  ~Uploader() { release(); }
+  cudaError_t init(double* dst, size_t stage_values) {
+    dst_ = dst;
+    cap_ = stage_values;
+    for (int b = 0; b < 2; ++b) {
+      cudaError_t e = cudaMallocHost(&buf_[b], cap_ * sizeof(double));
+      if (e != cudaSuccess) return e;
+      e = cudaEventCreateWithFlags(&ev_[b], cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking);
+  }
+  // Copy `count` values of `src` (row-major rows x cols with row stride cols) to
+  // arena offset `off`; returns false when a value is not finite.
+  bool put(int64_t off, const double* src, int64_t count, cudaError_t* err) {
+    if (count == 0) return true;
+    if (count > (int64_t)cap_) {  // a block larger than the staging buffer: copy in pieces
+      if ((*err = flush()) != cudaSuccess) return true;
+      bool finite = true;
+      for (int64_t s = 0; s < count && *err == cudaSuccess; s += (int64_t)cap_) {
+        const int64_t c = std::min<int64_t>(cap_, count - s);
+        finite &= put(off + s, src + s, c, err);
+        if (*err == cudaSuccess) *err = flush();
+      }
+      return finite;
+    }
+    if (fill_ > 0) {  // extend the staged range across the alignment gap, or flush it
+      const int64_t gap = off - (start_ + (int64_t)fill_);
+      if (gap < 0 || (int64_t)fill_ + gap + count > (int64_t)cap_) {
+        if ((*err = flush()) != cudaSuccess) return true;
+      } else {
+        std::memset(buf_[cur_] + fill_, 0, (size_t)gap * sizeof(double));
+        fill_ += (size_t)gap;
+      }
+    }
+    if (fill_ == 0) start_ = off;
+    double* b = buf_[cur_] + fill_;
+    bool finite = true;
+    for (int64_t i = 0; i < count; ++i) {
+      const double x = src[i];
+      finite &= std::isfinite(x);
+      b[i] = x;
+    }
+    fill_ += (size_t)count;
+    return finite;
+  }
+  cudaError_t flush() {
+    if (fill_ == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(dst_ + start_, buf_[cur_], fill_ * sizeof(double), cudaMemcpyHostToDevice, stream_);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev_[cur_], stream_);
+    if (e != cudaSuccess) return e;
+    cur_ ^= 1;
+    fill_ = 0;
+    return cudaEventSynchronize(ev_[cur_]);  // the other buffer's copy has finished
+  }
+  cudaError_t finish() {
+    cudaError_t e = flush();
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(stream_);
+  }
+  void release() {
+    if (stream_) { cudaStreamSynchronize(stream_); cudaStreamDestroy(stream_); stream_ = nullptr; }
+    for (int b = 0; b < 2; ++b) {
+      if (buf_[b]) { cudaFreeHost(buf_[b]); buf_[b] = nullptr; }
+      if (ev_[b]) { cudaEventDestroy(ev_[b]); ev_[b] = nullptr; }
+    }
+  }
+
+ private:
+  double* dst_ = nullptr;
+  double* buf_[2] = {nullptr, nullptr};
+  cudaEvent_t ev_[2] = {nullptr, nullptr};
+  cudaStream_t stream_ = nullptr;
+  size_t cap_ = 0, fill_ = 0;
+  int64_t start_ = 0;
+  int cur_ = 0;
+};
+
+void free_device(Handle* h) {
+  cudaFree(h->arena);
+  cudaFree(h->perm);
+  cudaFree(h->tasks);
+  cudaFree(h->entries);
+  cudaFree(h->tiles);
+  cudaFree(h->status);
+  cudaFree(h->ws);
+  cudaFree(h->us);
+  h->arena = nullptr; h->perm = nullptr; h->tasks = nullptr; h->entries = nullptr;
+  h->tiles = nullptr; h->status = nullptr; h->ws = nullptr; h->us = nullptr;
+}
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src, int64_t* bytes) {
+  const size_t n = std::max<size_t>(src.size(), 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)dst, n);
+  if (e != cudaSuccess) return e;
+  *bytes += (int64_t)n;
+  if (src.empty()) return cudaSuccess;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+hmat_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return HMAT_OK;
+  if (e == cudaErrorMemoryAllocation) return HMAT_ENOMEM;
+  return HMAT_ECUDA;
+}
+
+}  // namespace
+
+extern "C" hmat_status hmat_load(const hmat_desc* d, int flags, hmat_t* out) {
+  if (!out) return HMAT_EINVAL;
+  *out = nullptr;
+  if (flags != 0) return HMAT_EUNSUPPORTED;
+  Validated v;
+  hmat_status st = validate(d, &v);
+  if (st != HMAT_OK) return st;
+
+  std::unique_ptr<hmat_handle> h(new (std::nothrow) hmat_handle());
+  if (!h) return HMAT_ENOMEM;
+  if (cudaGetDevice(&h->device) != cudaSuccess) return HMAT_ECUDA;
+  h->n_points = d->n_points;
+  h->levels = d->levels;
+  h->n_nodes = v.n_nodes;
+  h->n_leaves = v.n_leaves;
+  h->n_near = v.n_near;
+  h->n_far = v.n_far;
+  h->begin.assign(d->node_begin, d->node_begin + v.n_nodes);
+  h->size.assign(d->node_size, d->node_size + v.n_nodes);
+  h->rank.assign(d->rank, d->rank + v.n_nodes);
+  h->skel_off.resize(v.n_nodes + 1);
+  h->skel_off[0] = 0;
+  for (int64_t a = 0; a < v.n_nodes; ++a) h->skel_off[a + 1] = h->skel_off[a] + h->rank[a];
+  h->sum_rank = h->skel_off[v.n_nodes];
+  const int64_t fl = v.first_leaf;
+  auto rows_of = [&](int64_t a) -> int64_t {
+    return a >= fl ? h->size[a] : (int64_t)h->rank[2 * a + 1] + h->rank[2 * a + 2];
+  };
+
+  // ---- arena layout: near blocks (CSR order), bases (node order), coupling (CSR order)
+  std::vector<int64_t> near_off(v.n_near), basis_off(v.n_nodes, -1), far_off(v.n_far);
+  int64_t off = 0;
+  for (int64_t i = 0; i < v.n_leaves; ++i)
+    for (int64_t e = d->near_ptr[i]; e < d->near_ptr[i + 1]; ++e) {
+      near_off[e] = off;
+      const int64_t cnt = h->size[fl + i] * h->size[fl + d->near_idx[e]];
+      h->near_values += cnt;
+      off = align_up(off + cnt, kAlignValues);
+    }
+  for (int64_t a = 0; a < v.n_nodes; ++a) {
+    if (h->rank[a] == 0) continue;
+    basis_off[a] = off;
+    const int64_t cnt = rows_of(a) * h->rank[a];
+    h->basis_values += cnt;
+    off = align_up(off + cnt, kAlignValues);
+  }
+  for (int64_t a = 0; a < v.n_nodes; ++a)
+    for (int64_t e = d->far_ptr[a]; e < d->far_ptr[a + 1]; ++e) {
+      far_off[e] = off;
+      const int64_t cnt = (int64_t)h->rank[a] * h->rank[d->far_idx[e]];
+      h->coupling_values += cnt;
+      off = align_up(off + cnt, kAlignValues);
+    }
+  h->arena_values = std::max<int64_t>(off, 1);
+
+  // ---- work lists
+  std::vector<GemmTask> tasks;
+  std::vector<GemmEntry> entries;
+  std::vector<GemmTile> tiles;
+  std::vector<int64_t> tile_cost;
+  auto add_phase = [&](PhaseKind kind, int32_t level, MatrixKind x, MatrixKind y,
+                       const std::vector<int32_t>& task_ids) {
+    Phase ph{kind, level, x, y, (int64_t)tiles.size(), 0, 0};
+    std::vector<std::pair<int64_t, GemmTile>> list;
+    for (int32_t t : task_ids) {
+      const GemmTask& tk = tasks[t];
+      int64_t kk = 0;
+      for (int32_t e = tk.e_begin; e < tk.e_end; ++e) kk += entries[e].k;
+      ph.max_m = std::max(ph.max_m, tk.m);
+      for (int32_t m0 = 0; m0 < tk.m; m0 += kTileRows) {
+        const int64_t rows = std::min(kTileRows, tk.m - m0);
+        list.push_back({rows * std::max<int64_t>(kk, 1), GemmTile{t, m0}});
+      }
+    }
+    // longest tiles first, so that the last wave of CTAs is short
+    std::stable_sort(list.begin(), list.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (auto& p : list) tiles.push_back(p.second);
+    ph.n_tiles = (int64_t)tiles.size() - ph.tile_begin;
+    if (ph.n_tiles > 0) h->phases.push_back(ph);
+  };
+  auto new_task = [&](int64_t out_row, int64_t m, int accumulate) -> int32_t {
+    tasks.push_back(GemmTask{out_row, (int32_t)m, (int32_t)entries.size(), (int32_t)entries.size(), accumulate});
+    return (int32_t)tasks.size() - 1;
+  };
+  auto add_entry = [&](int32_t t, int64_t a_off, int64_t x_row, int64_t k, int64_t lda, int trans) {
+    if (k == 0) return;
+    entries.push_back(GemmEntry{a_off, x_row, (int32_t)k, (int32_t)lda, trans, 0});
+    tasks[t].e_end = (int32_t)entries.size();
+  };
+
+  {  // near field: every leaf, so that every row of Y is written
+    std::vector<int32_t> ids;
+    for (int64_t i = 0; i < v.n_leaves; ++i) {
+      const int64_t a = fl + i;
+      if (h->size[a] == 0) continue;
+      const int32_t t = new_task(h->begin[a], h->size[a], 0);
+      for (int64_t e = d->near_ptr[i]; e < d->near_ptr[i + 1]; ++e) {
+        const int64_t b = fl + d->near_idx[e];
+        add_entry(t, near_off[e], h->begin[b], h->size[b], h->size[b], 0);
+      }
+      ids.push_back(t);
+    }
+    add_phase(PH_NEAR, d->levels, MAT_USER, MAT_USER, ids);
+  }
+  {  // upward pass, leaves
+    std::vector<int32_t> ids;
+    for (int64_t a = fl; a < v.n_nodes; ++a) {
+      if (h->rank[a] == 0) continue;
+      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0);
+      add_entry(t, basis_off[a], h->begin[a], h->size[a], h->rank[a], 1);
+      ids.push_back(t);
+    }
+    add_phase(PH_UP_LEAF, d->levels, MAT_USER, MAT_SKEL_W, ids);
+  }
+  for (int32_t level = d->levels - 1; level >= 1; --level) {  // upward pass, inner levels
+    std::vector<int32_t> ids;
+    for (int64_t a = ((int64_t)1 << level) - 1; a < ((int64_t)2 << level) - 1; ++a) {
+      if (h->rank[a] == 0) continue;
+      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0);
+      add_entry(t, basis_off[a], h->skel_off[2 * a + 1], rows_of(a), h->rank[a], 1);
+      ids.push_back(t);
+    }
+    add_phase(PH_UP_TRANS, level, MAT_SKEL_W, MAT_SKEL_W, ids);
+  }
+  {  // far field: every node with a basis (also initialises u for the downward pass)
+    std::vector<int32_t> ids;
+    for (int64_t a = 1; a < v.n_nodes; ++a) {
+      if (h->rank[a] == 0) continue;
+      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0);
+      for (int64_t e = d->far_ptr[a]; e < d->far_ptr[a + 1]; ++e) {
+        const int64_t b = d->far_idx[e];
+        add_entry(t, far_off[e], h->skel_off[b], h->rank[b], h->rank[b], 0);
+      }
+      ids.push_back(t);
+    }
+    add_phase(PH_COUPLING, 0, MAT_SKEL_W, MAT_SKEL_U, ids);
+  }
+  for (int32_t level = 1; level < d->levels; ++level) {  // downward pass, inner levels
+    std::vector<int32_t> ids;
+    for (int64_t a = ((int64_t)1 << level) - 1; a < ((int64_t)2 << level) - 1; ++a) {
+      if (h->rank[a] == 0 || rows_of(a) == 0) continue;
+      const int32_t t = new_task(h->skel_off[2 * a + 1], rows_of(a), 1);
+      add_entry(t, basis_off[a], h->skel_off[a], h->rank[a], h->rank[a], 0);
+      ids.push_back(t);
+    }
+    add_phase(PH_DOWN_TRANS, level, MAT_SKEL_U, MAT_SKEL_U, ids);
+  }
+  {  // downward pass, leaves (adds into Y)
+    std::vector<int32_t> ids;
+    for (int64_t a = fl; a < v.n_nodes; ++a) {
+      if (h->rank[a] == 0 || h->size[a] == 0) continue;
+      const int32_t t = new_task(h->begin[a], h->size[a], 1);
+      add_entry(t, basis_off[a], h->skel_off[a], h->rank[a], h->rank[a], 0);
+      ids.push_back(t);
+    }
+    add_phase(PH_DOWN_LEAF, d->levels, MAT_SKEL_U, MAT_USER, ids);
+  }
+
+  // ---- device allocations and upload
+  auto fail = [&](cudaError_t e) -> hmat_status {
+    free_device(h.get());
+    return cuda_status(e);
+  };
+  cudaError_t e = cudaMalloc((void**)&h->arena, (size_t)h->arena_values * sizeof(double));
+  if (e != cudaSuccess) return fail(e);
+  h->device_bytes += h->arena_values * (int64_t)sizeof(double);
+  {
+    Uploader up;
+    if ((e = up.init(h->arena, (size_t)1 << 23)) != cudaSuccess) return fail(e);
+    bool finite = true;
+    cudaError_t ce = cudaSuccess;
+    for (int64_t i = 0; i < v.n_leaves && ce == cudaSuccess; ++i)
+      for (int64_t ee = d->near_ptr[i]; ee < d->near_ptr[i + 1] && ce == cudaSuccess; ++ee) {
+        const int64_t cnt = h->size[fl + i] * h->size[fl + d->near_idx[ee]];
+        finite &= up.put(near_off[ee], d->near[ee], cnt, &ce);
+      }
+    for (int64_t a = 0; a < v.n_nodes && ce == cudaSuccess; ++a)
+      if (h->rank[a] > 0) finite &= up.put(basis_off[a], d->basis[a], rows_of(a) * h->rank[a], &ce);
+    for (int64_t a = 0; a < v.n_nodes && ce == cudaSuccess; ++a)
+      for (int64_t ee = d->far_ptr[a]; ee < d->far_ptr[a + 1] && ce == cudaSuccess; ++ee) {
+        const int64_t cnt = (int64_t)h->rank[a] * h->rank[d->far_idx[ee]];
+        finite &= up.put(far_off[ee], d->coupling[ee], cnt, &ce);
+      }
+    if (ce == cudaSuccess) ce = up.finish();
+    if (ce != cudaSuccess) return fail(ce);
+    if (!finite) { free_device(h.get()); return HMAT_EINVAL; }
+  }
+  std::vector<int64_t> perm(d->perm, d->perm + d->n_points);
+  if ((e = upload(&h->perm, perm, &h->device_bytes)) != cudaSuccess) return fail(e);
+  if ((e = upload(&h->tasks, tasks, &h->device_bytes)) != cudaSuccess) return fail(e);
+  if ((e = upload(&h->entries, entries, &h->device_bytes)) != cudaSuccess) return fail(e);
+  if ((e = upload(&h->tiles, tiles, &h->device_bytes)) != cudaSuccess) return fail(e);
+  std::vector<int> zero(1, 0);
+  if ((e = upload(&h->status, zero, &h->device_bytes)) != cudaSuccess) return fail(e);
+  *out = h.release();
+  return HMAT_OK;
+}
+
+extern "C" hmat_status hmat_reserve(hmat_t h, int64_t q_max) {
+  if (!h || q_max < 0) return HMAT_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
+  if (dev != h->device) return HMAT_EINVAL;
+  if (q_max <= h->q_cap) return HMAT_OK;
+  const size_t n = (size_t)std::max<int64_t>(h->sum_rank, 1) * (size_t)q_max * sizeof(double);
+  double *ws = nullptr, *us = nullptr;
+  cudaError_t e = cudaMalloc((void**)&ws, n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&us, n);
+  if (e != cudaSuccess) {
+    cudaFree(ws);
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  cudaDeviceSynchronize();  // earlier evaluations may still use the old workspace
+  cudaFree(h->ws);
+  cudaFree(h->us);
+  h->device_bytes += (int64_t)(2 * n) - h->ws_bytes;
+  h->ws_bytes = (int64_t)(2 * n);
+  h->ws = ws;
+  h->us = us;
+  h->q_cap = q_max;
+  return HMAT_OK;
+}
+
+extern "C" hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
+  if (!h || q < 0) return HMAT_EINVAL;
+  if (mode != HMAT_MODE_FP64) return HMAT_EUNSUPPORTED;
+  if (q == 0 || h->n_points == 0) return HMAT_OK;
+  if (!W || !Y || W == Y) return HMAT_EINVAL;
+  const char* w0 = (const char*)W;
+  const char* y0 = (const char*)Y;
+  const int64_t bytes = h->n_points * q * (int64_t)sizeof(double);
+  if (w0 < y0 + bytes && y0 < w0 + bytes) return HMAT_EINVAL;  // W and Y overlap
+  if (q > h->q_cap) {
+    hmat_status st = hmat_reserve(h, q);
+    if (st != HMAT_OK) return st;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
+  if (dev != h->device) return HMAT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (const Phase& ph : h->phases) {
+    const double* X = ph.x == MAT_USER ? W : (ph.x == MAT_SKEL_W ? h->ws : h->us);
+    double* Yd = ph.y == MAT_USER ? Y : (ph.y == MAT_SKEL_W ? h->ws : h->us);
+    const int64_t* xm = ph.x == MAT_USER ? h->perm : nullptr;
+    const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
+    cudaError_t e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return HMAT_OK;
+}
+
+extern "C" hmat_status hmat_status_poll(hmat_t h, void* stream) {
+  if (!h) return HMAT_EINVAL;
+  int word = 0;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&word, h->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && word != 0) e = cudaMemset(h->status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_status(e);
+  return (hmat_status)word;
+}
+
+extern "C" hmat_status hmat_info(hmat_t h, int64_t* out, int n_out) {
+  if (!h || !out || n_out < 0) return HMAT_EINVAL;
+  const int64_t vals[9] = {h->n_points, h->levels, h->n_near, h->n_far, h->near_values,
+                           h->basis_values, h->coupling_values, h->sum_rank, h->device_bytes};
+  for (int i = 0; i < n_out && i < 9; ++i) out[i] = vals[i];
+  return HMAT_OK;
+}
+
+extern "C" hmat_status hmat_free(hmat_t h) {
+  if (!h) return HMAT_OK;
+  cudaDeviceSynchronize();
+  free_device(h);
+  delete h;
+  return HMAT_OK;
+}
+
+extern "C" const char* hmat_strerror(hmat_status s) {
+  switch (s) {
+    case HMAT_OK: return "success";
+    case HMAT_EINVAL: return "invalid argument or HMatrix description";
+    case HMAT_ENOMEM: return "out of memory";
+    case HMAT_ECUDA: return "CUDA runtime error";
+    case HMAT_ETIMEOUT: return "a bounded device-side wait gave up";
+    case HMAT_EUNSUPPORTED: return "unsupported request";
+    case HMAT_EDEVICE: return "a kernel found an inconsistent index or size";
+  }
+  return "unknown status";
+}

@@ -1,0 +1,215 @@
+"""ctypes binding of libhmat.so (include/hmat.h): argument marshalling only.
+
+Every entry point has the name of the C function it calls. Device buffers are
+passed as torch CUDA tensors (or raw device addresses); the stream is a
+torch.cuda.Stream, a raw cudaStream_t or None for torch's current stream.
+Nothing here computes: if the library is missing, importing works but every
+call raises, so no caller can silently fall back to another path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+HMAT_OK = 0
+HMAT_EINVAL = -1
+HMAT_ENOMEM = -2
+HMAT_ECUDA = -3
+HMAT_ETIMEOUT = -4
+HMAT_EUNSUPPORTED = -5
+HMAT_EDEVICE = -6
+
+HMAT_MODE_FP64 = 0
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "lib", "libhmat.so")
+_HEADER = os.path.join(os.path.dirname(_PKG), "include", "hmat.h")
+
+_c_i64p = ctypes.POINTER(ctypes.c_int64)
+_c_i32p = ctypes.POINTER(ctypes.c_int32)
+_c_dpp = ctypes.POINTER(ctypes.c_void_p)
+
+
+class HmatDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_points", ctypes.c_int64),
+        ("levels", ctypes.c_int32),
+        ("node_begin", _c_i64p),
+        ("node_size", _c_i64p),
+        ("rank", _c_i32p),
+        ("near_ptr", _c_i64p),
+        ("near_idx", _c_i32p),
+        ("far_ptr", _c_i64p),
+        ("far_idx", _c_i32p),
+        ("basis", _c_dpp),
+        ("coupling", _c_dpp),
+        ("near", _c_dpp),
+        ("perm", _c_i64p),
+    ]
+
+
+class HmatError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {hmat_strerror(status)} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """The loaded libhmat.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libhmat.so is not built ({_LIB_PATH}); run paper_1812_07152_gb300.build.build()")
+        lib = ctypes.CDLL(_LIB_PATH)
+        lib.hmat_load.argtypes = [ctypes.POINTER(HmatDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+        lib.hmat_eval.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                  ctypes.c_int, ctypes.c_void_p]
+        lib.hmat_reserve.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        lib.hmat_status_poll.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        lib.hmat_info.argtypes = [ctypes.c_void_p, _c_i64p, ctypes.c_int]
+        lib.hmat_free.argtypes = [ctypes.c_void_p]
+        lib.hmat_strerror.argtypes = [ctypes.c_int]
+        lib.hmat_strerror.restype = ctypes.c_char_p
+        for name in ("hmat_load", "hmat_eval", "hmat_reserve", "hmat_status_poll", "hmat_info", "hmat_free"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def exported_symbols() -> List[str]:
+    """Entry points declared in include/hmat.h."""
+    with open(_HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:hmat_status|const char\*)\s+(hmat_\w+)\s*\(", text, re.M)))
+
+
+def _check(status: int, what: str) -> None:
+    if status != HMAT_OK:
+        raise HmatError(status, what)
+
+
+def _ptr(x) -> Optional[int]:
+    """Device address of a torch tensor, or an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def hmat_strerror(status: int) -> str:
+    return library().hmat_strerror(int(status)).decode()
+
+
+def hmat_load(n_points: int, levels: int, node_begin, node_size, rank, near_ptr, near_idx, far_ptr, far_idx,
+              basis: Sequence[Optional[np.ndarray]], coupling: Sequence[Optional[np.ndarray]],
+              near: Sequence[Optional[np.ndarray]], perm, flags: int = 0) -> int:
+    """Validate and upload one HMatrix; returns the handle (an opaque address).
+    Block arrays are FP64 row-major; the host arrays may be freed after the call."""
+    keep = []
+
+    def arr(x, dtype):
+        a = np.ascontiguousarray(np.asarray(x), dtype=dtype)
+        keep.append(a)
+        return a.ctypes.data_as(_c_i64p if dtype == np.int64 else _c_i32p)
+
+    def blocks(lst):
+        ptrs = (ctypes.c_void_p * max(len(lst), 1))()
+        for i, b in enumerate(lst):
+            if b is None or np.asarray(b).size == 0:
+                ptrs[i] = None
+            else:
+                a = np.ascontiguousarray(b, dtype=np.float64)
+                keep.append(a)
+                ptrs[i] = a.ctypes.data
+        keep.append(ptrs)
+        return ctypes.cast(ptrs, _c_dpp)
+
+    d = HmatDesc(int(n_points), int(levels), arr(node_begin, np.int64), arr(node_size, np.int64),
+                 arr(rank, np.int32), arr(near_ptr, np.int64), arr(near_idx, np.int32), arr(far_ptr, np.int64),
+                 arr(far_idx, np.int32), blocks(basis), blocks(coupling), blocks(near), arr(perm, np.int64))
+    h = ctypes.c_void_p()
+    _check(library().hmat_load(ctypes.byref(d), int(flags), ctypes.byref(h)), "hmat_load")
+    return int(h.value)
+
+
+def hmat_eval(handle: int, W, Y, q: int, mode: int = HMAT_MODE_FP64, stream=None) -> None:
+    """Enqueue Y = K~ W on `stream` (W, Y: n_points x q FP64 device buffers)."""
+    _check(library().hmat_eval(handle, _ptr(W), _ptr(Y), int(q), int(mode), _stream(stream)), "hmat_eval")
+
+
+def hmat_reserve(handle: int, q_max: int) -> None:
+    _check(library().hmat_reserve(handle, int(q_max)), "hmat_reserve")
+
+
+def hmat_status_poll(handle: int, stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device status word."""
+    return int(library().hmat_status_poll(handle, _stream(stream)))
+
+
+def hmat_info(handle: int) -> dict:
+    out = (ctypes.c_int64 * 9)()
+    _check(library().hmat_info(handle, out, 9), "hmat_info")
+    keys = ("n_points", "levels", "near_entries", "far_entries", "near_values", "basis_values",
+            "coupling_values", "sum_rank", "device_bytes")
+    return dict(zip(keys, [int(v) for v in out]))
+
+
+def hmat_free(handle: int) -> None:
+    _check(library().hmat_free(handle), "hmat_free")
+
+
+class DeviceHMatrix:
+    """Owns one libhmat handle; ``evaluate`` returns Y = K~ W as a torch tensor."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        self.info = hmat_info(handle)
+
+    @classmethod
+    def load(cls, **desc) -> "DeviceHMatrix":
+        return cls(hmat_load(**desc))
+
+    @property
+    def n_points(self) -> int:
+        return self.info["n_points"]
+
+    def evaluate(self, W, Y=None, mode: int = HMAT_MODE_FP64, stream=None):
+        import torch
+        if Y is None:
+            Y = torch.empty_like(W)
+        hmat_eval(self.handle, W, Y, W.shape[1], mode, stream)
+        return Y
+
+    def reserve(self, q_max: int) -> None:
+        hmat_reserve(self.handle, q_max)
+
+    def poll(self, stream=None) -> int:
+        return hmat_status_poll(self.handle, stream)
+
+    def close(self) -> None:
+        if self.handle:
+            hmat_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
