@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the HMatrix-matrix evaluation Y = K~ W on GB300 (one JSON line on stdout).
+
+Default workload: H2 geometric admissibility, N = 65536 points in d = 8 from a
+10-component Gaussian mixture, Gaussian kernel h = 1, leaf size 128, ID tolerance
+1e-5, rank <= 128, W = 65536 x 256 N(0, 1), FP64 evaluation. The HMatrix is built
+by the library's inspector (hmat_build); a step is one full evaluation (near
+field, upward pass, coupling, downward pass) through hmat_eval.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun every rank evaluates its own copy of the HMatrix on its own GPU
+(independent problems, no collective on the data path): value = columns of all
+ranks / the slowest rank's time ("weak" scaling). --impl reference times the FP64
+CPU oracle on the host cores on a bounded column sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "H-matmul cols/s and % HBM roofline, mixed vs FP64 at 1e-6 err; p50/p99 latency"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", default="h2_gmm8d_n65536")
+    ap.add_argument("--n", type=int, default=None, help="reduced point count (small profiling cases)")
+    ap.add_argument("--q", type=int, default=None, help="override the number of right-hand-side columns")
+    ap.add_argument("--cpu-baseline", choices=["auto", "off"], default="auto")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed helpers
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- clocks during the timed region
+
+CLOCK_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                "clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, device_index: int):
+        self.path = tempfile.mktemp(prefix="hmat_clocks_", suffix=".csv")
+        self.proc = None
+        self.device_index = device_index
+
+    def start(self):
+        try:
+            ident = self._gpu_id()
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={ident}", f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def _gpu_id(self) -> str:
+        import torch
+        try:
+            u = str(torch.cuda.get_device_properties(self.device_index).uuid)
+            return u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            return vis.split(",")[self.device_index] if vis else str(self.device_index)
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[4:8]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def workload(args):
+    from workloads import WORKLOADS, reduced
+    w = WORKLOADS[args.workload]
+    if args.n is not None or args.q is not None:
+        w = reduced(w, args.n or w.n, q=args.q)
+    return w
+
+
+def build_params(w):
+    return dict(kernel=w.kernel, kernel_param=w.kernel_param, admissibility=w.admissibility,
+                leaf_size=w.leaf_size, tol=w.tol, max_rank=w.max_rank, eta=w.eta, sample_seed=w.sample_seed)
+
+
+def run_gpu(args, dist: Dist) -> None:
+    import numpy as np
+    import torch
+
+    from paper_1812_07152_gb300 import build as hbuild
+    hbuild.build()
+    import paper_1812_07152_gb300 as hp
+    from workloads import make_points, normal_rhs
+
+    torch.cuda.set_device(dist.local_rank)
+    dist.init("nccl")
+    w = workload(args)
+    X = make_points(w)
+    t0 = time.perf_counter()
+    dev = hp.DeviceHMatrix.build(X, **build_params(w))
+    t_build = time.perf_counter() - t0
+    info = dev.info
+    q = w.q
+    W_host = torch.from_numpy(normal_rhs(w.n, q, w.rhs_seed)).pin_memory()
+    W = W_host.cuda()
+    Y = torch.empty_like(W)
+    dev.reserve(q)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        hp.hmat_eval(dev.handle, W, Y, q, hp.HMAT_MODE_FP64, stream)
+    torch.cuda.synchronize()
+    if dev.poll() != hp.HMAT_OK:
+        raise RuntimeError("device status error during warm-up")
+
+    clocks = ClockSampler(dist.local_rank)
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    hp.hmat_profile(dev.handle, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        hp.hmat_eval(dev.handle, W, Y, q, hp.HMAT_MODE_FP64, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms_local = e0.elapsed_time(e1) / args.steps
+    phases = hp.hmat_phase_times(dev.handle)
+    hp.hmat_profile(dev.handle, False)
+    ms = dist.max(ms_local)
+    if dev.poll() != hp.HMAT_OK:
+        raise RuntimeError("device status error during the timed steps")
+    value = dist.world * q / (ms / 1e3)
+
+    # end to end: host W -> device, evaluate, device Y -> host, every step (pinned host buffers)
+    Y_host = torch.empty_like(W_host).pin_memory()
+    hp.hmat_eval_host(dev.handle, W_host, Y_host, hp.HMAT_MODE_FP64, stream)
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        hp.hmat_eval_host(dev.handle, W_host, Y_host, hp.HMAT_MODE_FP64, stream)
+    e2e_s = dist.max((time.perf_counter() - t0) / args.steps)
+    e2e_value = dist.world * q / e2e_s
+
+    # roofline of the dominant kernel: the FP64 near-field grouped GEMM (bound by the DFMA pipe)
+    near_ms, near_launches = phases["near"]
+    near_ms_per_launch = near_ms / max(near_launches, 1)
+    near_flops = 2.0 * q * info["near_values"]
+    peak_gflops = hp.hmat_measure_fp64_peak()
+    achieved_tflops = near_flops / (near_ms_per_launch / 1e3) / 1e12
+    total_flops = 2.0 * q * (info["near_values"] + 2 * info["basis_values"] + info["coupling_values"])
+    bytes_step = 8.0 * (info["near_values"] + info["basis_values"] + info["coupling_values"]) + 2 * 8.0 * w.n * q
+    launches = sum(c for _, c in phases.values())
+
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "cols/s",
+        "n_gpus": dist.world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": w.name, "n": w.n, "d": w.d, "points": "10-component Gaussian mixture" if w.points == "gmm"
+            else "uniform", "q": q, "kernel": f"{w.kernel} {w.kernel_param}", "admissibility": w.admissibility,
+            "leaf_size": w.leaf_size, "tol": w.tol, "max_rank": w.max_rank, "mode": "fp64",
+            "near_entries": info["near_entries"], "far_entries": info["far_entries"],
+            "near_values": info["near_values"], "basis_values": info["basis_values"],
+            "coupling_values": info["coupling_values"], "sum_rank": info["sum_rank"],
+            "inspector_s": round(t_build, 2), "l2": "inputs larger than L2 (near blocks "
+            f"{8 * info['near_values'] / 1e9:.1f} GB read every step)",
+            "parallelism": f"replicas x{dist.world}",
+        },
+        "gflops": round(total_flops / (ms / 1e3) / 1e9, 2),
+        "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
+        "roofline": {
+            "bound": "alu", "kernel": "k_fp64_grouped_gemm (near field)",
+            "achieved": round(achieved_tflops, 4), "peak": round(peak_gflops / 1e3, 4), "unit": "TFLOP/s",
+            "frac": round(achieved_tflops / (peak_gflops / 1e3), 4), "traffic": None,
+            "peak_source": "FP64 DFMA loop measured in this run (hmat_measure_fp64_peak); nominal 1.25",
+            "step_bytes": bytes_step, "step_hbm_bound_ms": round(bytes_step / 6797.2e9 * 1e3, 3),
+        },
+        "e2e": {"value": round(e2e_value, 3), "unit": "cols/s", "h2d_bytes_per_step": int(W_host.numel() * 8),
+                "d2h_bytes_per_step": int(Y_host.numel() * 8)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    dev.close()
+
+    if dist.rank == 0 and dist.world == 1 and args.cpu_baseline == "auto":
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+# ----------------------------------------------------------------------------- CPU oracle (baseline / reference arm)
+
+def _cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _oracle_setup(w):
+    from oracle import hmatrix as hm
+    t0 = time.perf_counter()
+    H, _ = hm.compress_workload(w)
+    return hm, H, time.perf_counter() - t0
+
+
+def _oracle_sample_q(hm, H, w, target_s: float) -> int:
+    """Columns per sample so that one oracle evaluation takes about target_s seconds."""
+    from workloads import normal_rhs
+    q_probe = 4
+    t0 = time.perf_counter()
+    hm.evaluate(H, normal_rhs(w.n, q_probe, w.rhs_seed))
+    t_probe = time.perf_counter() - t0
+    q = int(q_probe * target_s / max(t_probe, 1e-3))
+    return max(1, min(w.q, q))
+
+
+def cpu_baseline(w, target_s: float) -> dict:
+    from workloads import normal_rhs
+    hm, H, t_compress = _oracle_setup(w)
+    qs = _oracle_sample_q(hm, H, w, target_s)
+    W = normal_rhs(w.n, w.q, w.rhs_seed)[:, :qs].copy()
+    t0 = time.perf_counter()
+    hm.evaluate(H, W)
+    dt = time.perf_counter() - t0
+    return {"value": round(qs / dt, 4), "unit": "cols/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"FP64 NumPy oracle evaluation of the same HMatrix recipe (oracle-compressed, "
+                      f"{t_compress:.0f} s, excluded) on the first {qs} of {w.q} columns of W: {dt:.1f} s"}
+
+
+def run_reference(args, dist: Dist) -> None:
+    if dist.rank != 0:
+        return
+    from workloads import normal_rhs
+    w = workload(args)
+    hm, H, t_compress = _oracle_setup(w)
+    per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(args.steps + args.warmup, 1)))
+    qs = _oracle_sample_q(hm, H, w, per_step)
+    W = normal_rhs(w.n, w.q, w.rhs_seed)[:, :qs].copy()
+    for _ in range(args.warmup):
+        hm.evaluate(H, W)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        hm.evaluate(H, W)
+        times.append(time.perf_counter() - t0)
+    mean = sum(times) / len(times)
+    value = qs / mean
+    sample = (f"FP64 NumPy oracle on the host cores, first {qs} of {w.q} columns per step "
+              f"(oracle compression {t_compress:.0f} s excluded)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "cols/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "d": w.d, "q": w.q, "q_sample": qs, "mode": "fp64"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "cols/s", "cores": _cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "cols/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    if args.impl == "reference":
+        run_reference(args, dist)
+    else:
+        run_gpu(args, dist)
+
+
+if __name__ == "__main__":
+    main()

@@ -83,6 +83,68 @@ typedef struct {
   const int64_t* perm;              /* [n_points] */
 } hmat_desc;
 
+/*
+ * Inspector (Section 3.1, "Modularizing compression"): tree construction,
+ * interaction computation and low-rank approximation in one native call.
+ *
+ * Kernel functions (Section 1): HMAT_KERNEL_GAUSSIAN exp(-r^2 / (2 h^2)) with
+ * kernel_param = h; HMAT_KERNEL_IMQ 1 / sqrt(r^2 + c^2) with kernel_param = c.
+ *
+ * Admissibility (Section 2.1, "Compression"; Section 4.1 for HSS):
+ * HMAT_ADM_HSS - every pair of distinct siblings is far (weak admissibility);
+ * HMAT_ADM_GEOMETRIC - nodes a, b are far when the distance of their centroids
+ *   exceeds eta * max(r_a, r_b), r the largest distance of a point of the node
+ *   to its centroid (the paper's tau * dist > diam_a + diam_b with tau = 2/eta);
+ * HMAT_ADM_NONE - nothing is far: every block is kept dense.
+ */
+#define HMAT_KERNEL_GAUSSIAN 0
+#define HMAT_KERNEL_IMQ 1
+#define HMAT_ADM_HSS 0
+#define HMAT_ADM_GEOMETRIC 1
+#define HMAT_ADM_NONE 2
+
+typedef struct {
+  int64_t n_points;
+  int32_t dim;
+  const double* points;      /* host, n_points x dim, row-major, caller order */
+  int32_t kernel;            /* HMAT_KERNEL_* */
+  double kernel_param;
+  int32_t admissibility;     /* HMAT_ADM_* */
+  double eta;
+  int32_t leaf_size;         /* >= 2 */
+  double tol;                /* ID tolerance (bacc): rank = #{|R_jj| > tol |R_11|} */
+  int32_t max_rank;          /* rank cap (>= 1) */
+  int32_t exact_columns;     /* 1: every far point as ID column, 0: a sample, -1: exact iff n_points <= 4096 */
+  uint64_t sample_seed;      /* seed of the column sample */
+  int32_t threads;           /* host threads of the inspector (0: all cores) */
+} hmat_build_params;
+
+/*
+ * hmat_build - compress the kernel matrix of a point set and load it.
+ *
+ * The cluster tree is a perfect kd-tree of depth L = ceil(log2(n / leaf_size)):
+ * every node above the leaves is split at the median of its widest bounding-box
+ * dimension (lowest dimension on ties; points ordered by that coordinate, then
+ * by input index; the left child takes floor(n/2)). Near/far pairs come from a
+ * dual-tree traversal from (root, root). Each node that is, or has an ancestor
+ * that is, in a far pair gets a nested row interpolative decomposition (column-
+ * pivoted Householder QR of K(R, C)^T; R = the node's points for a leaf and the
+ * children's skeletons otherwise; C = the points whose interaction with the node
+ * is approximated, or a seeded uniform sample of max(4 max_rank, 512) of them).
+ * The near blocks D and coupling blocks B are evaluated on the GPU directly into
+ * the packed device arena. Synchronous; host threads as requested.
+ */
+hmat_status hmat_build(const hmat_build_params* params, int flags, hmat_t* out);
+
+/*
+ * hmat_structure - copy out the structure of a loaded HMatrix (each pointer may
+ * be NULL to skip it): perm [n_points], rank [n_nodes], near_ptr [n_leaves + 1],
+ * near_idx [near entries], far_ptr [n_nodes + 1], far_idx [far entries], in the
+ * layout of hmat_desc.
+ */
+hmat_status hmat_structure(hmat_t h, int64_t* perm, int32_t* rank, int64_t* near_ptr, int32_t* near_idx,
+                           int64_t* far_ptr, int32_t* far_idx);
+
 /* Evaluation modes for hmat_eval. */
 #define HMAT_MODE_FP64 0            /* every block and every sum in FP64 (DFMA) */
 
@@ -115,6 +177,43 @@ hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q, int mode,
 
 /* hmat_reserve - size the workspace for right-hand sides of up to q_max columns. */
 hmat_status hmat_reserve(hmat_t h, int64_t q_max);
+
+/*
+ * hmat_eval_host - Y = K~ W with W and Y in HOST memory (n_points x q, FP64,
+ * caller order): copies W to a device buffer owned by the handle, evaluates as
+ * hmat_eval does, copies Y back, all on `stream`, and synchronises the stream
+ * before returning. Pinned host buffers give full copy bandwidth. The device
+ * buffers grow on demand (cudaMalloc, which synchronises the device).
+ */
+hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream);
+
+/*
+ * hmat_profile - enable (1) or disable (0) CUDA-event timing of every kernel
+ * launch of later evaluations on this handle; enabling clears earlier records.
+ * hmat_phase_times - synchronise on the recorded events and return, for phase
+ * kind k < n, the summed device time in ms[k] and the number of launches in
+ * launches[k] since profiling was enabled; then clear the records. Phase kinds:
+ * HMAT_PHASE_NEAR (near-field reduction over D), HMAT_PHASE_UP_LEAF (w = P^T W
+ * at the leaves), HMAT_PHASE_UP_TRANSFER (w = P^T [w_l; w_r], one launch per
+ * level), HMAT_PHASE_COUPLING (u = sum B w), HMAT_PHASE_DOWN_TRANSFER
+ * ([u_l; u_r] += P u, one launch per level), HMAT_PHASE_DOWN_LEAF (Y += P u).
+ */
+#define HMAT_PHASE_NEAR 0
+#define HMAT_PHASE_UP_LEAF 1
+#define HMAT_PHASE_UP_TRANSFER 2
+#define HMAT_PHASE_COUPLING 3
+#define HMAT_PHASE_DOWN_TRANSFER 4
+#define HMAT_PHASE_DOWN_LEAF 5
+#define HMAT_PHASE_COUNT 6
+hmat_status hmat_profile(hmat_t h, int enable);
+hmat_status hmat_phase_times(hmat_t h, double* ms, int64_t* launches, int n);
+
+/*
+ * hmat_measure_fp64_peak - FP64 FMA throughput of the current device, measured
+ * with a register-resident DFMA loop on every SM (about 0.1 s); *gflops receives
+ * GFLOP/s (2 flops per FMA). This is the ceiling of the FP64 evaluation mode.
+ */
+hmat_status hmat_measure_fp64_peak(double* gflops);
 
 /*
  * hmat_status_poll - synchronise `stream` and return the device status word

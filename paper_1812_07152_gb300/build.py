@@ -16,7 +16,7 @@ BUILDDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(LIBDIR, "libhmat.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", "-I" + os.path.join(ROOT, "include")]
+CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3,-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]
 
 
 def _nvcc() -> str:

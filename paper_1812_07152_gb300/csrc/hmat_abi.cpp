@@ -35,7 +35,7 @@ int level_of(int64_t a) {
   return l;
 }
 
-hmat_status validate(const hmat_desc* d, Validated* v) {
+hmat_status validate(const hmat_desc* d, bool host_blocks, Validated* v) {
   if (!d || d->levels < 0 || d->levels > 24 || d->n_points < 0) return HMAT_EINVAL;
   const int64_t n_nodes = ((int64_t)2 << d->levels) - 1;
   const int64_t n_leaves = (int64_t)1 << d->levels;
@@ -68,14 +68,15 @@ hmat_status validate(const hmat_desc* d, Validated* v) {
     if (d->near_ptr[i + 1] < d->near_ptr[i]) return HMAT_EINVAL;
   const int64_t n_near = d->near_ptr[n_leaves];
   if (n_near > INT32_MAX) return HMAT_EINVAL;
-  if (n_near > 0 && (!d->near_idx || !d->near)) return HMAT_EINVAL;
+  if (n_near > 0 && (!d->near_idx || (host_blocks && !d->near))) return HMAT_EINVAL;
   for (int64_t e = 0; e < n_near; ++e) {
     if (d->near_idx[e] < 0 || d->near_idx[e] >= n_leaves) return HMAT_EINVAL;
   }
   for (int64_t i = 0; i < n_leaves; ++i)
     for (int64_t e = d->near_ptr[i]; e < d->near_ptr[i + 1]; ++e) {
       const int64_t j = d->near_idx[e];
-      if (d->node_size[first_leaf + i] * d->node_size[first_leaf + j] > 0 && !d->near[e]) return HMAT_EINVAL;
+      if (host_blocks && d->node_size[first_leaf + i] * d->node_size[first_leaf + j] > 0 && !d->near[e])
+        return HMAT_EINVAL;
     }
   // far CSR over nodes
   if (d->far_ptr[0] != 0) return HMAT_EINVAL;
@@ -83,12 +84,12 @@ hmat_status validate(const hmat_desc* d, Validated* v) {
     if (d->far_ptr[a + 1] < d->far_ptr[a]) return HMAT_EINVAL;
   const int64_t n_far = d->far_ptr[n_nodes];
   if (n_far > INT32_MAX) return HMAT_EINVAL;
-  if (n_far > 0 && (!d->far_idx || !d->coupling)) return HMAT_EINVAL;
+  if (n_far > 0 && (!d->far_idx || (host_blocks && !d->coupling))) return HMAT_EINVAL;
   for (int64_t a = 0; a < n_nodes; ++a)
     for (int64_t e = d->far_ptr[a]; e < d->far_ptr[a + 1]; ++e) {
       const int64_t b = d->far_idx[e];
       if (b < 0 || b >= n_nodes || b == a || level_of(a) != level_of(b)) return HMAT_EINVAL;
-      if ((int64_t)d->rank[a] * d->rank[b] > 0 && !d->coupling[e]) return HMAT_EINVAL;
+      if (host_blocks && (int64_t)d->rank[a] * d->rank[b] > 0 && !d->coupling[e]) return HMAT_EINVAL;
     }
   // bases
   for (int64_t a = 0; a < n_nodes; ++a) {
@@ -189,6 +190,17 @@ class Uploader {
 };
 
 void free_device(Handle* h) {
+  for (auto& r : h->prof) {
+    h->event_pool.push_back(r.start);
+    h->event_pool.push_back(r.stop);
+  }
+  h->prof.clear();
+  for (cudaEvent_t ev : h->event_pool) cudaEventDestroy(ev);
+  h->event_pool.clear();
+  cudaFree(h->host_w);
+  cudaFree(h->host_y);
+  h->host_w = nullptr;
+  h->host_y = nullptr;
   cudaFree(h->arena);
   cudaFree(h->perm);
   cudaFree(h->tasks);
@@ -219,12 +231,12 @@ hmat_status cuda_status(cudaError_t e) {
 
 }  // namespace
 
-extern "C" hmat_status hmat_load(const hmat_desc* d, int flags, hmat_t* out) {
-  if (!out) return HMAT_EINVAL;
+namespace hmat {
+
+hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, hmat_handle** out) {
   *out = nullptr;
-  if (flags != 0) return HMAT_EUNSUPPORTED;
   Validated v;
-  hmat_status st = validate(d, &v);
+  hmat_status st = validate(d, src == nullptr, &v);
   if (st != HMAT_OK) return st;
 
   std::unique_ptr<hmat_handle> h(new (std::nothrow) hmat_handle());
@@ -239,6 +251,11 @@ extern "C" hmat_status hmat_load(const hmat_desc* d, int flags, hmat_t* out) {
   h->begin.assign(d->node_begin, d->node_begin + v.n_nodes);
   h->size.assign(d->node_size, d->node_size + v.n_nodes);
   h->rank.assign(d->rank, d->rank + v.n_nodes);
+  h->perm_host.assign(d->perm, d->perm + d->n_points);
+  h->near_ptr.assign(d->near_ptr, d->near_ptr + v.n_leaves + 1);
+  h->near_idx.assign(d->near_idx, d->near_idx + v.n_near);
+  h->far_ptr.assign(d->far_ptr, d->far_ptr + v.n_nodes + 1);
+  h->far_idx.assign(d->far_idx, d->far_idx + v.n_far);
   h->skel_off.resize(v.n_nodes + 1);
   h->skel_off[0] = 0;
   for (int64_t a = 0; a < v.n_nodes; ++a) h->skel_off[a + 1] = h->skel_off[a] + h->rank[a];
@@ -390,21 +407,57 @@ extern "C" hmat_status hmat_load(const hmat_desc* d, int flags, hmat_t* out) {
     if ((e = up.init(h->arena, (size_t)1 << 23)) != cudaSuccess) return fail(e);
     bool finite = true;
     cudaError_t ce = cudaSuccess;
-    for (int64_t i = 0; i < v.n_leaves && ce == cudaSuccess; ++i)
-      for (int64_t ee = d->near_ptr[i]; ee < d->near_ptr[i + 1] && ce == cudaSuccess; ++ee) {
-        const int64_t cnt = h->size[fl + i] * h->size[fl + d->near_idx[ee]];
-        finite &= up.put(near_off[ee], d->near[ee], cnt, &ce);
-      }
+    if (!src) {
+      for (int64_t i = 0; i < v.n_leaves && ce == cudaSuccess; ++i)
+        for (int64_t ee = d->near_ptr[i]; ee < d->near_ptr[i + 1] && ce == cudaSuccess; ++ee) {
+          const int64_t cnt = h->size[fl + i] * h->size[fl + d->near_idx[ee]];
+          finite &= up.put(near_off[ee], d->near[ee], cnt, &ce);
+        }
+    }
     for (int64_t a = 0; a < v.n_nodes && ce == cudaSuccess; ++a)
       if (h->rank[a] > 0) finite &= up.put(basis_off[a], d->basis[a], rows_of(a) * h->rank[a], &ce);
-    for (int64_t a = 0; a < v.n_nodes && ce == cudaSuccess; ++a)
-      for (int64_t ee = d->far_ptr[a]; ee < d->far_ptr[a + 1] && ce == cudaSuccess; ++ee) {
-        const int64_t cnt = (int64_t)h->rank[a] * h->rank[d->far_idx[ee]];
-        finite &= up.put(far_off[ee], d->coupling[ee], cnt, &ce);
-      }
+    if (!src) {
+      for (int64_t a = 0; a < v.n_nodes && ce == cudaSuccess; ++a)
+        for (int64_t ee = d->far_ptr[a]; ee < d->far_ptr[a + 1] && ce == cudaSuccess; ++ee) {
+          const int64_t cnt = (int64_t)h->rank[a] * h->rank[d->far_idx[ee]];
+          finite &= up.put(far_off[ee], d->coupling[ee], cnt, &ce);
+        }
+    }
     if (ce == cudaSuccess) ce = up.finish();
     if (ce != cudaSuccess) return fail(ce);
     if (!finite) { free_device(h.get()); return HMAT_EINVAL; }
+  }
+  if (src) {  // evaluate D and B on the device from the points
+    std::vector<BlockJob> jobs;
+    for (int64_t i = 0; i < v.n_leaves; ++i)
+      for (int64_t ee = d->near_ptr[i]; ee < d->near_ptr[i + 1]; ++ee) {
+        const int64_t a = fl + i, b = fl + d->near_idx[ee];
+        if (h->size[a] * h->size[b] == 0) continue;
+        jobs.push_back(BlockJob{near_off[ee], h->begin[a], h->begin[b], (int32_t)h->size[a], (int32_t)h->size[b], 0, 0});
+      }
+    for (int64_t a = 0; a < v.n_nodes; ++a)
+      for (int64_t ee = d->far_ptr[a]; ee < d->far_ptr[a + 1]; ++ee) {
+        const int64_t b = d->far_idx[ee];
+        if ((int64_t)h->rank[a] * h->rank[b] == 0) continue;
+        jobs.push_back(BlockJob{far_off[ee], h->skel_off[a], h->skel_off[b], h->rank[a], h->rank[b], 1, 1});
+      }
+    std::vector<double> pts(src->points_tree, src->points_tree + d->n_points * (int64_t)src->dim);
+    std::vector<int64_t> skel(src->skel_points, src->skel_points + h->sum_rank);
+    double* dpts = nullptr;
+    int64_t* dskel = nullptr;
+    BlockJob* djobs = nullptr;
+    int64_t scratch = 0;
+    cudaError_t ce = upload(&dpts, pts, &scratch);
+    if (ce == cudaSuccess) ce = upload(&dskel, skel, &scratch);
+    if (ce == cudaSuccess) ce = upload(&djobs, jobs, &scratch);
+    if (ce == cudaSuccess && !jobs.empty())
+      ce = launch_eval_blocks(djobs, (int64_t)jobs.size(), dpts, src->dim, dskel, src->kernel, src->kernel_param,
+                              h->arena, 0);
+    if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+    cudaFree(dpts);
+    cudaFree(dskel);
+    cudaFree(djobs);
+    if (ce != cudaSuccess) return fail(ce);
   }
   std::vector<int64_t> perm(d->perm, d->perm + d->n_points);
   if ((e = upload(&h->perm, perm, &h->device_bytes)) != cudaSuccess) return fail(e);
@@ -414,6 +467,30 @@ extern "C" hmat_status hmat_load(const hmat_desc* d, int flags, hmat_t* out) {
   std::vector<int> zero(1, 0);
   if ((e = upload(&h->status, zero, &h->device_bytes)) != cudaSuccess) return fail(e);
   *out = h.release();
+  return HMAT_OK;
+}
+
+}  // namespace hmat
+
+extern "C" hmat_status hmat_load(const hmat_desc* d, int flags, hmat_t* out) {
+  if (!out) return HMAT_EINVAL;
+  *out = nullptr;
+  if (flags != 0) return HMAT_EUNSUPPORTED;
+  return load_impl(d, nullptr, out);
+}
+
+extern "C" hmat_status hmat_structure(hmat_t h, int64_t* perm, int32_t* rank, int64_t* near_ptr, int32_t* near_idx,
+                                      int64_t* far_ptr, int32_t* far_idx) {
+  if (!h) return HMAT_EINVAL;
+  auto put = [](auto* dst, const auto& v) {
+    if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(v[0]));
+  };
+  put(perm, h->perm_host);
+  put(rank, h->rank);
+  put(near_ptr, h->near_ptr);
+  put(near_idx, h->near_idx);
+  put(far_ptr, h->far_ptr);
+  put(far_idx, h->far_idx);
   return HMAT_OK;
 }
 
@@ -465,10 +542,94 @@ extern "C" hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q
     double* Yd = ph.y == MAT_USER ? Y : (ph.y == MAT_SKEL_W ? h->ws : h->us);
     const int64_t* xm = ph.x == MAT_USER ? h->perm : nullptr;
     const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
+    Handle::ProfRecord rec{(int32_t)ph.kind, nullptr, nullptr};
+    if (h->profiling) {
+      for (cudaEvent_t* ev : {&rec.start, &rec.stop}) {
+        if (!h->event_pool.empty()) {
+          *ev = h->event_pool.back();
+          h->event_pool.pop_back();
+        } else if (cudaEventCreate(ev) != cudaSuccess) {
+          return HMAT_ECUDA;
+        }
+      }
+      if (cudaEventRecord(rec.start, s) != cudaSuccess) return HMAT_ECUDA;
+    }
     cudaError_t e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, s);
     if (e != cudaSuccess) return cuda_status(e);
+    if (h->profiling) {
+      if (cudaEventRecord(rec.stop, s) != cudaSuccess) return HMAT_ECUDA;
+      h->prof.push_back(rec);
+    }
   }
   return HMAT_OK;
+}
+
+extern "C" hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
+  if (!h || q < 0) return HMAT_EINVAL;
+  if (mode != HMAT_MODE_FP64) return HMAT_EUNSUPPORTED;
+  if (q == 0 || h->n_points == 0) return HMAT_OK;
+  if (!W || !Y) return HMAT_EINVAL;
+  const int64_t values = h->n_points * q;
+  if (values > h->host_cap) {
+    double *w = nullptr, *y = nullptr;
+    cudaError_t e = cudaMalloc((void**)&w, (size_t)values * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&y, (size_t)values * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaFree(w);
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+    cudaDeviceSynchronize();
+    cudaFree(h->host_w);
+    cudaFree(h->host_y);
+    h->device_bytes += 2 * (values - h->host_cap) * (int64_t)sizeof(double);
+    h->host_w = w;
+    h->host_y = y;
+    h->host_cap = values;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)values * sizeof(double);
+  cudaError_t e = cudaMemcpyAsync(h->host_w, W, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  hmat_status st = hmat_eval(h, h->host_w, h->host_y, q, mode, stream);
+  if (st != HMAT_OK) return st;
+  e = cudaMemcpyAsync(Y, h->host_y, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e);
+}
+
+extern "C" hmat_status hmat_profile(hmat_t h, int enable) {
+  if (!h) return HMAT_EINVAL;
+  for (auto& r : h->prof) {
+    h->event_pool.push_back(r.start);
+    h->event_pool.push_back(r.stop);
+  }
+  h->prof.clear();
+  h->profiling = enable != 0;
+  return HMAT_OK;
+}
+
+extern "C" hmat_status hmat_phase_times(hmat_t h, double* ms, int64_t* launches, int n) {
+  if (!h || n < 0 || (n > 0 && (!ms || !launches))) return HMAT_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  hmat_status st = HMAT_OK;
+  for (auto& r : h->prof) {
+    float t = 0.0f;
+    cudaError_t e = cudaEventSynchronize(r.stop);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.start, r.stop);
+    if (e != cudaSuccess) st = HMAT_ECUDA;
+    if (r.kind < n) {
+      ms[r.kind] += t;
+      launches[r.kind] += 1;
+    }
+    h->event_pool.push_back(r.start);
+    h->event_pool.push_back(r.stop);
+  }
+  h->prof.clear();
+  return st;
 }
 
 extern "C" hmat_status hmat_status_poll(hmat_t h, void* stream) {

@@ -1,0 +1,368 @@
+// Inspector: the compression modules of Section 3.1 on the host, in native code.
+//
+//  * tree construction: a perfect kd-tree by median splits (the widest bounding-box
+//    dimension; lowest dimension on ties; ties of coordinates by input index);
+//  * interaction computation: a dual-tree traversal from (root, root) that marks a
+//    pair far when it is admissible (Section 2.1) and near when two leaves are not;
+//  * low-rank approximation: a nested row interpolative decomposition per node,
+//    bottom-up, from a column-pivoted Householder QR of K(R, C)^T whose rank is the
+//    number of pivots above tol * |R_11| (the srank tuned to the block accuracy),
+//    capped at max_rank.
+//
+// The dense near blocks and the coupling blocks are not formed here: the loader
+// evaluates them on the GPU into the packed arena (hmat_blocks.cu).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+#include "hmat_internal.h"
+
+namespace hmat {
+namespace {
+
+constexpr int64_t kExactColumnsMaxN = 4096;
+
+double kernel_value(int kernel, double param, const double* x, const double* y, int d) {
+  double r2 = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const double diff = x[k] - y[k];
+    r2 += diff * diff;
+  }
+  return kernel == HMAT_KERNEL_GAUSSIAN ? std::exp(-r2 / (2.0 * param * param)) : 1.0 / std::sqrt(r2 + param * param);
+}
+
+template <class F>
+void parallel_for(int64_t n, int threads, F&& f) {
+  if (n <= 0) return;
+  const int t = (int)std::min<int64_t>(threads, n);
+  if (t <= 1) {
+    for (int64_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  std::vector<std::thread> pool;
+  for (int w = 0; w < t; ++w)
+    pool.emplace_back([&]() {
+      for (int64_t i; (i = next.fetch_add(1)) < n;) f(i);
+    });
+  for (auto& th : pool) th.join();
+}
+
+uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct Tree {
+  int levels = 0;
+  int64_t n_nodes = 0, first_leaf = 0;
+  std::vector<int64_t> begin, size, perm;
+};
+
+int tree_depth(int64_t n, int64_t leaf) {
+  int L = 0;
+  while ((n + ((int64_t)1 << L) - 1) / ((int64_t)1 << L) > leaf) ++L;
+  return L;
+}
+
+void build_tree(const double* X, int64_t n, int d, int leaf, int threads, Tree* t) {
+  t->levels = tree_depth(n, leaf);
+  t->n_nodes = ((int64_t)2 << t->levels) - 1;
+  t->first_leaf = ((int64_t)1 << t->levels) - 1;
+  t->begin.assign(t->n_nodes, 0);
+  t->size.assign(t->n_nodes, 0);
+  t->perm.resize(n);
+  std::iota(t->perm.begin(), t->perm.end(), 0);
+  t->size[0] = n;
+  for (int level = 0; level < t->levels; ++level) {
+    const int64_t lo = ((int64_t)1 << level) - 1, cnt = (int64_t)1 << level;
+    parallel_for(cnt, threads, [&](int64_t k) {
+      const int64_t a = lo + k, b0 = t->begin[a], nb = t->size[a];
+      int64_t* idx = t->perm.data() + b0;
+      int dim = 0;
+      double best = -1.0;
+      for (int j = 0; j < d; ++j) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (int64_t i = 0; i < nb; ++i) {
+          const double v = X[idx[i] * d + j];
+          mn = std::min(mn, v);
+          mx = std::max(mx, v);
+        }
+        if (nb > 0 && mx - mn > best) { best = mx - mn; dim = j; }  // strict: first maximum wins
+      }
+      std::sort(idx, idx + nb, [&](int64_t p, int64_t q) {
+        const double vp = X[p * d + dim], vq = X[q * d + dim];
+        return vp < vq || (vp == vq && p < q);
+      });
+      const int64_t half = nb / 2;
+      t->begin[2 * a + 1] = b0;
+      t->size[2 * a + 1] = half;
+      t->begin[2 * a + 2] = b0 + half;
+      t->size[2 * a + 2] = nb - half;
+    });
+  }
+}
+
+// Centroid (mean, accumulated point by point in tree order) and radius per node.
+void geometry(const Tree& t, const double* Xt, int d, int threads, std::vector<double>* cent, std::vector<double>* rad) {
+  cent->assign(t.n_nodes * d, 0.0);
+  rad->assign(t.n_nodes, 0.0);
+  parallel_for(t.n_nodes, threads, [&](int64_t a) {
+    const int64_t b0 = t.begin[a], nb = t.size[a];
+    if (nb == 0) return;
+    double* c = cent->data() + a * d;
+    for (int64_t i = 0; i < nb; ++i)
+      for (int j = 0; j < d; ++j) c[j] += Xt[(b0 + i) * d + j];
+    for (int j = 0; j < d; ++j) c[j] /= (double)nb;
+    double r = 0.0;
+    for (int64_t i = 0; i < nb; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < d; ++j) {
+        const double diff = Xt[(b0 + i) * d + j] - c[j];
+        s += diff * diff;
+      }
+      r = std::max(r, std::sqrt(s));
+    }
+    (*rad)[a] = r;
+  });
+}
+
+void interactions(const Tree& t, const double* Xt, int d, int adm, double eta, int threads,
+                  std::vector<std::pair<int64_t, int64_t>>* near, std::vector<std::pair<int64_t, int64_t>>* far) {
+  std::vector<double> cent, rad;
+  if (adm == HMAT_ADM_GEOMETRIC) geometry(t, Xt, d, threads, &cent, &rad);
+  auto admissible = [&](int64_t a, int64_t b) {
+    if (a == b || adm == HMAT_ADM_NONE) return false;
+    if (adm == HMAT_ADM_HSS) return true;
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) {
+      const double diff = cent[a * d + j] - cent[b * d + j];
+      s += diff * diff;
+    }
+    return std::sqrt(s) > eta * std::max(rad[a], rad[b]);
+  };
+  std::vector<std::pair<int64_t, int64_t>> frontier{{0, 0}}, next;
+  for (int level = 0; level <= t.levels; ++level) {
+    next.clear();
+    for (auto [a, b] : frontier) {
+      if (admissible(a, b)) far->push_back({a, b});
+      else if (level == t.levels) near->push_back({a, b});
+      else
+        for (int64_t ca : {2 * a + 1, 2 * a + 2})
+          for (int64_t cb : {2 * b + 1, 2 * b + 2}) next.push_back({ca, cb});
+    }
+    frontier.swap(next);
+  }
+  std::sort(near->begin(), near->end());
+  std::sort(far->begin(), far->end());
+}
+
+// Row ID of M = K(rows, cols) (|rows| x |cols|): M ~= P M[skel, :], from a column-
+// pivoted Householder QR of A = M^T (|cols| x |rows|, column-major) stopped at the
+// first pivot |R_kk| <= tol |R_11| or at max_rank. P is |rows| x k row-major.
+void row_id(const std::vector<double>& Xt, int d, int kernel, double param, const std::vector<int64_t>& rows,
+            const std::vector<int64_t>& cols, double tol, int max_rank, std::vector<int64_t>* skel,
+            std::vector<double>* P) {
+  const int64_t n = (int64_t)rows.size(), m = (int64_t)cols.size();
+  skel->clear();
+  P->clear();
+  if (n == 0 || m == 0) return;
+  std::vector<double> A((size_t)(m * n));
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i)
+      A[j * m + i] = kernel_value(kernel, param, &Xt[cols[i] * d], &Xt[rows[j] * d], d);
+  std::vector<int64_t> piv(n);
+  std::iota(piv.begin(), piv.end(), 0);
+  std::vector<double> vn1(n), vn2(n);
+  for (int64_t j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) s += A[j * m + i] * A[j * m + i];
+    vn1[j] = vn2[j] = std::sqrt(s);
+  }
+  const double tol3z = std::sqrt(2.220446049250313e-16);
+  const int64_t kmax = std::min<int64_t>({(int64_t)max_rank, n, m});
+  double r11 = 0.0;
+  int64_t k = 0;
+  for (; k < kmax; ++k) {
+    int64_t p = k;
+    for (int64_t j = k + 1; j < n; ++j)
+      if (vn1[j] > vn1[p]) p = j;
+    if (p != k) {
+      std::swap_ranges(A.begin() + p * m, A.begin() + (p + 1) * m, A.begin() + k * m);
+      std::swap(piv[p], piv[k]);
+      vn1[p] = vn1[k];
+      vn2[p] = vn2[k];
+    }
+    // Householder reflector of A[k:m, k]
+    double* col = &A[k * m];
+    const double alpha = col[k];
+    double xn = 0.0;
+    for (int64_t i = k + 1; i < m; ++i) xn += col[i] * col[i];
+    xn = std::sqrt(xn);
+    double beta = alpha, tau = 0.0;
+    if (xn != 0.0) {
+      beta = -std::copysign(std::hypot(alpha, xn), alpha);
+      tau = (beta - alpha) / beta;
+      const double scal = 1.0 / (alpha - beta);
+      for (int64_t i = k + 1; i < m; ++i) col[i] *= scal;
+    }
+    col[k] = beta;
+    const double rkk = std::fabs(beta);
+    if (k == 0) r11 = rkk;
+    if (!(rkk > tol * r11) || r11 == 0.0) break;  // this pivot is below the accuracy: rank = k
+    // apply (I - tau v v^T), v = [1; col[k+1:m]], to the remaining columns
+    if (tau != 0.0)
+      for (int64_t j = k + 1; j < n; ++j) {
+        double* cj = &A[j * m];
+        double w = cj[k];
+        for (int64_t i = k + 1; i < m; ++i) w += col[i] * cj[i];
+        w *= tau;
+        cj[k] -= w;
+        for (int64_t i = k + 1; i < m; ++i) cj[i] -= w * col[i];
+      }
+    // downdate the partial column norms (recompute when cancellation is large)
+    for (int64_t j = k + 1; j < n; ++j) {
+      if (vn1[j] == 0.0) continue;
+      const double r = std::fabs(A[j * m + k]) / vn1[j];
+      const double temp = std::max(0.0, (1.0 + r) * (1.0 - r));
+      const double ratio = vn1[j] / vn2[j];
+      if (temp * ratio * ratio <= tol3z) {
+        double s = 0.0;
+        for (int64_t i = k + 1; i < m; ++i) s += A[j * m + i] * A[j * m + i];
+        vn1[j] = vn2[j] = std::sqrt(s);
+      } else {
+        vn1[j] *= std::sqrt(temp);
+      }
+    }
+  }
+  // T = R11^{-1} R12 (k x (n - k)), back substitution column by column
+  const int64_t nt = n - k;
+  std::vector<double> T((size_t)(k * nt));
+  for (int64_t c = 0; c < nt; ++c) {
+    for (int64_t i = k - 1; i >= 0; --i) {
+      double s = A[(k + c) * m + i];
+      for (int64_t j = i + 1; j < k; ++j) s -= A[j * m + i] * T[j * nt + c];
+      T[i * nt + c] = s / A[i * m + i];
+    }
+  }
+  P->assign((size_t)(n * k), 0.0);
+  skel->resize(k);
+  for (int64_t j = 0; j < k; ++j) {
+    (*P)[piv[j] * k + j] = 1.0;
+    (*skel)[j] = rows[piv[j]];
+  }
+  for (int64_t c = 0; c < nt; ++c)
+    for (int64_t j = 0; j < k; ++j) (*P)[piv[k + c] * k + j] = T[j * nt + c];
+}
+
+}  // namespace
+}  // namespace hmat
+
+using namespace hmat;
+
+extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t* out) {
+  if (!out) return HMAT_EINVAL;
+  *out = nullptr;
+  if (flags != 0) return HMAT_EUNSUPPORTED;
+  if (!p || p->n_points < 1 || p->dim < 1 || p->dim > 64 || !p->points || p->leaf_size < 2 || p->max_rank < 1 ||
+      !(p->tol >= 0.0) || !(p->kernel_param > 0.0) ||
+      (p->kernel != HMAT_KERNEL_GAUSSIAN && p->kernel != HMAT_KERNEL_IMQ) ||
+      (p->admissibility != HMAT_ADM_HSS && p->admissibility != HMAT_ADM_GEOMETRIC &&
+       p->admissibility != HMAT_ADM_NONE) ||
+      (p->admissibility == HMAT_ADM_GEOMETRIC && !(p->eta > 0.0)))
+    return HMAT_EINVAL;
+  const int64_t n = p->n_points;
+  const int d = p->dim;
+  for (int64_t i = 0; i < n * d; ++i)
+    if (!std::isfinite(p->points[i])) return HMAT_EINVAL;
+  const int threads = p->threads > 0 ? p->threads : (int)std::max(1u, std::thread::hardware_concurrency());
+
+  Tree t;
+  build_tree(p->points, n, d, p->leaf_size, threads, &t);
+  std::vector<double> Xt((size_t)(n * d));
+  for (int64_t k = 0; k < n; ++k) std::memcpy(&Xt[k * d], &p->points[t.perm[k] * d], d * sizeof(double));
+
+  std::vector<std::pair<int64_t, int64_t>> near, far;
+  interactions(t, Xt.data(), d, p->admissibility, p->eta, threads, &near, &far);
+  std::vector<std::vector<int64_t>> far_of(t.n_nodes);
+  for (auto [a, b] : far) far_of[a].push_back(b);
+  std::vector<uint8_t> needs(t.n_nodes, 0);
+  for (int64_t a = 1; a < t.n_nodes; ++a) needs[a] = !far_of[a].empty() || needs[(a - 1) / 2];
+
+  const bool exact = p->exact_columns > 0 || (p->exact_columns < 0 && n <= kExactColumnsMaxN);
+  const int64_t n_sample = std::max<int64_t>(4 * (int64_t)p->max_rank, 512);
+  std::vector<std::vector<int64_t>> skel(t.n_nodes);
+  std::vector<std::vector<double>> basis(t.n_nodes);
+  std::vector<int32_t> rank(t.n_nodes, 0);
+  for (int level = t.levels; level >= 1; --level) {
+    const int64_t lo = ((int64_t)1 << level) - 1, cnt = (int64_t)1 << level;
+    parallel_for(cnt, threads, [&](int64_t k) {
+      const int64_t a = lo + k;
+      if (!needs[a]) return;
+      std::vector<int64_t> rows;
+      if (level == t.levels) {
+        rows.resize(t.size[a]);
+        std::iota(rows.begin(), rows.end(), t.begin[a]);
+      } else {
+        rows = skel[2 * a + 1];
+        rows.insert(rows.end(), skel[2 * a + 2].begin(), skel[2 * a + 2].end());
+      }
+      std::vector<int64_t> cols;
+      for (int64_t g = a;; g = (g - 1) / 2) {
+        for (int64_t b : far_of[g])
+          for (int64_t i = 0; i < t.size[b]; ++i) cols.push_back(t.begin[b] + i);
+        if (g == 0) break;
+      }
+      std::sort(cols.begin(), cols.end());
+      if (!exact && (int64_t)cols.size() > n_sample) {  // seeded uniform sample without replacement
+        uint64_t state = p->sample_seed * 0x100000001B3ull + (uint64_t)a;
+        for (int64_t i = 0; i < n_sample; ++i) {
+          const int64_t j = i + (int64_t)(splitmix64(state) % (uint64_t)(cols.size() - i));
+          std::swap(cols[i], cols[j]);
+        }
+        cols.resize(n_sample);
+        std::sort(cols.begin(), cols.end());
+      }
+      row_id(Xt, d, p->kernel, p->kernel_param, rows, cols, p->tol, p->max_rank, &skel[a], &basis[a]);
+      rank[a] = (int32_t)skel[a].size();
+    });
+  }
+
+  // assemble the hmat_desc structure (blocks are evaluated on the device)
+  std::vector<int64_t> near_ptr(t.first_leaf + 2, 0), far_ptr(t.n_nodes + 1, 0);
+  std::vector<int32_t> near_idx, far_idx;
+  for (auto [i, j] : near) near_ptr[i - t.first_leaf + 1]++;
+  for (size_t i = 1; i < near_ptr.size(); ++i) near_ptr[i] += near_ptr[i - 1];
+  for (auto [i, j] : near) near_idx.push_back((int32_t)(j - t.first_leaf));
+  for (auto [a, b] : far) far_ptr[a + 1]++;
+  for (size_t i = 1; i < far_ptr.size(); ++i) far_ptr[i] += far_ptr[i - 1];
+  for (auto [a, b] : far) far_idx.push_back((int32_t)b);
+  std::vector<const double*> basis_ptr(t.n_nodes, nullptr);
+  std::vector<int64_t> skel_points;
+  for (int64_t a = 0; a < t.n_nodes; ++a) {
+    if (rank[a] > 0) basis_ptr[a] = basis[a].data();
+    skel_points.insert(skel_points.end(), skel[a].begin(), skel[a].end());
+  }
+  hmat_desc desc;
+  desc.n_points = n;
+  desc.levels = t.levels;
+  desc.node_begin = t.begin.data();
+  desc.node_size = t.size.data();
+  desc.rank = rank.data();
+  desc.near_ptr = near_ptr.data();
+  desc.near_idx = near_idx.data();
+  desc.far_ptr = far_ptr.data();
+  desc.far_idx = far_idx.data();
+  desc.basis = basis_ptr.data();
+  desc.coupling = nullptr;
+  desc.near = nullptr;
+  desc.perm = t.perm.data();
+  DeviceBlockSource src{Xt.data(), d, skel_points.data(), p->kernel, p->kernel_param};
+  return load_impl(&desc, &src, out);
+}

@@ -73,8 +73,8 @@ struct Handle {
   int64_t near_values = 0, basis_values = 0, coupling_values = 0;
   int64_t sum_rank = 0;
 
-  std::vector<int64_t> begin, size, skel_off;
-  std::vector<int32_t> rank;
+  std::vector<int64_t> begin, size, skel_off, perm_host, near_ptr, far_ptr;
+  std::vector<int32_t> rank, near_idx, far_idx;
   std::vector<Phase> phases;
 
   // device
@@ -89,8 +89,52 @@ struct Handle {
   double* us = nullptr;          // skeleton potentials u (sum_rank x q_cap)
   int64_t q_cap = 0;
   int64_t ws_bytes = 0;
+  double* host_w = nullptr;      // device copies of W / Y for hmat_eval_host
+  double* host_y = nullptr;
+  int64_t host_cap = 0;          // capacity of host_w / host_y in values
+
+  // per-launch event timing (hmat_profile / hmat_phase_times)
+  struct ProfRecord {
+    int32_t kind;
+    cudaEvent_t start, stop;
+  };
+  bool profiling = false;
+  std::vector<ProfRecord> prof;
+  std::vector<cudaEvent_t> event_pool;
   int64_t device_bytes = 0;
 };
+
+// A dense kernel block evaluated on the device: arena[a_off + r * cols + c] =
+// k(x[row point r], x[col point c]); a point index list is either the range
+// row_off .. row_off + rows - 1 of tree-order points (skel = 0) or the entries
+// row_off .. of the skeleton point list (skel = 1).
+struct BlockJob {
+  int64_t a_off;
+  int64_t row_off;
+  int64_t col_off;
+  int32_t rows;
+  int32_t cols;
+  int32_t row_skel;
+  int32_t col_skel;
+};
+
+// Source of the near and coupling blocks when they are evaluated on the device.
+struct DeviceBlockSource {
+  const double* points_tree;   // host, n_points x dim, tree order
+  int32_t dim;
+  const int64_t* skel_points;  // host, sum of ranks entries in node order (tree-order point ids)
+  int32_t kernel;
+  double kernel_param;
+};
+
+// Shared body of hmat_load (src == nullptr: every block from the host arrays of d)
+// and hmat_build (src != nullptr: d->near and d->coupling are ignored and the
+// blocks are evaluated on the device from the points).
+hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, hmat_handle** out);
+
+cudaError_t launch_eval_blocks(const BlockJob* jobs, int64_t n_jobs, const double* pts, int dim,
+                               const int64_t* skel_pts, int kernel, double param, double* arena,
+                               cudaStream_t stream);
 
 // Launch the FP64 grouped GEMM of one phase on `stream`.
 cudaError_t launch_fp64_phase(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map,

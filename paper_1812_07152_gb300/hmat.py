@@ -25,6 +25,8 @@ HMAT_EDEVICE = -6
 
 HMAT_MODE_FP64 = 0
 
+PHASES = ("near", "up_leaf", "up_transfer", "coupling", "down_transfer", "down_leaf")
+
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "lib", "libhmat.so")
 _HEADER = os.path.join(os.path.dirname(_PKG), "include", "hmat.h")
@@ -52,6 +54,34 @@ class HmatDesc(ctypes.Structure):
     ]
 
 
+HMAT_KERNEL_GAUSSIAN = 0
+HMAT_KERNEL_IMQ = 1
+HMAT_ADM_HSS = 0
+HMAT_ADM_GEOMETRIC = 1
+HMAT_ADM_NONE = 2
+
+_KERNELS = {"gaussian": HMAT_KERNEL_GAUSSIAN, "imq": HMAT_KERNEL_IMQ}
+_ADMISSIBILITY = {"hss": HMAT_ADM_HSS, "geometric": HMAT_ADM_GEOMETRIC, "none": HMAT_ADM_NONE}
+
+
+class HmatBuildParams(ctypes.Structure):
+    _fields_ = [
+        ("n_points", ctypes.c_int64),
+        ("dim", ctypes.c_int32),
+        ("points", ctypes.POINTER(ctypes.c_double)),
+        ("kernel", ctypes.c_int32),
+        ("kernel_param", ctypes.c_double),
+        ("admissibility", ctypes.c_int32),
+        ("eta", ctypes.c_double),
+        ("leaf_size", ctypes.c_int32),
+        ("tol", ctypes.c_double),
+        ("max_rank", ctypes.c_int32),
+        ("exact_columns", ctypes.c_int32),
+        ("sample_seed", ctypes.c_uint64),
+        ("threads", ctypes.c_int32),
+    ]
+
+
 class HmatError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {hmat_strerror(status)} (status {status})")
@@ -71,13 +101,22 @@ def library() -> ctypes.CDLL:
         lib.hmat_load.argtypes = [ctypes.POINTER(HmatDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
         lib.hmat_eval.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                   ctypes.c_int, ctypes.c_void_p]
+        lib.hmat_build.argtypes = [ctypes.POINTER(HmatBuildParams), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+        lib.hmat_structure.argtypes = [ctypes.c_void_p, _c_i64p, _c_i32p, _c_i64p, _c_i32p, _c_i64p, _c_i32p]
         lib.hmat_reserve.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        lib.hmat_eval_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_int, ctypes.c_void_p]
+        lib.hmat_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.hmat_phase_times.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), _c_i64p, ctypes.c_int]
+        lib.hmat_measure_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
         lib.hmat_status_poll.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         lib.hmat_info.argtypes = [ctypes.c_void_p, _c_i64p, ctypes.c_int]
         lib.hmat_free.argtypes = [ctypes.c_void_p]
         lib.hmat_strerror.argtypes = [ctypes.c_int]
         lib.hmat_strerror.restype = ctypes.c_char_p
-        for name in ("hmat_load", "hmat_eval", "hmat_reserve", "hmat_status_poll", "hmat_info", "hmat_free"):
+        for name in ("hmat_load", "hmat_build", "hmat_structure", "hmat_eval", "hmat_reserve", "hmat_status_poll",
+                     "hmat_info", "hmat_free", "hmat_eval_host", "hmat_profile", "hmat_phase_times",
+                     "hmat_measure_fp64_peak"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -149,9 +188,68 @@ def hmat_load(n_points: int, levels: int, node_begin, node_size, rank, near_ptr,
     return int(h.value)
 
 
+def hmat_build(points: np.ndarray, kernel: str, kernel_param: float, admissibility: str, leaf_size: int,
+               tol: float, max_rank: int, eta: float = 2.0, exact_columns: int = -1, sample_seed: int = 2,
+               threads: int = 0, flags: int = 0) -> int:
+    """Compress the kernel matrix of `points` (n x d, caller order) and load it; returns the handle."""
+    X = np.ascontiguousarray(points, dtype=np.float64)
+    p = HmatBuildParams(X.shape[0], X.shape[1], X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        _KERNELS[kernel], float(kernel_param), _ADMISSIBILITY[admissibility], float(eta),
+                        int(leaf_size), float(tol), int(max_rank), int(exact_columns), int(sample_seed), int(threads))
+    h = ctypes.c_void_p()
+    _check(library().hmat_build(ctypes.byref(p), int(flags), ctypes.byref(h)), "hmat_build")
+    return int(h.value)
+
+
+def hmat_structure(handle: int) -> dict:
+    """perm, rank and the near/far CSR lists of a loaded HMatrix, as numpy arrays."""
+    info = hmat_info(handle)
+    levels = info["levels"]
+    n_nodes, n_leaves = 2 ** (levels + 1) - 1, 2 ** levels
+    out = dict(perm=np.zeros(info["n_points"], np.int64), rank=np.zeros(n_nodes, np.int32),
+               near_ptr=np.zeros(n_leaves + 1, np.int64), near_idx=np.zeros(info["near_entries"], np.int32),
+               far_ptr=np.zeros(n_nodes + 1, np.int64), far_idx=np.zeros(info["far_entries"], np.int32))
+    args = [out[k].ctypes.data_as(_c_i64p if out[k].dtype == np.int64 else _c_i32p)
+            for k in ("perm", "rank", "near_ptr", "near_idx", "far_ptr", "far_idx")]
+    _check(library().hmat_structure(handle, *args), "hmat_structure")
+    return out
+
+
 def hmat_eval(handle: int, W, Y, q: int, mode: int = HMAT_MODE_FP64, stream=None) -> None:
     """Enqueue Y = K~ W on `stream` (W, Y: n_points x q FP64 device buffers)."""
     _check(library().hmat_eval(handle, _ptr(W), _ptr(Y), int(q), int(mode), _stream(stream)), "hmat_eval")
+
+
+def hmat_eval_host(handle: int, W: np.ndarray, Y: np.ndarray, mode: int = HMAT_MODE_FP64, stream=None) -> None:
+    """Y = K~ W with host arrays (n x q FP64, C-contiguous; pinned memory copies fastest).
+    W and Y may be numpy arrays or CPU torch tensors; synchronises the stream."""
+    if hasattr(W, "data_ptr"):
+        wp, yp, q = int(W.data_ptr()), int(Y.data_ptr()), int(W.shape[1])
+    else:
+        if not (W.flags.c_contiguous and Y.flags.c_contiguous and W.dtype == np.float64 and Y.dtype == np.float64):
+            raise ValueError("W and Y must be C-contiguous float64 arrays")
+        wp, yp, q = W.ctypes.data, Y.ctypes.data, int(W.shape[1])
+    _check(library().hmat_eval_host(handle, wp, yp, q, int(mode), _stream(stream)), "hmat_eval_host")
+
+
+def hmat_profile(handle: int, enable: bool = True) -> None:
+    _check(library().hmat_profile(handle, 1 if enable else 0), "hmat_profile")
+
+
+def hmat_phase_times(handle: int) -> dict:
+    """{phase: (summed ms, launches)} of the evaluations recorded since hmat_profile."""
+    n = len(PHASES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    _check(library().hmat_phase_times(handle, ms, cnt, n), "hmat_phase_times")
+    return {PHASES[k]: (float(ms[k]), int(cnt[k])) for k in range(n)}
+
+
+def hmat_measure_fp64_peak() -> float:
+    """FP64 FMA throughput of the current device in GFLOP/s."""
+    g = ctypes.c_double()
+    _check(library().hmat_measure_fp64_peak(ctypes.byref(g)), "hmat_measure_fp64_peak")
+    return float(g.value)
 
 
 def hmat_reserve(handle: int, q_max: int) -> None:
@@ -185,6 +283,13 @@ class DeviceHMatrix:
     @classmethod
     def load(cls, **desc) -> "DeviceHMatrix":
         return cls(hmat_load(**desc))
+
+    @classmethod
+    def build(cls, points, **params) -> "DeviceHMatrix":
+        return cls(hmat_build(points, **params))
+
+    def structure(self) -> dict:
+        return hmat_structure(self.handle)
 
     @property
     def n_points(self) -> int:

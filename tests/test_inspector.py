@@ -1,0 +1,98 @@
+"""The library's inspector (hmat_build: kd-tree, admissibility, nested ID on the
+host; D and B evaluated on the GPU) against the oracle's compression.
+
+The tree and the near/far lists are index work and must be identical to the
+oracle's; the ranks come from a different pivoted QR and may differ by a pivot
+or two, so the bases are checked by what they must achieve: eps_f against the
+dense product K W (the oracle's unapproximated GEMM) of the same order as the
+oracle's own compression, <= 100 tol with the rank cap lifted, and exact
+(<= 1e-13) with tol = 0 and no cap.
+"""
+import numpy as np
+import pytest
+
+import paper_1812_07152_gb300 as hp
+from oracle import hmatrix as hm
+from tests.fixtures import oracle_case, rhs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _params(w, **ov):
+    p = dict(kernel=w.kernel, kernel_param=w.kernel_param, admissibility=w.admissibility, leaf_size=w.leaf_size,
+             tol=w.tol, max_rank=w.max_rank, eta=w.eta, sample_seed=w.sample_seed)
+    p.update(ov)
+    return p
+
+
+def _eval(h, W):
+    Wd = torch.from_numpy(W).cuda()
+    Yd = torch.empty_like(Wd)
+    hp.hmat_eval(h, Wd, Yd, W.shape[1])
+    assert hp.hmat_status_poll(h) == hp.HMAT_OK
+    return Yd.cpu().numpy()
+
+
+@pytest.mark.parametrize("base,n,ov", [
+    ("hss_uniform3d_n2048", 2048, ()),
+    ("h2_imq3d_n262144", 3000, ()),
+    ("h2_gmm8d_n65536", 4096, ()),
+    ("h2_imq3d_n262144", 4000, (("leaf_size", 40),)),
+])
+def test_structure_identical_and_accuracy_comparable(base, n, ov):
+    w, H, X = oracle_case(base, n, 8, **dict(ov))
+    h = hp.hmat_build(X, **_params(w, **dict(ov)))
+    try:
+        st = hp.hmat_structure(h)
+        near_ptr, near_idx = H.near_csr()
+        far_ptr, far_idx = H.far_csr()
+        assert np.array_equal(st["perm"], H.tree.perm)
+        assert np.array_equal(st["near_ptr"], near_ptr) and np.array_equal(st["near_idx"], near_idx)
+        assert np.array_equal(st["far_ptr"], far_ptr) and np.array_equal(st["far_idx"], far_idx)
+        assert np.array_equal(st["rank"] > 0, H.rank > 0)
+        assert np.abs(st["rank"].astype(int) - H.rank).max() <= 3
+        W = rhs(w.n, 8, 21)
+        KW = hm.dense_product(X, w.kernel, w.kernel_param, W)
+        e_lib = hm.overall_error(_eval(h, W), KW)
+        e_orc = hm.overall_error(hm.evaluate(H, W), KW)
+        assert e_lib <= 3 * e_orc + 1e-12, (e_lib, e_orc)
+    finally:
+        hp.hmat_free(h)
+
+
+@pytest.mark.parametrize("base,n", [("hss_uniform3d_n2048", 2048), ("h2_imq3d_n262144", 4096)])
+def test_error_order_tol_uncapped(base, n):
+    w, _, X = oracle_case(base, n, 8)
+    W = rhs(w.n, 8, 22)
+    KW = hm.dense_product(X, w.kernel, w.kernel_param, W)
+    for tol in (1e-4, 1e-7):
+        h = hp.hmat_build(X, **_params(w, tol=tol, max_rank=10 ** 6))
+        try:
+            assert hm.overall_error(_eval(h, W), KW) <= 100 * tol
+        finally:
+            hp.hmat_free(h)
+
+
+def test_full_rank_hss_is_exact():
+    w, _, X = oracle_case("hss_uniform3d_n2048", 1024, 4)
+    h = hp.hmat_build(X, **_params(w, tol=0.0, max_rank=10 ** 6))
+    try:
+        W = rhs(w.n, 4, 23)
+        KW = hm.dense_product(X, w.kernel, w.kernel_param, W)
+        assert hm.overall_error(_eval(h, W), KW) <= 1e-13
+    finally:
+        hp.hmat_free(h)
+
+
+def test_build_rejects_bad_parameters():
+    X = np.random.default_rng(0).random((100, 3))
+    base = dict(kernel="gaussian", kernel_param=0.5, admissibility="hss", leaf_size=16, tol=1e-6, max_rank=32)
+    for bad in (dict(leaf_size=1), dict(max_rank=0), dict(kernel_param=0.0), dict(tol=-1.0)):
+        with pytest.raises(hp.HmatError) as ei:
+            hp.hmat_build(X, **{**base, **bad})
+        assert ei.value.status == hp.HMAT_EINVAL
+    Xn = X.copy()
+    Xn[3, 1] = np.nan
+    with pytest.raises(hp.HmatError):
+        hp.hmat_build(Xn, **base)
