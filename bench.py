@@ -218,11 +218,12 @@ def run_gpu(args, dist: Dist) -> None:
     e2e_value = dist.world * q / e2e_s
 
     # roofline of the dominant kernel: the FP64 near-field grouped GEMM (bound by the DFMA pipe)
+    # (a phase may be split into one launch per row-tile size: the unit is one evaluation's near field)
     near_ms, near_launches = phases["near"]
-    near_ms_per_launch = near_ms / max(near_launches, 1)
+    near_ms_per_eval = near_ms / args.steps
     near_flops = 2.0 * q * info["near_values"]
     peak_gflops = hp.hmat_measure_fp64_peak()
-    achieved_tflops = near_flops / (near_ms_per_launch / 1e3) / 1e12
+    achieved_tflops = near_flops / (near_ms_per_eval / 1e3) / 1e12
     total_flops = 2.0 * q * (info["near_values"] + 2 * info["basis_values"] + info["coupling_values"])
     bytes_step = 8.0 * (info["near_values"] + info["basis_values"] + info["coupling_values"]) + 2 * 8.0 * w.n * q
     launches = sum(c for _, c in phases.values())
@@ -255,6 +256,7 @@ def run_gpu(args, dist: Dist) -> None:
         "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
         "roofline": {
             "bound": "alu", "kernel": "k_fp64_grouped_gemm (near field)",
+            "launches_per_eval": near_launches // args.steps,
             "achieved": round(achieved_tflops, 4), "peak": round(peak_gflops / 1e3, 4), "unit": "TFLOP/s",
             "frac": round(achieved_tflops / (peak_gflops / 1e3), 4), "traffic": None,
             "peak_source": "FP64 DFMA loop measured in this run (hmat_measure_fp64_peak); nominal 1.25",

@@ -21,7 +21,6 @@ using namespace hmat;
 namespace {
 
 constexpr int64_t kAlignValues = 16;  // every packed block starts on a 128-byte boundary
-constexpr int kTileRows = 64;         // rows per CTA tile of the FP64 kernels
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
@@ -296,25 +295,31 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, hmat_han
   std::vector<GemmEntry> entries;
   std::vector<GemmTile> tiles;
   std::vector<int64_t> tile_cost;
+  // One launch per row-tile size: tasks of at most 16 or 32 rows get smaller tiles so
+  // that the FP64 kernels spend no DFMA on padding rows of small skeleton blocks.
   auto add_phase = [&](PhaseKind kind, int32_t level, MatrixKind x, MatrixKind y,
                        const std::vector<int32_t>& task_ids) {
-    Phase ph{kind, level, x, y, (int64_t)tiles.size(), 0, 0};
-    std::vector<std::pair<int64_t, GemmTile>> list;
-    for (int32_t t : task_ids) {
-      const GemmTask& tk = tasks[t];
-      int64_t kk = 0;
-      for (int32_t e = tk.e_begin; e < tk.e_end; ++e) kk += entries[e].k;
-      ph.max_m = std::max(ph.max_m, tk.m);
-      for (int32_t m0 = 0; m0 < tk.m; m0 += kTileRows) {
-        const int64_t rows = std::min(kTileRows, tk.m - m0);
-        list.push_back({rows * std::max<int64_t>(kk, 1), GemmTile{t, m0}});
+    for (int32_t rows_cls : {64, 32, 16}) {
+      Phase ph{kind, level, x, y, (int64_t)tiles.size(), 0, 0, rows_cls};
+      std::vector<std::pair<int64_t, GemmTile>> list;
+      for (int32_t t : task_ids) {
+        const GemmTask& tk = tasks[t];
+        const int32_t cls = tk.m <= 16 ? 16 : (tk.m <= 32 ? 32 : 64);
+        if (cls != rows_cls) continue;
+        int64_t kk = 0;
+        for (int32_t e = tk.e_begin; e < tk.e_end; ++e) kk += entries[e].k;
+        ph.max_m = std::max(ph.max_m, tk.m);
+        for (int32_t m0 = 0; m0 < tk.m; m0 += rows_cls) {
+          const int64_t rows = std::min(rows_cls, tk.m - m0);
+          list.push_back({rows * std::max<int64_t>(kk, 1), GemmTile{t, m0}});
+        }
       }
+      // longest tiles first, so that the last wave of CTAs is short
+      std::stable_sort(list.begin(), list.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+      for (auto& p : list) tiles.push_back(p.second);
+      ph.n_tiles = (int64_t)tiles.size() - ph.tile_begin;
+      if (ph.n_tiles > 0) h->phases.push_back(ph);
     }
-    // longest tiles first, so that the last wave of CTAs is short
-    std::stable_sort(list.begin(), list.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-    for (auto& p : list) tiles.push_back(p.second);
-    ph.n_tiles = (int64_t)tiles.size() - ph.tile_begin;
-    if (ph.n_tiles > 0) h->phases.push_back(ph);
   };
   auto new_task = [&](int64_t out_row, int64_t m, int accumulate) -> int32_t {
     tasks.push_back(GemmTask{out_row, (int32_t)m, (int32_t)entries.size(), (int32_t)entries.size(), accumulate});

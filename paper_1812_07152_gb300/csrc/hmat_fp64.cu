@@ -16,12 +16,12 @@
 namespace hmat {
 namespace {
 
-constexpr int BM = 64;   // rows per tile (must match the tile list built at load time)
 constexpr int BK = 16;   // depth of one operand chunk
 constexpr int TM = 4;    // outputs per thread: TM rows x TN columns
 constexpr int TN = 4;
 
-template <int BN>
+// BM rows (the phase's tile_rows) x BN right-hand-side columns per CTA.
+template <int BM, int BN>
 struct Cfg {
   static constexpr int kThreads = (BM / TM) * (BN / TN);
   static constexpr int kAPer = BM * BK / kThreads;  // A values loaded per thread per chunk
@@ -30,22 +30,25 @@ struct Cfg {
 
 __device__ __forceinline__ int64_t map_row(const int64_t* __restrict__ m, int64_t r) { return m ? m[r] : r; }
 
-template <int BN>
-__global__ void __launch_bounds__(Cfg<BN>::kThreads)
+// The grid is one-dimensional: CTA b works on tile b / n_col_tiles and column tile
+// b % n_col_tiles, so the column tiles of one output block run side by side and
+// read each block of A from HBM once (the others hit L2).
+template <int BM, int BN>
+__global__ void __launch_bounds__(Cfg<BM, BN>::kThreads)
 k_fp64_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
                     const GemmEntry* __restrict__ entries, const double* __restrict__ arena,
                     const double* X, const int64_t* __restrict__ x_map,
-                    double* Y, const int64_t* __restrict__ y_map, int64_t q) {
-  using C = Cfg<BN>;
+                    double* Y, const int64_t* __restrict__ y_map, int64_t q, int n_col_tiles) {
+  using C = Cfg<BM, BN>;
   constexpr int NT = C::kThreads;
   constexpr int TX = BN / TN;
   __shared__ double As[2][BK][BM + 1];
   __shared__ double Xs[2][BK][BN];
 
-  const GemmTile tile = tiles[blockIdx.x];
+  const GemmTile tile = tiles[blockIdx.x / n_col_tiles];
   const GemmTask task = tasks[tile.task];
   const int m0 = tile.m0;
-  const int64_t q0 = (int64_t)blockIdx.y * BN;
+  const int64_t q0 = (int64_t)(blockIdx.x % n_col_tiles) * BN;
   const int tid = threadIdx.x;
   const int ty = tid / TX, tx = tid % TX;
 
@@ -141,13 +144,23 @@ k_fp64_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restri
   }
 }
 
-template <int BN>
+template <int BM, int BN>
 cudaError_t launch(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map, double* Y,
                    const int64_t* y_map, int64_t q, cudaStream_t s) {
-  const dim3 grid((unsigned)ph.n_tiles, (unsigned)((q + BN - 1) / BN));
-  k_fp64_grouped_gemm<BN><<<grid, Cfg<BN>::kThreads, 0, s>>>(h.tiles + ph.tile_begin, h.tasks, h.entries,
-                                                             h.arena, X, x_map, Y, y_map, q);
+  const int64_t n_col = (q + BN - 1) / BN;
+  const int64_t blocks = ph.n_tiles * n_col;
+  if (blocks > 2147483647LL) return cudaErrorInvalidValue;
+  k_fp64_grouped_gemm<BM, BN><<<(unsigned)blocks, Cfg<BM, BN>::kThreads, 0, s>>>(
+      h.tiles + ph.tile_begin, h.tasks, h.entries, h.arena, X, x_map, Y, y_map, q, (int)n_col);
   return cudaGetLastError();
+}
+
+template <int BM>
+cudaError_t launch_bn(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map, double* Y,
+                      const int64_t* y_map, int64_t q, cudaStream_t s) {
+  if (q <= 16) return launch<BM, 16>(h, ph, X, x_map, Y, y_map, q, s);
+  if (q <= 32) return launch<BM, 32>(h, ph, X, x_map, Y, y_map, q, s);
+  return launch<BM, 64>(h, ph, X, x_map, Y, y_map, q, s);
 }
 
 }  // namespace
@@ -155,10 +168,12 @@ cudaError_t launch(const Handle& h, const Phase& ph, const double* X, const int6
 cudaError_t launch_fp64_phase(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map,
                               double* Y, const int64_t* y_map, int64_t q, cudaStream_t stream) {
   if (ph.n_tiles == 0 || q == 0) return cudaSuccess;
-  if ((q + 15) / 16 > 65535) return cudaErrorInvalidValue;
-  if (q <= 16) return launch<16>(h, ph, X, x_map, Y, y_map, q, stream);
-  if (q <= 32) return launch<32>(h, ph, X, x_map, Y, y_map, q, stream);
-  return launch<64>(h, ph, X, x_map, Y, y_map, q, stream);
+  if (q > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+  switch (ph.tile_rows) {
+    case 16: return launch_bn<16>(h, ph, X, x_map, Y, y_map, q, stream);
+    case 32: return launch_bn<32>(h, ph, X, x_map, Y, y_map, q, stream);
+    default: return launch_bn<64>(h, ph, X, x_map, Y, y_map, q, stream);
+  }
 }
 
 }  // namespace hmat

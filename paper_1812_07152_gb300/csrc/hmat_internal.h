@@ -33,7 +33,7 @@ struct GemmEntry {
   int32_t pad;
 };
 
-// A CTA's share of a task: output rows [m0, m0 + BM) of task `task`.
+// A CTA's share of a task: output rows [m0, m0 + tile_rows) of task `task`.
 struct GemmTile {
   int32_t task;
   int32_t m0;
@@ -59,7 +59,8 @@ struct Phase {
   MatrixKind y;
   int64_t tile_begin;  // into the tile array (one array for all phases)
   int64_t n_tiles;
-  int32_t max_m;       // largest task height of the phase
+  int32_t max_m;       // largest task height of the launch
+  int32_t tile_rows;   // rows per CTA tile of this launch (16, 32 or 64)
 };
 
 struct Handle {
