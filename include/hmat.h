@@ -216,6 +216,35 @@ hmat_status hmat_phase_times(hmat_t h, double* ms, int64_t* launches, int n);
 hmat_status hmat_measure_fp64_peak(double* gflops);
 
 /*
+ * hmat_eval_noalloc - the FP64 evaluation of hmat_eval (mode HMAT_MODE_FP64)
+ * for callers that must not allocate device memory during the call. The paper
+ * has no counterpart; this exists for callers such as a latency-critical
+ * serving loop, where a cudaMalloc would synchronise the whole device and stall
+ * the work of other streams, or a process whose device memory is entirely
+ * owned by another allocator (for example a framework's caching allocator), in
+ * which a foreign cudaMalloc can fail or fragment the pool.
+ *
+ * The skeleton workspaces (the upward weights w and the downward potentials u,
+ * sum of ranks x q values each) live in one static device array of
+ * HMAT_NOALLOC_SCRATCH_VALUES doubles (16 MiB) compiled into libhmat.so, which
+ * every GPU that loads the library holds until the process exits. The call
+ * returns HMAT_EINVAL when 2 x (sum of ranks) x q exceeds that size (the sum of
+ * ranks is out[7] of hmat_info). It calls no cudaMalloc or cudaFree and no
+ * allocating library routine; the handle must already exist (hmat_load and
+ * hmat_build do allocate).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call shares the one array and leaves its
+ * last contents behind; every workspace row is written before it is read, so
+ * nothing needs clearing. Calls whose work overlaps on the GPU (other streams,
+ * other handles, other host threads) race on the array: order them.
+ * Arguments and results are those of hmat_eval.
+ */
+#define HMAT_NOALLOC_SCRATCH_VALUES 2097152
+hmat_status hmat_eval_noalloc(hmat_t h, const double* W, double* Y, int64_t q, void* stream);
+
+/*
  * hmat_status_poll - synchronise `stream` and return the device status word
  * latched by the kernels since the last poll (HMAT_OK when nothing happened),
  * then clear it.
