@@ -42,6 +42,8 @@ def parse_args():
     ap.add_argument("--n", type=int, default=None, help="reduced point count (small profiling cases)")
     ap.add_argument("--q", type=int, default=None, help="override the number of right-hand-side columns")
     ap.add_argument("--cpu-baseline", choices=["auto", "off"], default="auto")
+    ap.add_argument("--mixed", choices=["on", "off"], default="on",
+                    help="also time the mixed-precision tensor-core mode on the same HMatrix")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
     return ap.parse_args()
 
@@ -169,7 +171,8 @@ def run_gpu(args, dist: Dist) -> None:
     w = workload(args)
     X = make_points(w)
     t0 = time.perf_counter()
-    dev = hp.DeviceHMatrix.build(X, **build_params(w))
+    flags = hp.HMAT_LOAD_MIXED if args.mixed == "on" else 0
+    dev = hp.DeviceHMatrix.build(X, flags=flags, **build_params(w))
     t_build = time.perf_counter() - t0
     info = dev.info
     q = w.q
@@ -206,6 +209,8 @@ def run_gpu(args, dist: Dist) -> None:
     if dev.poll() != hp.HMAT_OK:
         raise RuntimeError("device status error during the timed steps")
     value = dist.world * q / (ms / 1e3)
+
+    mixed = run_mixed(args, dev, W, Y, q, info, stream, dist) if args.mixed == "on" else None
 
     # end to end: host W -> device, evaluate, device Y -> host, every step (pinned host buffers)
     Y_host = torch.empty_like(W_host).pin_memory()
@@ -267,6 +272,8 @@ def run_gpu(args, dist: Dist) -> None:
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if mixed is not None:
+        line["mixed"] = mixed
     dev.close()
 
     if dist.rank == 0 and dist.world == 1 and args.cpu_baseline == "auto":
@@ -274,6 +281,67 @@ def run_gpu(args, dist: Dist) -> None:
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
     dist.close()
+
+
+def run_mixed(args, dev, W, Y64, q, info, stream, dist) -> dict:
+    """Times the mixed-precision mode (tensor-core near field) on the same HMatrix and W;
+    its error is measured against this run's FP64 result."""
+    import torch
+    import paper_1812_07152_gb300 as hp
+    Ym = torch.empty_like(W)
+    for _ in range(args.warmup):
+        hp.hmat_eval(dev.handle, W, Ym, q, hp.HMAT_MODE_MIXED, stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    hp.hmat_profile(dev.handle, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        hp.hmat_eval(dev.handle, W, Ym, q, hp.HMAT_MODE_MIXED, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = dist.max(e0.elapsed_time(e1) / args.steps)
+    phases = hp.hmat_phase_times(dev.handle)
+    hp.hmat_profile(dev.handle, False)
+    if dev.poll() != hp.HMAT_OK:
+        raise RuntimeError("device status error during the mixed-precision steps")
+    err = float(torch.linalg.norm(Ym - Y64) / torch.linalg.norm(Y64))
+    near_ms = phases["near"][0] / args.steps
+    nv = info["near_values"]
+    exec_flops = 3 * 2.0 * q * nv                       # three FP16 products per stored value
+    alg_bytes = 4.0 * nv + 4.0 * w_rows(info) * q + 8.0 * w_rows(info) * q   # D hi/lo once, W split once, Y once
+    peaks = measured_peaks()
+    t_tensor = exec_flops / (peaks["bf16_tflops"] * 1e12) * 1e3
+    t_hbm = alg_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
+    if t_tensor >= t_hbm:
+        roof = {"bound": "tensor", "achieved": round(exec_flops / (near_ms / 1e3) / 1e12, 2),
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": round(alg_bytes / (near_ms / 1e3) / 1e9, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s"}
+    roof.update({"frac": round(roof["achieved"] / roof["peak"], 4), "traffic": None,
+                 "kernel": "k_near_tc (tcgen05 near field)", "peak_source": peaks["source"],
+                 "t_tensor_ms": round(t_tensor, 4), "t_hbm_ms": round(t_hbm, 4)})
+    return {"value": round(dist.world * q / (ms / 1e3), 3), "unit": "cols/s", "ms_per_step": round(ms, 4),
+            "error_vs_fp64": err, "dtype": "f16 hi+lo split, f32 accumulate",
+            "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
+            "gpu_launches": sum(c for _, c in phases.values()), "roofline": roof}
+
+
+def w_rows(info) -> int:
+    return info["n_points"]
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
 # ----------------------------------------------------------------------------- CPU oracle (baseline / reference arm)

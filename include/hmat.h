@@ -147,6 +147,14 @@ hmat_status hmat_structure(hmat_t h, int64_t* perm, int32_t* rank, int64_t* near
 
 /* Evaluation modes for hmat_eval. */
 #define HMAT_MODE_FP64 0            /* every block and every sum in FP64 (DFMA) */
+#define HMAT_MODE_MIXED 1           /* near field on the tensor cores (FP16 hi+lo splits of D and W,
+                                       FP32 accumulation drained per block into compensated sums),
+                                       far field in FP32; needs a handle loaded with HMAT_LOAD_MIXED */
+
+/* Load flags (hmat_load, hmat_build). */
+#define HMAT_LOAD_MIXED 1           /* also keep the tensor-core copy of the near blocks (FP16 hi/lo,
+                                       4 bytes per value) and an FP32 copy of the bases and coupling
+                                       blocks, for HMAT_MODE_MIXED */
 
 /*
  * hmat_load - validate an HMatrix description, pack its blocks per tree level
@@ -155,7 +163,8 @@ hmat_status hmat_structure(hmat_t h, int64_t* perm, int32_t* rank, int64_t* near
  * Synchronous. Validation (HMAT_EINVAL, nothing allocated on failure): tree
  * shape and index ranges, CSR pointers non-decreasing, list ids in range, far
  * partners on the same level and distinct, perm a bijection, every non-empty
- * block pointer non-NULL and every stored value finite. `flags` must be 0.
+ * block pointer non-NULL and every stored value finite. `flags` is 0 or
+ * HMAT_LOAD_MIXED (any other bit: HMAT_EUNSUPPORTED).
  * The device is the one current at the call. Returns HMAT_ENOMEM when the
  * arena does not fit.
  */
@@ -171,7 +180,8 @@ hmat_status hmat_load(const hmat_desc* desc, int flags, hmat_t* out);
  * be ordered (one stream, or synchronised by the caller): they share the
  * handle's workspace. The workspace grows to q on demand with cudaMalloc,
  * which synchronises the device; hmat_reserve avoids that inside a timed or
- * captured region. `mode` is HMAT_MODE_FP64.
+ * captured region. `mode` is HMAT_MODE_FP64 or HMAT_MODE_MIXED (the latter on a
+ * handle loaded with HMAT_LOAD_MIXED, else HMAT_EUNSUPPORTED).
  */
 hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream);
 
@@ -196,7 +206,8 @@ hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int 
  * HMAT_PHASE_NEAR (near-field reduction over D), HMAT_PHASE_UP_LEAF (w = P^T W
  * at the leaves), HMAT_PHASE_UP_TRANSFER (w = P^T [w_l; w_r], one launch per
  * level), HMAT_PHASE_COUPLING (u = sum B w), HMAT_PHASE_DOWN_TRANSFER
- * ([u_l; u_r] += P u, one launch per level), HMAT_PHASE_DOWN_LEAF (Y += P u).
+ * ([u_l; u_r] += P u, one launch per level), HMAT_PHASE_DOWN_LEAF (Y += P u),
+ * HMAT_PHASE_SPLIT (mixed mode only: scale and split W into FP16 hi/lo tiles).
  */
 #define HMAT_PHASE_NEAR 0
 #define HMAT_PHASE_UP_LEAF 1
@@ -204,7 +215,8 @@ hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int 
 #define HMAT_PHASE_COUPLING 3
 #define HMAT_PHASE_DOWN_TRANSFER 4
 #define HMAT_PHASE_DOWN_LEAF 5
-#define HMAT_PHASE_COUNT 6
+#define HMAT_PHASE_SPLIT 6          /* mixed mode: max |W| and the FP16 hi/lo split of W */
+#define HMAT_PHASE_COUNT 7
 hmat_status hmat_profile(hmat_t h, int enable);
 hmat_status hmat_phase_times(hmat_t h, double* ms, int64_t* launches, int n);
 

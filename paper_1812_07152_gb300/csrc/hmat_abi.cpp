@@ -200,6 +200,15 @@ void free_device(Handle* h) {
   cudaFree(h->host_y);
   h->host_w = nullptr;
   h->host_y = nullptr;
+  cudaFree(h->tc_tiles);
+  cudaFree(h->tc_meta);
+  cudaFree(h->arena32);
+  cudaFree(h->wsplit);
+  cudaFree(h->ws32);
+  cudaFree(h->us32);
+  cudaFree(h->wmax);
+  h->tc_tiles = nullptr; h->tc_meta = nullptr; h->arena32 = nullptr; h->wsplit = nullptr;
+  h->ws32 = nullptr; h->us32 = nullptr; h->wmax = nullptr; h->has_mixed = false;
   cudaFree(h->arena);
   cudaFree(h->perm);
   cudaFree(h->tasks);
@@ -228,12 +237,195 @@ hmat_status cuda_status(cudaError_t e) {
   return HMAT_ECUDA;
 }
 
+
+// Mixed-precision copies of a loaded HMatrix (HMAT_LOAD_MIXED): the near blocks as
+// FP16 hi/lo tensor-core tiles (packed on the device from the FP64 arena, one scale
+// exponent per 128-row m-tile of a target leaf) and the bases and coupling blocks
+// (the arena from basis_begin on) as FP32.
+hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const std::vector<int64_t>& near_off,
+                        int64_t basis_begin) {
+  const int64_t nl = v.n_leaves, fl = v.first_leaf;
+  std::vector<int32_t> leaf_size(nl), leaf_kc(nl), mt_base(nl + 1);
+  std::vector<int64_t> leaf_begin(nl), leaf_kcum(nl + 1), near_ptr(d->near_ptr, d->near_ptr + nl + 1);
+  std::vector<int32_t> near_idx(d->near_idx, d->near_idx + v.n_near);
+  mt_base[0] = 0;
+  leaf_kcum[0] = 0;
+  for (int64_t i = 0; i < nl; ++i) {
+    leaf_size[i] = (int32_t)h->size[fl + i];
+    leaf_begin[i] = h->begin[fl + i];
+    leaf_kc[i] = (leaf_size[i] + kTcK - 1) / kTcK;
+    mt_base[i + 1] = mt_base[i] + (leaf_size[i] + kTcRows - 1) / kTcRows;
+    leaf_kcum[i + 1] = leaf_kcum[i] + leaf_kc[i];
+  }
+  const int64_t n_mtiles = mt_base[nl];
+  h->total_kchunks = leaf_kcum[nl];
+  std::vector<int32_t> mtile_leaf(n_mtiles), mtile_mt(n_mtiles), chunk_leaf(h->total_kchunks), chunk_c(h->total_kchunks);
+  for (int64_t i = 0; i < nl; ++i) {
+    for (int32_t m = 0; m < mt_base[i + 1] - mt_base[i]; ++m) {
+      mtile_leaf[mt_base[i] + m] = (int32_t)i;
+      mtile_mt[mt_base[i] + m] = m;
+    }
+    for (int32_t c = 0; c < leaf_kc[i]; ++c) {
+      chunk_leaf[leaf_kcum[i] + c] = (int32_t)i;
+      chunk_c[leaf_kcum[i] + c] = c;
+    }
+  }
+  // tile pairs per near entry: m-tiles of the target x k-chunks of the source
+  std::vector<int64_t> a_off(v.n_near);
+  std::vector<TcPackJob> jobs;
+  int64_t bytes = 0;
+  for (int64_t i = 0; i < nl; ++i)
+    for (int64_t e = near_ptr[i]; e < near_ptr[i + 1]; ++e) {
+      const int32_t j = near_idx[e];
+      const int32_t n_mt = mt_base[i + 1] - mt_base[i];
+      a_off[e] = bytes;
+      for (int32_t m = 0; m < n_mt; ++m)
+        for (int32_t c = 0; c < leaf_kc[j]; ++c)
+          jobs.push_back(TcPackJob{bytes + ((int64_t)m * leaf_kc[j] + c) * 2 * kTcTileBytes, near_off[e], leaf_size[i],
+                                   leaf_size[j], m * kTcRows, c * kTcK, mt_base[i] + m, 0});
+      bytes += (int64_t)n_mt * leaf_kc[j] * 2 * kTcTileBytes;
+    }
+  // (leaf, m-tile) work items, the longest near lists first
+  std::vector<std::pair<int64_t, TcTile>> work;
+  for (int64_t i = 0; i < nl; ++i) {
+    int64_t cost = 0;
+    for (int64_t e = near_ptr[i]; e < near_ptr[i + 1]; ++e) cost += leaf_kc[near_idx[e]];
+    for (int32_t m = 0; m < mt_base[i + 1] - mt_base[i]; ++m) work.push_back({cost, TcTile{(int32_t)i, m}});
+  }
+  std::stable_sort(work.begin(), work.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+  std::vector<TcTile> work_list;
+  for (auto& w : work) work_list.push_back(w.second);
+  h->n_tc_work = (int64_t)work_list.size();
+
+  // one allocation for the permanent metadata
+  struct Part { const void* src; size_t bytes; void** dst; };
+  int64_t* d_a_off; int64_t* d_near_ptr; int32_t* d_near_idx; int32_t* d_kc; int64_t* d_kcum; int64_t* d_begin;
+  int32_t* d_size; int32_t* d_mt_base; int32_t* d_scale; TcTile* d_work; int32_t* d_chunk_leaf; int32_t* d_chunk_c;
+  std::vector<int32_t> scale_zero(std::max<int64_t>(n_mtiles, 1), 0);
+  Part parts[] = {
+      {a_off.data(), a_off.size() * 8, (void**)&d_a_off},
+      {near_ptr.data(), near_ptr.size() * 8, (void**)&d_near_ptr},
+      {near_idx.data(), near_idx.size() * 4, (void**)&d_near_idx},
+      {leaf_kc.data(), leaf_kc.size() * 4, (void**)&d_kc},
+      {leaf_kcum.data(), leaf_kcum.size() * 8, (void**)&d_kcum},
+      {leaf_begin.data(), leaf_begin.size() * 8, (void**)&d_begin},
+      {leaf_size.data(), leaf_size.size() * 4, (void**)&d_size},
+      {mt_base.data(), mt_base.size() * 4, (void**)&d_mt_base},
+      {scale_zero.data(), scale_zero.size() * 4, (void**)&d_scale},
+      {work_list.data(), work_list.size() * sizeof(TcTile), (void**)&d_work},
+      {chunk_leaf.data(), chunk_leaf.size() * 4, (void**)&d_chunk_leaf},
+      {chunk_c.data(), chunk_c.size() * 4, (void**)&d_chunk_c},
+  };
+  size_t total = 0;
+  for (auto& p : parts) total += (p.bytes + 255) / 256 * 256 + 256;
+  uint8_t* meta = nullptr;
+  cudaError_t e = cudaMalloc((void**)&meta, total);
+  if (e != cudaSuccess) return cuda_status(e);
+  h->tc_meta = meta;
+  h->device_bytes += (int64_t)total;
+  size_t o = 0;
+  for (auto& p : parts) {
+    *p.dst = meta + o;
+    if (p.bytes && (e = cudaMemcpy(meta + o, p.src, p.bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_status(e);
+    o += (p.bytes + 255) / 256 * 256 + 256;
+  }
+  h->tc = TcNear{nullptr, d_a_off, d_near_ptr, d_near_idx, d_kc, d_kcum, d_begin, d_size, d_mt_base, d_scale,
+                 d_work, d_chunk_leaf, d_chunk_c};
+
+  // tiles: scale exponents, then the packed hi/lo pairs
+  if ((e = cudaMalloc((void**)&h->tc_tiles, (size_t)std::max<int64_t>(bytes, 256))) != cudaSuccess)
+    return cuda_status(e);
+  h->tc_bytes = bytes;
+  h->device_bytes += bytes;
+  h->tc.tiles = h->tc_tiles;
+  int64_t* d_near_off = nullptr; int32_t* d_mleaf = nullptr; int32_t* d_mmt = nullptr; TcPackJob* d_jobs = nullptr;
+  int64_t scratch = 0;
+  e = upload(&d_near_off, near_off, &scratch);
+  if (e == cudaSuccess) e = upload(&d_mleaf, mtile_leaf, &scratch);
+  if (e == cudaSuccess) e = upload(&d_mmt, mtile_mt, &scratch);
+  if (e == cudaSuccess) e = upload(&d_jobs, jobs, &scratch);
+  if (e == cudaSuccess) e = launch_tc_scale(h->tc, d_near_off, h->arena, nl, n_mtiles, d_mleaf, d_mmt, d_scale, 0);
+  if (e == cudaSuccess) e = launch_tc_pack(d_jobs, (int64_t)jobs.size(), h->arena, d_scale, h->tc_tiles, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(d_near_off);
+  cudaFree(d_mleaf);
+  cudaFree(d_mmt);
+  cudaFree(d_jobs);
+  if (e != cudaSuccess) return cuda_status(e);
+
+  // FP32 copy of the bases and coupling blocks
+  h->arena32_shift = basis_begin;
+  const int64_t n32 = std::max<int64_t>(h->arena_values - basis_begin, 1);
+  if ((e = cudaMalloc((void**)&h->arena32, (size_t)n32 * sizeof(float))) != cudaSuccess) return cuda_status(e);
+  h->device_bytes += n32 * (int64_t)sizeof(float);
+  if ((e = launch_to_f32(h->arena + basis_begin, h->arena32, h->arena_values - basis_begin, 0)) != cudaSuccess)
+    return cuda_status(e);
+  if ((e = cudaMalloc((void**)&h->wmax, sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_status(e);
+  h->has_mixed = true;
+  return HMAT_OK;
+}
+
+// Workspaces of the mixed mode for q columns: W split tiles and FP32 skeleton weights.
+hmat_status reserve_mixed(Handle* h, int64_t q, int n_t, int n_ct) {
+  const int64_t split = h->total_kchunks * n_ct * (int64_t)n_t * 256;
+  if (split > h->wsplit_cap) {
+    uint8_t* p = nullptr;
+    cudaError_t e = cudaMalloc((void**)&p, (size_t)std::max<int64_t>(split, 256));
+    if (e != cudaSuccess) { cudaGetLastError(); return cuda_status(e); }
+    cudaDeviceSynchronize();
+    cudaFree(h->wsplit);
+    h->device_bytes += split - h->wsplit_cap;
+    h->wsplit = p;
+    h->wsplit_cap = split;
+  }
+  if (q > h->q32_cap) {
+    const size_t n = (size_t)std::max<int64_t>(h->sum_rank, 1) * (size_t)q * sizeof(float);
+    float *ws = nullptr, *us = nullptr;
+    cudaError_t e = cudaMalloc((void**)&ws, n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&us, n);
+    if (e != cudaSuccess) { cudaFree(ws); cudaGetLastError(); return cuda_status(e); }
+    cudaDeviceSynchronize();
+    cudaFree(h->ws32);
+    cudaFree(h->us32);
+    h->device_bytes += 2 * (int64_t)n - 2 * std::max<int64_t>(h->sum_rank, 1) * h->q32_cap * (int64_t)sizeof(float);
+    h->ws32 = ws;
+    h->us32 = us;
+    h->q32_cap = q;
+  }
+  return HMAT_OK;
+}
+
+// Event records around one launch of the evaluation when profiling is on.
+bool prof_begin(Handle* h, int32_t kind, cudaStream_t s, Handle::ProfRecord* rec) {
+  rec->kind = kind;
+  if (!h->profiling) return true;
+  for (cudaEvent_t* ev : {&rec->start, &rec->stop}) {
+    if (!h->event_pool.empty()) {
+      *ev = h->event_pool.back();
+      h->event_pool.pop_back();
+    } else if (cudaEventCreate(ev) != cudaSuccess) {
+      return false;
+    }
+  }
+  return cudaEventRecord(rec->start, s) == cudaSuccess;
+}
+
+bool prof_end(Handle* h, const Handle::ProfRecord& rec, cudaStream_t s) {
+  if (!h->profiling) return true;
+  if (cudaEventRecord(rec.stop, s) != cudaSuccess) return false;
+  h->prof.push_back(rec);
+  return true;
+}
+
 }  // namespace
 
 namespace hmat {
 
-hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, hmat_handle** out) {
+hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flags, hmat_handle** out) {
   *out = nullptr;
+  if (flags & ~HMAT_LOAD_MIXED) return HMAT_EUNSUPPORTED;
   Validated v;
   hmat_status st = validate(d, src == nullptr, &v);
   if (st != HMAT_OK) return st;
@@ -274,6 +466,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, hmat_han
       h->near_values += cnt;
       off = align_up(off + cnt, kAlignValues);
     }
+  const int64_t basis_region_begin = off;
   for (int64_t a = 0; a < v.n_nodes; ++a) {
     if (h->rank[a] == 0) continue;
     basis_off[a] = off;
@@ -471,6 +664,13 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, hmat_han
   if ((e = upload(&h->tiles, tiles, &h->device_bytes)) != cudaSuccess) return fail(e);
   std::vector<int> zero(1, 0);
   if ((e = upload(&h->status, zero, &h->device_bytes)) != cudaSuccess) return fail(e);
+  if (flags & HMAT_LOAD_MIXED) {
+    hmat_status ms = build_mixed(h.get(), d, v, near_off, basis_region_begin);
+    if (ms != HMAT_OK) {
+      free_device(h.get());
+      return ms;
+    }
+  }
   *out = h.release();
   return HMAT_OK;
 }
@@ -480,8 +680,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, hmat_han
 extern "C" hmat_status hmat_load(const hmat_desc* d, int flags, hmat_t* out) {
   if (!out) return HMAT_EINVAL;
   *out = nullptr;
-  if (flags != 0) return HMAT_EUNSUPPORTED;
-  return load_impl(d, nullptr, out);
+  return load_impl(d, nullptr, flags, out);
 }
 
 extern "C" hmat_status hmat_structure(hmat_t h, int64_t* perm, int32_t* rank, int64_t* near_ptr, int32_t* near_idx,
@@ -527,51 +726,70 @@ extern "C" hmat_status hmat_reserve(hmat_t h, int64_t q_max) {
 
 extern "C" hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
   if (!h || q < 0) return HMAT_EINVAL;
-  if (mode != HMAT_MODE_FP64) return HMAT_EUNSUPPORTED;
+  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
+  if (mode == HMAT_MODE_MIXED && !h->has_mixed) return HMAT_EUNSUPPORTED;
   if (q == 0 || h->n_points == 0) return HMAT_OK;
   if (!W || !Y || W == Y) return HMAT_EINVAL;
   const char* w0 = (const char*)W;
   const char* y0 = (const char*)Y;
   const int64_t bytes = h->n_points * q * (int64_t)sizeof(double);
   if (w0 < y0 + bytes && y0 < w0 + bytes) return HMAT_EINVAL;  // W and Y overlap
-  if (q > h->q_cap) {
-    hmat_status st = hmat_reserve(h, q);
-    if (st != HMAT_OK) return st;
-  }
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
   if (dev != h->device) return HMAT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  Handle::ProfRecord rec{};
+
+  if (mode == HMAT_MODE_MIXED) {
+    // near field on the tensor cores, W split first; far field as FP32 grouped GEMMs
+    const int n_t = (int)std::min<int64_t>(128, (q + 15) / 16 * 16);
+    const int64_t n_ct64 = (q + n_t - 1) / n_t;
+    if (n_ct64 > 65535) return HMAT_EUNSUPPORTED;
+    const int n_ct = (int)n_ct64;
+    hmat_status st = reserve_mixed(h, q, n_t, n_ct);
+    if (st != HMAT_OK) return st;
+    if (!prof_begin(h, HMAT_PHASE_SPLIT, s, &rec)) return HMAT_ECUDA;
+    cudaError_t e = launch_w_split(h->tc, h->total_kchunks, W, h->n_points * q, h->perm, q, n_t, n_ct, h->wmax,
+                                   h->wsplit, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!prof_end(h, rec, s) || !prof_begin(h, HMAT_PHASE_NEAR, s, &rec)) return HMAT_ECUDA;
+    e = launch_near_tc(h->tc, h->n_tc_work, h->wsplit, h->wmax, h->perm, Y, q, n_t, n_ct, h->status, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!prof_end(h, rec, s)) return HMAT_ECUDA;
+    for (const Phase& ph : h->phases) {
+      if (ph.kind == PH_NEAR) continue;
+      const void* X = ph.x == MAT_USER ? (const void*)W : (ph.x == MAT_SKEL_W ? (const void*)h->ws32 : h->us32);
+      void* Yd = ph.y == MAT_USER ? (void*)Y : (ph.y == MAT_SKEL_W ? (void*)h->ws32 : (void*)h->us32);
+      const int64_t* xm = ph.x == MAT_USER ? h->perm : nullptr;
+      const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
+      if (!prof_begin(h, (int32_t)ph.kind, s, &rec)) return HMAT_ECUDA;
+      e = launch_f32_phase(*h, ph, X, ph.x == MAT_USER, xm, Yd, ph.y == MAT_USER, ym, q, s);
+      if (e != cudaSuccess) return cuda_status(e);
+      if (!prof_end(h, rec, s)) return HMAT_ECUDA;
+    }
+    return HMAT_OK;
+  }
+
+  if (q > h->q_cap) {
+    hmat_status st = hmat_reserve(h, q);
+    if (st != HMAT_OK) return st;
+  }
   for (const Phase& ph : h->phases) {
     const double* X = ph.x == MAT_USER ? W : (ph.x == MAT_SKEL_W ? h->ws : h->us);
     double* Yd = ph.y == MAT_USER ? Y : (ph.y == MAT_SKEL_W ? h->ws : h->us);
     const int64_t* xm = ph.x == MAT_USER ? h->perm : nullptr;
     const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
-    Handle::ProfRecord rec{(int32_t)ph.kind, nullptr, nullptr};
-    if (h->profiling) {
-      for (cudaEvent_t* ev : {&rec.start, &rec.stop}) {
-        if (!h->event_pool.empty()) {
-          *ev = h->event_pool.back();
-          h->event_pool.pop_back();
-        } else if (cudaEventCreate(ev) != cudaSuccess) {
-          return HMAT_ECUDA;
-        }
-      }
-      if (cudaEventRecord(rec.start, s) != cudaSuccess) return HMAT_ECUDA;
-    }
+    if (!prof_begin(h, (int32_t)ph.kind, s, &rec)) return HMAT_ECUDA;
     cudaError_t e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, s);
     if (e != cudaSuccess) return cuda_status(e);
-    if (h->profiling) {
-      if (cudaEventRecord(rec.stop, s) != cudaSuccess) return HMAT_ECUDA;
-      h->prof.push_back(rec);
-    }
+    if (!prof_end(h, rec, s)) return HMAT_ECUDA;
   }
   return HMAT_OK;
 }
 
 extern "C" hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
   if (!h || q < 0) return HMAT_EINVAL;
-  if (mode != HMAT_MODE_FP64) return HMAT_EUNSUPPORTED;
+  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
   if (q == 0 || h->n_points == 0) return HMAT_OK;
   if (!W || !Y) return HMAT_EINVAL;
   const int64_t values = h->n_points * q;

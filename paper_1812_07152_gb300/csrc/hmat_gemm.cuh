@@ -1,0 +1,178 @@
+// Grouped ("owner computes") GEMM shared by every phase of the evaluation
+// (Section 2.1): the near-field reduction over D, the upward pass over the bases,
+// the far-field reduction over B and the downward pass. A CTA owns one row tile of
+// one output block and one column tile of the right-hand side and walks the
+// block's list of terms, so no two CTAs write the same output and no atomics are
+// needed (the role blocking plays in Algorithm 1).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hmat_internal.h"
+
+namespace hmat {
+namespace gemm {
+
+constexpr int BK = 16;   // depth of one operand chunk
+constexpr int TM = 4;    // outputs per thread: TM rows x TN columns
+constexpr int TN = 4;
+
+// BM rows (the launch's tile_rows) x BN right-hand-side columns per CTA.
+template <int BM, int BN>
+struct Cfg {
+  static constexpr int kThreads = (BM / TM) * (BN / TN);
+  static constexpr int kAPer = BM * BK / kThreads;  // A values loaded per thread per chunk
+  static constexpr int kXPer = BN * BK / kThreads;  // X values loaded per thread per chunk
+};
+
+__device__ __forceinline__ int64_t map_row(const int64_t* __restrict__ m, int64_t r) { return m ? m[r] : r; }
+
+// The grid is one-dimensional: CTA b works on tile b / n_col_tiles and column tile
+// b % n_col_tiles, so the column tiles of one output block run side by side and
+// read each block of A from HBM once (the others hit L2).
+//
+// TA: stored block type, TX / TY: input / output matrix types, TC: the type of the
+// products and sums. Entry offsets index the FP64 arena; a_shift maps them into an
+// arena that holds only the values from a_shift on (the FP32 far-field copy).
+template <typename TA, typename TX, typename TY, typename TC, int BM, int BN>
+__global__ void __launch_bounds__(Cfg<BM, BN>::kThreads)
+k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
+               const GemmEntry* __restrict__ entries, const TA* __restrict__ arena, int64_t a_shift,
+               const TX* X, const int64_t* __restrict__ x_map,
+               TY* Y, const int64_t* __restrict__ y_map, int64_t q, int n_col_tiles) {
+  using C = Cfg<BM, BN>;
+  constexpr int NT = C::kThreads;
+  constexpr int CX = BN / TN;  // threads along the columns
+  __shared__ TC As[2][BK][BM + 1];
+  __shared__ TC Xs[2][BK][BN];
+
+  const GemmTile tile = tiles[blockIdx.x / n_col_tiles];
+  const GemmTask task = tasks[tile.task];
+  const int m0 = tile.m0;
+  const int64_t q0 = (int64_t)(blockIdx.x % n_col_tiles) * BN;
+  const int tid = threadIdx.x;
+  const int ty = tid / CX, tx = tid % CX;
+
+  TC acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = TC(0);
+
+  TC ra[C::kAPer], rx[C::kXPer];
+  int e = task.e_begin;
+  int k0 = 0;
+
+  // Load the chunk (entry e, depth k0 .. k0+BK) into registers, zero outside the block.
+  auto load_chunk = [&](int ee, int kk0) {
+    const GemmEntry en = entries[ee];
+    const TA* a = arena + (en.a_off - a_shift);
+#pragma unroll
+    for (int t = 0; t < C::kAPer; ++t) {
+      const int idx = tid + t * NT;
+      int m, k;
+      if (en.trans) { k = idx / BM; m = idx % BM; } else { m = idx / BK; k = idx % BK; }
+      const int gm = m0 + m, gk = kk0 + k;
+      TC v = TC(0);
+      if (gm < task.m && gk < en.k)
+        v = (TC)(en.trans ? a[(int64_t)gk * en.lda + gm] : a[(int64_t)gm * en.lda + gk]);
+      ra[t] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < C::kXPer; ++t) {
+      const int idx = tid + t * NT;
+      const int k = idx / BN, n = idx % BN;
+      const int gk = kk0 + k;
+      const int64_t gq = q0 + n;
+      TC v = TC(0);
+      if (gk < en.k && gq < q) v = (TC)X[map_row(x_map, en.x_row + gk) * q + gq];
+      rx[t] = v;
+    }
+  };
+  auto store_chunk = [&](int buf, int trans) {
+#pragma unroll
+    for (int t = 0; t < C::kAPer; ++t) {
+      const int idx = tid + t * NT;
+      int m, k;
+      if (trans) { k = idx / BM; m = idx % BM; } else { m = idx / BK; k = idx % BK; }
+      As[buf][k][m] = ra[t];
+    }
+#pragma unroll
+    for (int t = 0; t < C::kXPer; ++t) {
+      const int idx = tid + t * NT;
+      Xs[buf][idx / BN][idx % BN] = rx[t];
+    }
+  };
+
+  if (e < task.e_end) {
+    load_chunk(e, k0);
+    int buf = 0;
+    while (true) {
+      store_chunk(buf, entries[e].trans);
+      __syncthreads();
+      // advance to the next chunk and start its loads before computing this one
+      k0 += BK;
+      if (k0 >= entries[e].k) { ++e; k0 = 0; }
+      const bool more = e < task.e_end;
+      if (more) load_chunk(e, k0);
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        TC av[TM], xv[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) av[i] = As[buf][k][ty * TM + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) xv[j] = Xs[buf][k][tx * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], xv[j], acc[i][j]);
+      }
+      if (!more) break;
+      buf ^= 1;
+    }
+  }
+
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int r = m0 + ty * TM + i;
+    if (r >= task.m) continue;
+    TY* dst = Y + map_row(y_map, task.out_row + r) * q;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t c = q0 + tx * TN + j;
+      if (c < q) dst[c] = task.accumulate ? (TY)(dst[c] + (TY)acc[i][j]) : (TY)acc[i][j];
+    }
+  }
+}
+
+template <typename TA, typename TX, typename TY, typename TC, int BM, int BN>
+cudaError_t launch(const Handle& h, const Phase& ph, const TA* arena, int64_t a_shift, const TX* X,
+                   const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q, cudaStream_t s) {
+  const int64_t n_col = (q + BN - 1) / BN;
+  const int64_t blocks = ph.n_tiles * n_col;
+  if (blocks > 2147483647LL) return cudaErrorInvalidValue;
+  k_grouped_gemm<TA, TX, TY, TC, BM, BN><<<(unsigned)blocks, Cfg<BM, BN>::kThreads, 0, s>>>(
+      h.tiles + ph.tile_begin, h.tasks, h.entries, arena, a_shift, X, x_map, Y, y_map, q, (int)n_col);
+  return cudaGetLastError();
+}
+
+// One launch of a phase: the tile-row class of the launch picks BM, q picks BN.
+template <typename TA, typename TX, typename TY, typename TC>
+cudaError_t launch_phase(const Handle& h, const Phase& ph, const TA* arena, int64_t a_shift, const TX* X,
+                         const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q, cudaStream_t s) {
+  if (ph.n_tiles == 0 || q == 0) return cudaSuccess;
+  if (q > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+#define HMAT_GEMM_BN(BMV)                                                                              \
+  if (q <= 16) return launch<TA, TX, TY, TC, BMV, 16>(h, ph, arena, a_shift, X, x_map, Y, y_map, q, s); \
+  if (q <= 32) return launch<TA, TX, TY, TC, BMV, 32>(h, ph, arena, a_shift, X, x_map, Y, y_map, q, s); \
+  return launch<TA, TX, TY, TC, BMV, 64>(h, ph, arena, a_shift, X, x_map, Y, y_map, q, s);
+  switch (ph.tile_rows) {
+    case 16: { HMAT_GEMM_BN(16) }
+    case 32: { HMAT_GEMM_BN(32) }
+    default: { HMAT_GEMM_BN(64) }
+  }
+#undef HMAT_GEMM_BN
+}
+
+}  // namespace gemm
+}  // namespace hmat

@@ -269,7 +269,7 @@ using namespace hmat;
 extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t* out) {
   if (!out) return HMAT_EINVAL;
   *out = nullptr;
-  if (flags != 0) return HMAT_EUNSUPPORTED;
+  if (flags & ~HMAT_LOAD_MIXED) return HMAT_EUNSUPPORTED;
   if (!p || p->n_points < 1 || p->dim < 1 || p->dim > 64 || !p->points || p->leaf_size < 2 || p->max_rank < 1 ||
       !(p->tol >= 0.0) || !(p->kernel_param > 0.0) ||
       (p->kernel != HMAT_KERNEL_GAUSSIAN && p->kernel != HMAT_KERNEL_IMQ) ||
@@ -364,5 +364,5 @@ extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t*
   desc.near = nullptr;
   desc.perm = t.perm.data();
   DeviceBlockSource src{Xt.data(), d, skel_points.data(), p->kernel, p->kernel_param};
-  return load_impl(&desc, &src, out);
+  return load_impl(&desc, &src, flags, out);
 }

@@ -63,6 +63,48 @@ struct Phase {
   int32_t tile_rows;   // rows per CTA tile of this launch (16, 32 or 64)
 };
 
+// Mixed-precision near field (tensor cores). The near blocks of a target leaf are
+// cut into m-tiles of 128 rows and k-chunks of 64 columns; each (m-tile, k-chunk) is
+// stored as an FP16 hi tile and an FP16 lo tile (hi = fp16(x), lo = fp16(x - hi),
+// x = the value times 2^scale of its m-tile), 128 rows x 128 bytes each in the
+// canonical K-major 128-byte-swizzled layout of a tcgen05 operand, so one bulk copy
+// lands a tile in shared memory ready for the MMA.
+constexpr int kTcRows = 128;        // rows per m-tile (MMA M)
+constexpr int kTcK = 64;            // FP16 values per k-chunk row (128 bytes)
+constexpr int kTcTileBytes = kTcRows * kTcK * 2;   // one FP16 tile: 16 KB
+
+struct TcTile {
+  int32_t leaf;  // leaf-local id
+  int32_t mt;    // m-tile of the leaf
+};
+
+// One (near entry, m-tile, k-chunk) tile pair to pack from the FP64 arena.
+struct TcPackJob {
+  int64_t dst;        // byte offset of the hi tile (the lo tile follows)
+  int64_t src;        // FP64 arena offset of the block
+  int32_t rows, cols; // block shape n_i x n_j
+  int32_t r0, k0;     // first row / column of the tile inside the block
+  int32_t scale_idx;  // index of the m-tile's scale exponent
+  int32_t pad;
+};
+
+// Device-side description of the mixed near field, passed by value to its kernels.
+struct TcNear {
+  const uint8_t* tiles;        // packed hi/lo tiles
+  const int64_t* a_off;        // per near entry: byte offset of its (m-tile 0, chunk 0) pair
+  const int64_t* near_ptr;     // per leaf (leaf-local), CSR
+  const int32_t* near_idx;     // per entry: source leaf (leaf-local)
+  const int32_t* leaf_kc;      // per leaf: k-chunks = ceil(n / 64)
+  const int64_t* leaf_kcum;    // per leaf: k-chunks of the preceding leaves
+  const int64_t* leaf_begin;   // per leaf: first tree-order point
+  const int32_t* leaf_size;    // per leaf: points
+  const int32_t* mt_base;      // per leaf: index of its first m-tile scale
+  const int32_t* scale;        // per m-tile: scale exponent of D
+  const TcTile* work;          // (leaf, m-tile) work items, longest first
+  const int32_t* chunk_leaf;   // per global k-chunk: its leaf
+  const int32_t* chunk_c;      // per global k-chunk: its chunk index within the leaf
+};
+
 struct Handle {
   int device = -1;
   int64_t n_points = 0;
@@ -93,6 +135,23 @@ struct Handle {
   double* host_w = nullptr;      // device copies of W / Y for hmat_eval_host
   double* host_y = nullptr;
   int64_t host_cap = 0;          // capacity of host_w / host_y in values
+
+  // mixed precision (HMAT_LOAD_MIXED)
+  bool has_mixed = false;
+  uint8_t* tc_tiles = nullptr;   // FP16 hi/lo near tiles
+  int64_t tc_bytes = 0;
+  void* tc_meta = nullptr;       // one allocation for the TcNear arrays
+  TcNear tc{};
+  int64_t n_tc_work = 0;         // (leaf, m-tile) work items
+  int64_t total_kchunks = 0;     // sum over leaves of ceil(n / 64)
+  float* arena32 = nullptr;      // FP32 copy of the bases and coupling blocks
+  int64_t arena32_shift = 0;     // FP64-arena offset of arena32[0]
+  uint8_t* wsplit = nullptr;     // W as FP16 hi/lo operand tiles (per evaluation)
+  int64_t wsplit_cap = 0;        // bytes
+  float* ws32 = nullptr;         // FP32 skeleton workspaces of the mixed mode
+  float* us32 = nullptr;
+  int64_t q32_cap = 0;
+  unsigned long long* wmax = nullptr;  // max |W| of the current evaluation (FP64 bits)
 
   // per-launch event timing (hmat_profile / hmat_phase_times)
   struct ProfRecord {
@@ -131,11 +190,28 @@ struct DeviceBlockSource {
 // Shared body of hmat_load (src == nullptr: every block from the host arrays of d)
 // and hmat_build (src != nullptr: d->near and d->coupling are ignored and the
 // blocks are evaluated on the device from the points).
-hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, hmat_handle** out);
+hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flags, hmat_handle** out);
 
 cudaError_t launch_eval_blocks(const BlockJob* jobs, int64_t n_jobs, const double* pts, int dim,
                                const int64_t* skel_pts, int kernel, double param, double* arena,
                                cudaStream_t stream);
+
+// Mixed mode: load-time packing and per-evaluation kernels (hmat_mixed.cu).
+cudaError_t launch_tc_scale(const TcNear& tc, const int64_t* near_off, const double* arena, int64_t n_leaves,
+                            int64_t n_mtiles, const int32_t* mtile_leaf, const int32_t* mtile_mt, int32_t* scale_out,
+                            cudaStream_t stream);
+cudaError_t launch_tc_pack(const TcPackJob* jobs, int64_t n_jobs, const double* arena, const int32_t* scale,
+                           uint8_t* tiles, cudaStream_t stream);
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t stream);
+cudaError_t launch_w_split(const TcNear& tc, int64_t total_kchunks, const double* W, int64_t n_values,
+                           const int64_t* perm, int64_t q, int n_t, int n_ct, unsigned long long* wmax,
+                           uint8_t* wsplit, cudaStream_t stream);
+cudaError_t launch_near_tc(const TcNear& tc, int64_t n_work, const uint8_t* wsplit, const unsigned long long* wmax,
+                           const int64_t* perm, double* Y, int64_t q, int n_t, int n_ct, int* status,
+                           cudaStream_t stream);
+// FP32 grouped GEMM of one far-field phase of the mixed mode (hmat_far32.cu).
+cudaError_t launch_f32_phase(const Handle& h, const Phase& ph, const void* X, bool x_is_f64, const int64_t* x_map,
+                             void* Y, bool y_is_f64, const int64_t* y_map, int64_t q, cudaStream_t stream);
 
 // Launch the FP64 grouped GEMM of one phase on `stream`.
 cudaError_t launch_fp64_phase(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map,

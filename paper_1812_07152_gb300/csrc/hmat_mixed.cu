@@ -1,0 +1,578 @@
+// Mixed-precision near field on the tcgen05 tensor cores (HMAT_MODE_MIXED).
+//
+// The near-field reduction Y_i = sum_j D_ij W_j (Section 2.1, "Evaluation") is a
+// chain of dense contractions, so it runs on the 5th-generation tensor cores:
+//
+//  * D and W are split into two FP16 terms, x ~= hi + lo with hi = fp16(x) and
+//    lo = fp16(x - hi), after a power-of-two scaling that puts the largest |value|
+//    of a D m-tile (128 rows of one target leaf, over its whole near list) and of
+//    W into [2^13, 2^14): 22 significant bits per value, no overflow, no
+//    subnormal lo for values down to 2^-16 of the maximum;
+//  * Y_i = sum_j (Dh Wh + Dh Wl + Dl Wh), the dropped Dl Wl term is 2^-22 relative;
+//  * the tensor core's FP32 accumulator truncates (rounds toward zero, measured on
+//    this GPU), so the dominant Dh Wh product is accumulated in TMEM for one near
+//    block only and then drained by the epilogue warps into a compensated FP32
+//    (hi, lo) pair per output (hi in registers, lo in TMEM columns 384..511); the
+//    two small cross terms (2^-11 of the result) accumulate over the whole near
+//    list in a second TMEM accumulator.
+//
+// Operands are packed once (D at load, W per evaluation) in the canonical K-major
+// 128-byte-swizzled tcgen05 layout, so one cp.async.bulk (TMA) copy per tile lands
+// it in shared memory. Warp roles: warp 0 issues the bulk copies, warp 1 issues the
+// MMAs (one thread) and owns the TMEM allocation, warps 2..9 drain the accumulators
+// and write Y. All waits are bounded; on a timeout the kernel records
+// HMAT_ETIMEOUT in the status word, lets its own copies and MMAs finish, frees its
+// TMEM and returns.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "hmat_internal.h"
+
+namespace hmat {
+namespace {
+
+constexpr int kStages = 3;
+constexpr int kStageBytes = 65536;           // A hi+lo (32 KB) + B hi+lo (<= 32 KB)
+constexpr int kTcThreads = 320;              // warp 0 copies, warp 1 MMAs, warps 2..9 epilogue
+constexpr int kMaxNt = 128;                  // columns of W per CTA (MMA N)
+constexpr uint32_t kTmemCols = 512;          // main[0], main[1], cross, compensation terms
+constexpr uint64_t kWaitNs = 2000000000ull;  // give up a wait after 2 s
+constexpr int kScaleTop = 13;                // scaled maxima land in [2^13, 2^14)
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of `bar` with the given parity; false after kWaitNs or when
+// another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  uint64_t t0 = 0;
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 31) == 31) {
+      if (*abort_flag) return false;
+      const uint64_t t = gtimer();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > kWaitNs) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, FP16 A and B, both K-major.
+__device__ __forceinline__ uint32_t idesc_f16(int m, int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive TMEM columns of this warp's 32 lanes: one FP32 value per column per
+// thread. The registers pass through the wait so that no use is scheduled before it.
+#define HMAT_R16(r) "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), \
+    "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+#define HMAT_RW16(r) "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), \
+    "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+#define HMAT_LD16 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(HMAT_LD16 : HMAT_R16(r) : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : HMAT_RW16(r)::"memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float* va, float* vb) {
+  uint32_t r[16], t[16];
+  asm volatile(HMAT_LD16 : HMAT_R16(r) : "r"(ta));
+  asm volatile(HMAT_LD16 : HMAT_R16(t) : "r"(tb));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : HMAT_RW16(r), HMAT_RW16(t)::"memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    va[j] = __uint_as_float(r[j]);
+    vb[j] = __uint_as_float(t[j]);
+  }
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Exact sum of two FP32 values as s + err (Knuth's TwoSum), err added to the low part.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+__device__ __forceinline__ int scale_exponent(double maxabs) {
+  return maxabs > 0.0 ? kScaleTop - ilogb(maxabs) : 0;
+}
+
+// Byte offset of FP16 value (row r, column k) inside a 128-row x 64-column SW128 tile.
+__device__ __forceinline__ int sw128_chunk(int r, int chunk) { return r * 128 + ((chunk ^ (r & 7)) << 4); }
+
+__device__ __forceinline__ void split_fp16(double x, __half& hi, __half& lo) {
+  hi = __double2half(x);
+  lo = __double2half(x - (double)__half2float(hi));
+}
+
+__device__ double block_max_d(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+  if (threadIdx.x < 32)
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ------------------------------------------------------------------ load-time packing
+
+// Scale exponent of one m-tile: the largest |D| over the tile's rows of every near block.
+__global__ void __launch_bounds__(256) k_tc_scale(TcNear tc, const int64_t* __restrict__ near_off,
+                                                  const double* __restrict__ arena,
+                                                  const int32_t* __restrict__ mtile_leaf,
+                                                  const int32_t* __restrict__ mtile_mt, int32_t* __restrict__ out) {
+  const int t = blockIdx.x;
+  const int leaf = mtile_leaf[t], mt = mtile_mt[t];
+  const int n_i = tc.leaf_size[leaf];
+  const int r0 = mt * kTcRows, r1 = min(n_i, r0 + kTcRows);
+  double m = 0.0;
+  for (int64_t e = tc.near_ptr[leaf]; e < tc.near_ptr[leaf + 1]; ++e) {
+    const int n_j = tc.leaf_size[tc.near_idx[e]];
+    const double* D = arena + near_off[e] + (int64_t)r0 * n_j;
+    const int64_t cnt = (int64_t)(r1 - r0) * n_j;
+    for (int64_t x = threadIdx.x; x < cnt; x += blockDim.x) m = fmax(m, fabs(D[x]));
+  }
+  m = block_max_d(m);
+  if (threadIdx.x == 0) out[t] = scale_exponent(m);
+}
+
+// One (near entry, m-tile, k-chunk): scaled FP64 values -> FP16 hi and lo SW128 tiles.
+__global__ void __launch_bounds__(256) k_tc_pack(const TcPackJob* __restrict__ jobs, const double* __restrict__ arena,
+                                                 const int32_t* __restrict__ scale, uint8_t* __restrict__ tiles) {
+  const TcPackJob job = jobs[blockIdx.x];
+  const int k = scale[job.scale_idx];
+  uint8_t* hi_t = tiles + job.dst;
+  uint8_t* lo_t = hi_t + kTcTileBytes;
+  for (int task = threadIdx.x; task < kTcRows * 8; task += blockDim.x) {
+    const int r = task >> 3, ck = task & 7;
+    const int gr = job.r0 + r;
+    __align__(16) __half hv[8], lv[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int gk = job.k0 + ck * 8 + t;
+      double x = 0.0;
+      if (gr < job.rows && gk < job.cols) x = ldexp(arena[job.src + (int64_t)gr * job.cols + gk], k);
+      split_fp16(x, hv[t], lv[t]);
+    }
+    const int off = sw128_chunk(r, ck);
+    *reinterpret_cast<uint4*>(hi_t + off) = *reinterpret_cast<const uint4*>(hv);
+    *reinterpret_cast<uint4*>(lo_t + off) = *reinterpret_cast<const uint4*>(lv);
+  }
+}
+
+__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+// ------------------------------------------------------------------ per-evaluation W split
+
+__global__ void __launch_bounds__(256) k_w_absmax(const double* __restrict__ W, int64_t n,
+                                                  unsigned long long* __restrict__ out) {
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(W[i]));
+  m = block_max_d(m);
+  if (threadIdx.x == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// One (k-chunk of a source leaf, column tile): 64 rows of W (tree order) x n_t columns
+// -> B-operand tiles: n_t rows (columns of W) x 64 values (rows of W), hi then lo.
+__global__ void __launch_bounds__(256) k_w_split(TcNear tc, const double* __restrict__ W,
+                                                 const int64_t* __restrict__ perm, int64_t q, int n_t, int n_ct,
+                                                 const unsigned long long* __restrict__ wmax,
+                                                 uint8_t* __restrict__ wsplit) {
+  __shared__ __align__(16) uint8_t sh[2 * kMaxNt * 128];
+  const int64_t g = blockIdx.x / n_ct;
+  const int ct = blockIdx.x % n_ct;
+  const int leaf = tc.chunk_leaf[g], c = tc.chunk_c[g];
+  const int n_j = tc.leaf_size[leaf];
+  const int64_t row0 = tc.leaf_begin[leaf] + (int64_t)c * kTcK;
+  const int k_w = scale_exponent(__longlong_as_double((long long)*wmax));
+  const int64_t q0 = (int64_t)ct * n_t;
+  __half* hi_s = reinterpret_cast<__half*>(sh);
+  __half* lo_s = reinterpret_cast<__half*>(sh + n_t * 128);
+  for (int x = threadIdx.x; x < kTcK * n_t; x += blockDim.x) {
+    const int k = x / n_t, n = x % n_t;
+    double v = 0.0;
+    if (c * kTcK + k < n_j && q0 + n < q) v = ldexp(W[perm[row0 + k] * q + q0 + n], k_w);
+    __half h, l;
+    split_fp16(v, h, l);
+    const int off = (sw128_chunk(n, k >> 3) + (k & 7) * 2) >> 1;
+    hi_s[off] = h;
+    lo_s[off] = l;
+  }
+  __syncthreads();
+  uint4* dst = reinterpret_cast<uint4*>(wsplit + (g * n_ct + ct) * (int64_t)(2 * n_t * 128));
+  const uint4* src = reinterpret_cast<const uint4*>(sh);
+  for (int x = threadIdx.x; x < 2 * n_t * 8; x += blockDim.x) dst[x] = src[x];
+}
+
+// ------------------------------------------------------------------ the near-field kernel
+
+struct NearTcArgs {
+  TcNear tc;
+  const uint8_t* wsplit;
+  const unsigned long long* wmax;
+  const int64_t* perm;
+  double* Y;
+  int64_t q;
+  int n_t;
+  int n_ct;
+  int* status;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], mfull_bar[2], mempty_bar[2], cfull_bar,
+      done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  __shared__ volatile int issued, consumed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TcTile work = a.tc.work[blockIdx.x / a.n_ct];
+  const int ct = blockIdx.x % a.n_ct;
+  const int leaf = work.leaf, mt = work.mt;
+  const int64_t e0 = a.tc.near_ptr[leaf], e1 = a.tc.near_ptr[leaf + 1];
+  const uint32_t b_bytes = 2u * (uint32_t)a.n_t * 128u;
+  const uint32_t a_bytes = 2u * kTcTileBytes;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&mfull_bar[b]), 1);
+      mbar_init(smem_u32(&mempty_bar[b]), 8);
+    }
+    mbar_init(smem_u32(&cfull_bar), 1);
+    mbar_init(smem_u32(&done_bar), 1);
+    abort_flag = 0;
+    issued = 0;
+    consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  auto fail = [&]() {
+    abort_flag = 1;
+    atomicCAS(a.status, 0, (int)HMAT_ETIMEOUT);
+  };
+
+  if (warp == 0) {
+    // ---- producer: one bulk copy of the D tile pair and one of the W tile pair per k-chunk
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int64_t e = e0; e < e1 && ok; ++e) {
+        const int j = a.tc.near_idx[e];
+        const int kc = a.tc.leaf_kc[j];
+        if (kc == 0) continue;
+        const uint8_t* abase = a.tc.tiles + a.tc.a_off[e] + (int64_t)mt * kc * a_bytes;
+        const int64_t g0 = a.tc.leaf_kcum[j];
+        for (int c = 0; c < kc; ++c, ++it) {
+          const int s = it % kStages, r = it / kStages;
+          if (r > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (r - 1) & 1, &abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          const uint32_t st = smem_u32(smem + s * kStageBytes);
+          mbar_expect_tx(smem_u32(&full_bar[s]), a_bytes + b_bytes);
+          bulk_g2s(st, abase + (int64_t)c * a_bytes, a_bytes, smem_u32(&full_bar[s]));
+          bulk_g2s(st + a_bytes, a.wsplit + ((g0 + c) * a.n_ct + ct) * (int64_t)b_bytes, b_bytes,
+                   smem_u32(&full_bar[s]));
+          issued = it + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer: main[b] = Dh*Wh for one near block, cross += Dh*Wl + Dl*Wh
+    if (lane == 0) {
+      const uint32_t idesc = idesc_f16(kTcRows, a.n_t);
+      const uint32_t cross = tmem + 256;
+      int it = 0, blk = 0;
+      bool ok = true;
+      for (int64_t e = e0; e < e1 && ok; ++e) {
+        const int kc = a.tc.leaf_kc[a.tc.near_idx[e]];
+        if (kc == 0) continue;
+        const int b = blk & 1, rb = blk >> 1;
+        if (rb > 0 && !mbar_wait(smem_u32(&mempty_bar[b]), (rb - 1) & 1, &abort_flag)) {
+          fail();
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t main_acc = tmem + (uint32_t)b * 128;
+        for (int c = 0; c < kc; ++c, ++it) {
+          const int s = it % kStages, r = it / kStages;
+          if (!mbar_wait(smem_u32(&full_bar[s]), r & 1, &abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t st = smem_u32(smem + s * kStageBytes);
+          const uint32_t a_hi = st, a_lo = st + kTcTileBytes;
+          const uint32_t b_hi = st + 2 * kTcTileBytes, b_lo = b_hi + (uint32_t)a.n_t * 128;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t o = kk * 32;
+            mma_f16(main_acc, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc, (c | kk) ? 1u : 0u);
+            mma_f16(cross, desc_sw128(a_hi + o), desc_sw128(b_lo + o), idesc, (it | kk) ? 1u : 0u);
+            mma_f16(cross, desc_sw128(a_lo + o), desc_sw128(b_hi + o), idesc, 1u);
+          }
+          mma_commit(smem_u32(&empty_bar[s]));
+          consumed = it + 1;
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&mfull_bar[b]));
+        ++blk;
+      }
+      if (ok && blk > 0) mma_commit(smem_u32(&cfull_bar));
+      mma_commit(smem_u32(&done_bar));
+      uint64_t t0 = gtimer();
+      while (!mbar_try(smem_u32(&done_bar), 0) && gtimer() - t0 < kWaitNs) {
+      }
+    }
+  } else {
+    // ---- epilogue: warp w drains TMEM lanes 32*(w%4).. of column half (w-2)/4
+    const int eq = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_base = (uint32_t)(eq * 32) << 16;
+    const uint32_t comp = tmem + lane_base + 384 + half * 64;  // this warp's compensation terms
+    float hi[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) hi[j] = 0.0f;
+    {
+      float z[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) z[j] = 0.0f;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) tmem_st16(comp + cc * 16, z);
+    }
+    int blk = 0;
+    bool ok = true;
+    for (int64_t e = e0; e < e1; ++e) {
+      if (a.tc.leaf_kc[a.tc.near_idx[e]] == 0) continue;
+      const int b = blk & 1, rb = blk >> 1;
+      // every lane must agree before the warp-collective TMEM loads
+      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&mfull_bar[b]), rb & 1, &abort_flag))) {
+        if (lane == 0) fail();
+        ok = false;
+        break;
+      }
+      fence_after();
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        float v[16], l[16];
+        tmem_ld16x2(tmem + lane_base + (uint32_t)(b * 128 + half * 64 + cc * 16), comp + cc * 16, v, l);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) two_sum_acc(hi[cc * 16 + j], l[j], v[j]);
+        tmem_st16(comp + cc * 16, l);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&mempty_bar[b]));
+      ++blk;
+    }
+    bool have_cross = false;
+    if (ok && blk > 0) {
+      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&cfull_bar), 0, &abort_flag))) {
+        if (lane == 0) fail();
+        ok = false;
+      } else {
+        fence_after();
+        have_cross = true;
+      }
+    }
+    const int row = mt * kTcRows + eq * 32 + lane;
+    const bool write = ok && row < a.tc.leaf_size[leaf];
+    const int k_d = a.tc.scale[a.tc.mt_base[leaf] + mt];
+    const int k_w = scale_exponent(__longlong_as_double((long long)*a.wmax));
+    const double sc = ldexp(1.0, -(k_d + k_w));
+    double* dst = a.Y + (write ? a.perm[a.tc.leaf_begin[leaf] + row] * a.q : 0);
+    const int64_t c0 = (int64_t)ct * a.n_t + half * 64;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      float v[16], l[16];
+      if (have_cross) {
+        tmem_ld16x2(comp + cc * 16, tmem + lane_base + (uint32_t)(256 + half * 64 + cc * 16), l, v);
+      } else {
+        tmem_ld16(comp + cc * 16, l);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = cc * 16 + j;
+        const int64_t gc = c0 + col;
+        if (write && half * 64 + col < a.n_t && gc < a.q)
+          dst[gc] = ((double)hi[col] + (double)l[j] + (double)v[j]) * sc;
+      }
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0) {
+    // let the bulk copies this CTA issued land before its shared memory goes away
+    for (int it = consumed; it < issued; ++it) {
+      const uint64_t t0 = gtimer();
+      while (!mbar_try(smem_u32(&full_bar[it % kStages]), (it / kStages) & 1) && gtimer() - t0 < kWaitNs) {
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+
+cudaError_t launch_tc_scale(const TcNear& tc, const int64_t* near_off, const double* arena, int64_t n_leaves,
+                            int64_t n_mtiles, const int32_t* mtile_leaf, const int32_t* mtile_mt, int32_t* scale_out,
+                            cudaStream_t stream) {
+  (void)n_leaves;
+  if (n_mtiles == 0) return cudaSuccess;
+  if (n_mtiles > 2147483647LL) return cudaErrorInvalidValue;
+  k_tc_scale<<<(unsigned)n_mtiles, 256, 0, stream>>>(tc, near_off, arena, mtile_leaf, mtile_mt, scale_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_pack(const TcPackJob* jobs, int64_t n_jobs, const double* arena, const int32_t* scale,
+                           uint8_t* tiles, cudaStream_t stream) {
+  if (n_jobs == 0) return cudaSuccess;
+  if (n_jobs > 2147483647LL) return cudaErrorInvalidValue;
+  k_tc_pack<<<(unsigned)n_jobs, 256, 0, stream>>>(jobs, arena, scale, tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_to_f32<<<(unsigned)blocks, 256, 0, stream>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_w_split(const TcNear& tc, int64_t total_kchunks, const double* W, int64_t n_values,
+                           const int64_t* perm, int64_t q, int n_t, int n_ct, unsigned long long* wmax,
+                           uint8_t* wsplit, cudaStream_t stream) {
+  if (n_t <= 0 || n_t > kMaxNt || n_t % 16 != 0) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(wmax, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = std::min<int64_t>((n_values + 255) / 256, 152 * 8);
+  k_w_absmax<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, stream>>>(W, n_values, wmax);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int64_t grid = total_kchunks * n_ct;
+  if (grid == 0) return cudaSuccess;
+  if (grid > 2147483647LL) return cudaErrorInvalidValue;
+  k_w_split<<<(unsigned)grid, 256, 0, stream>>>(tc, W, perm, q, n_t, n_ct, wmax, wsplit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_tc(const TcNear& tc, int64_t n_work, const uint8_t* wsplit, const unsigned long long* wmax,
+                           const int64_t* perm, double* Y, int64_t q, int n_t, int n_ct, int* status,
+                           cudaStream_t stream) {
+  if (n_work == 0) return cudaSuccess;
+  if (n_t <= 0 || n_t > kMaxNt || n_t % 16 != 0) return cudaErrorInvalidValue;
+  const int64_t grid = n_work * n_ct;
+  if (grid > 2147483647LL) return cudaErrorInvalidValue;
+  const int smem = kStages * kStageBytes + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  NearTcArgs args{tc, wsplit, wmax, perm, Y, q, n_t, n_ct, status};
+  k_near_tc<<<(unsigned)grid, kTcThreads, smem, stream>>>(args);
+  return cudaGetLastError();
+}
+
+}  // namespace hmat

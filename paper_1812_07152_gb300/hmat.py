@@ -24,8 +24,10 @@ HMAT_EUNSUPPORTED = -5
 HMAT_EDEVICE = -6
 
 HMAT_MODE_FP64 = 0
+HMAT_MODE_MIXED = 1
+HMAT_LOAD_MIXED = 1
 
-PHASES = ("near", "up_leaf", "up_transfer", "coupling", "down_transfer", "down_leaf")
+PHASES = ("near", "up_leaf", "up_transfer", "coupling", "down_transfer", "down_leaf", "split")
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "lib", "libhmat.so")
