@@ -207,9 +207,15 @@ void free_device(Handle* h) {
   cudaFree(h->ws32);
   cudaFree(h->us32);
   cudaFree(h->wmax);
+  if (h->aux) cudaStreamDestroy(h->aux);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  h->aux = nullptr; h->ev_fork = nullptr; h->ev_join = nullptr;
   h->tc_tiles = nullptr; h->tc_meta = nullptr; h->arena32 = nullptr; h->wsplit = nullptr;
   h->ws32 = nullptr; h->us32 = nullptr; h->wmax = nullptr; h->has_mixed = false;
   cudaFree(h->arena);
+  cudaFree(h->far_rows);
+  h->far_rows = nullptr;
   cudaFree(h->perm);
   cudaFree(h->tasks);
   cudaFree(h->entries);
@@ -362,6 +368,9 @@ hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const
   if ((e = launch_to_f32(h->arena + basis_begin, h->arena32, h->arena_values - basis_begin, 0)) != cudaSuccess)
     return cuda_status(e);
   if ((e = cudaMalloc((void**)&h->wmax, sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_status(e);
   h->has_mixed = true;
   return HMAT_OK;
@@ -474,13 +483,26 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     h->basis_values += cnt;
     off = align_up(off + cnt, kAlignValues);
   }
-  for (int64_t a = 0; a < v.n_nodes; ++a)
+  // coupling: the blocks of one target node side by side, B_a = [B_ab1 | B_ab2 | ...]
+  // (s_a x K_a, K_a = sum of the partners' ranks), so the far-field reduction of a
+  // node is one product B_a [w_b1; w_b2; ...] whose right operand is gathered through
+  // the row map far_rows.
+  std::vector<int64_t> far_task_off(v.n_nodes, -1), far_k(v.n_nodes, 0), far_rows_off(v.n_nodes, 0);
+  std::vector<int64_t> far_rows_host;
+  for (int64_t a = 0; a < v.n_nodes; ++a) {
+    far_rows_off[a] = (int64_t)far_rows_host.size();
     for (int64_t e = d->far_ptr[a]; e < d->far_ptr[a + 1]; ++e) {
-      far_off[e] = off;
-      const int64_t cnt = (int64_t)h->rank[a] * h->rank[d->far_idx[e]];
-      h->coupling_values += cnt;
-      off = align_up(off + cnt, kAlignValues);
+      const int64_t b = d->far_idx[e];
+      far_off[e] = far_k[a];  // column offset of B_ab inside B_a
+      far_k[a] += h->rank[b];
+      for (int32_t r = 0; r < h->rank[b]; ++r) far_rows_host.push_back(h->skel_off[b] + r);
     }
+    if (h->rank[a] == 0 || far_k[a] == 0) continue;
+    far_task_off[a] = off;
+    const int64_t cnt = (int64_t)h->rank[a] * far_k[a];
+    h->coupling_values += cnt;
+    off = align_up(off + cnt, kAlignValues);
+  }
   h->arena_values = std::max<int64_t>(off, 1);
 
   // ---- work lists
@@ -491,9 +513,9 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
   // One launch per row-tile size: tasks of at most 16 or 32 rows get smaller tiles so
   // that the FP64 kernels spend no DFMA on padding rows of small skeleton blocks.
   auto add_phase = [&](PhaseKind kind, int32_t level, MatrixKind x, MatrixKind y,
-                       const std::vector<int32_t>& task_ids) {
+                       const std::vector<int32_t>& task_ids, XMap xmap) {
     for (int32_t rows_cls : {64, 32, 16}) {
-      Phase ph{kind, level, x, y, (int64_t)tiles.size(), 0, 0, rows_cls};
+      Phase ph{kind, level, x, y, xmap, (int64_t)tiles.size(), 0, 0, rows_cls};
       std::vector<std::pair<int64_t, GemmTile>> list;
       for (int32_t t : task_ids) {
         const GemmTask& tk = tasks[t];
@@ -536,7 +558,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
       }
       ids.push_back(t);
     }
-    add_phase(PH_NEAR, d->levels, MAT_USER, MAT_USER, ids);
+    add_phase(PH_NEAR, d->levels, MAT_USER, MAT_USER, ids, XMAP_PERM);
   }
   {  // upward pass, leaves
     std::vector<int32_t> ids;
@@ -546,7 +568,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
       add_entry(t, basis_off[a], h->begin[a], h->size[a], h->rank[a], 1);
       ids.push_back(t);
     }
-    add_phase(PH_UP_LEAF, d->levels, MAT_USER, MAT_SKEL_W, ids);
+    add_phase(PH_UP_LEAF, d->levels, MAT_USER, MAT_SKEL_W, ids, XMAP_PERM);
   }
   for (int32_t level = d->levels - 1; level >= 1; --level) {  // upward pass, inner levels
     std::vector<int32_t> ids;
@@ -556,20 +578,17 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
       add_entry(t, basis_off[a], h->skel_off[2 * a + 1], rows_of(a), h->rank[a], 1);
       ids.push_back(t);
     }
-    add_phase(PH_UP_TRANS, level, MAT_SKEL_W, MAT_SKEL_W, ids);
+    add_phase(PH_UP_TRANS, level, MAT_SKEL_W, MAT_SKEL_W, ids, XMAP_NONE);
   }
   {  // far field: every node with a basis (also initialises u for the downward pass)
     std::vector<int32_t> ids;
     for (int64_t a = 1; a < v.n_nodes; ++a) {
       if (h->rank[a] == 0) continue;
       const int32_t t = new_task(h->skel_off[a], h->rank[a], 0);
-      for (int64_t e = d->far_ptr[a]; e < d->far_ptr[a + 1]; ++e) {
-        const int64_t b = d->far_idx[e];
-        add_entry(t, far_off[e], h->skel_off[b], h->rank[b], h->rank[b], 0);
-      }
+      if (far_task_off[a] >= 0) add_entry(t, far_task_off[a], far_rows_off[a], far_k[a], far_k[a], 0);
       ids.push_back(t);
     }
-    add_phase(PH_COUPLING, 0, MAT_SKEL_W, MAT_SKEL_U, ids);
+    add_phase(PH_COUPLING, 0, MAT_SKEL_W, MAT_SKEL_U, ids, XMAP_FAR);
   }
   for (int32_t level = 1; level < d->levels; ++level) {  // downward pass, inner levels
     std::vector<int32_t> ids;
@@ -579,7 +598,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
       add_entry(t, basis_off[a], h->skel_off[a], h->rank[a], h->rank[a], 0);
       ids.push_back(t);
     }
-    add_phase(PH_DOWN_TRANS, level, MAT_SKEL_U, MAT_SKEL_U, ids);
+    add_phase(PH_DOWN_TRANS, level, MAT_SKEL_U, MAT_SKEL_U, ids, XMAP_NONE);
   }
   {  // downward pass, leaves (adds into Y)
     std::vector<int32_t> ids;
@@ -589,7 +608,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
       add_entry(t, basis_off[a], h->skel_off[a], h->rank[a], h->rank[a], 0);
       ids.push_back(t);
     }
-    add_phase(PH_DOWN_LEAF, d->levels, MAT_SKEL_U, MAT_USER, ids);
+    add_phase(PH_DOWN_LEAF, d->levels, MAT_SKEL_U, MAT_USER, ids, XMAP_NONE);
   }
 
   // ---- device allocations and upload
@@ -615,11 +634,16 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     for (int64_t a = 0; a < v.n_nodes && ce == cudaSuccess; ++a)
       if (h->rank[a] > 0) finite &= up.put(basis_off[a], d->basis[a], rows_of(a) * h->rank[a], &ce);
     if (!src) {
-      for (int64_t a = 0; a < v.n_nodes && ce == cudaSuccess; ++a)
-        for (int64_t ee = d->far_ptr[a]; ee < d->far_ptr[a + 1] && ce == cudaSuccess; ++ee) {
-          const int64_t cnt = (int64_t)h->rank[a] * h->rank[d->far_idx[ee]];
-          finite &= up.put(far_off[ee], d->coupling[ee], cnt, &ce);
-        }
+      for (int64_t a = 0; a < v.n_nodes && ce == cudaSuccess; ++a) {
+        if (far_task_off[a] < 0) continue;
+        for (int32_t r = 0; r < h->rank[a] && ce == cudaSuccess; ++r)
+          for (int64_t ee = d->far_ptr[a]; ee < d->far_ptr[a + 1] && ce == cudaSuccess; ++ee) {
+            const int32_t sb = h->rank[d->far_idx[ee]];
+            if (sb > 0)
+              finite &= up.put(far_task_off[a] + r * far_k[a] + far_off[ee], d->coupling[ee] + (int64_t)r * sb, sb,
+                               &ce);
+          }
+      }
     }
     if (ce == cudaSuccess) ce = up.finish();
     if (ce != cudaSuccess) return fail(ce);
@@ -631,13 +655,15 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
       for (int64_t ee = d->near_ptr[i]; ee < d->near_ptr[i + 1]; ++ee) {
         const int64_t a = fl + i, b = fl + d->near_idx[ee];
         if (h->size[a] * h->size[b] == 0) continue;
-        jobs.push_back(BlockJob{near_off[ee], h->begin[a], h->begin[b], (int32_t)h->size[a], (int32_t)h->size[b], 0, 0});
+        jobs.push_back(BlockJob{near_off[ee], h->size[b], h->begin[a], h->begin[b], (int32_t)h->size[a],
+                                (int32_t)h->size[b], 0, 0});
       }
     for (int64_t a = 0; a < v.n_nodes; ++a)
       for (int64_t ee = d->far_ptr[a]; ee < d->far_ptr[a + 1]; ++ee) {
         const int64_t b = d->far_idx[ee];
         if ((int64_t)h->rank[a] * h->rank[b] == 0) continue;
-        jobs.push_back(BlockJob{far_off[ee], h->skel_off[a], h->skel_off[b], h->rank[a], h->rank[b], 1, 1});
+        jobs.push_back(BlockJob{far_task_off[a] + far_off[ee], far_k[a], h->skel_off[a], h->skel_off[b], h->rank[a],
+                                h->rank[b], 1, 1});
       }
     std::vector<double> pts(src->points_tree, src->points_tree + d->n_points * (int64_t)src->dim);
     std::vector<int64_t> skel(src->skel_points, src->skel_points + h->sum_rank);
@@ -659,6 +685,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
   }
   std::vector<int64_t> perm(d->perm, d->perm + d->n_points);
   if ((e = upload(&h->perm, perm, &h->device_bytes)) != cudaSuccess) return fail(e);
+  if ((e = upload(&h->far_rows, far_rows_host, &h->device_bytes)) != cudaSuccess) return fail(e);
   if ((e = upload(&h->tasks, tasks, &h->device_bytes)) != cudaSuccess) return fail(e);
   if ((e = upload(&h->entries, entries, &h->device_bytes)) != cudaSuccess) return fail(e);
   if ((e = upload(&h->tiles, tiles, &h->device_bytes)) != cudaSuccess) return fail(e);
@@ -748,25 +775,37 @@ extern "C" hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q
     const int n_ct = (int)n_ct64;
     hmat_status st = reserve_mixed(h, q, n_t, n_ct);
     if (st != HMAT_OK) return st;
+    // the far chain (up, coupling, down to the leaves' skeletons) reads only W: run it on the
+    // auxiliary stream beside the tensor-core near field; the leaf step of the downward pass
+    // adds into Y, so it follows both on the caller's stream
+    if (cudaEventRecord(h->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(h->aux, h->ev_fork, 0) != cudaSuccess)
+      return HMAT_ECUDA;
+    cudaError_t e = cudaSuccess;
+    auto far_launch = [&](const Phase& ph, cudaStream_t strm) -> hmat_status {
+      const void* X = ph.x == MAT_USER ? (const void*)W : (ph.x == MAT_SKEL_W ? (const void*)h->ws32 : h->us32);
+      void* Yd = ph.y == MAT_USER ? (void*)Y : (ph.y == MAT_SKEL_W ? (void*)h->ws32 : (void*)h->us32);
+      const int64_t* xm = phase_x_map(*h, ph);
+      const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
+      if (!prof_begin(h, (int32_t)ph.kind, strm, &rec)) return HMAT_ECUDA;
+      e = launch_f32_phase(*h, ph, X, ph.x == MAT_USER, xm, Yd, ph.y == MAT_USER, ym, q, strm);
+      if (e != cudaSuccess) return cuda_status(e);
+      return prof_end(h, rec, strm) ? HMAT_OK : HMAT_ECUDA;
+    };
+    for (const Phase& ph : h->phases) {
+      if (ph.kind == PH_NEAR || ph.kind == PH_DOWN_LEAF) continue;
+      if ((st = far_launch(ph, h->aux)) != HMAT_OK) return st;
+    }
+    if (cudaEventRecord(h->ev_join, h->aux) != cudaSuccess) return HMAT_ECUDA;
     if (!prof_begin(h, HMAT_PHASE_SPLIT, s, &rec)) return HMAT_ECUDA;
-    cudaError_t e = launch_w_split(h->tc, h->total_kchunks, W, h->n_points * q, h->perm, q, n_t, n_ct, h->wmax,
-                                   h->wsplit, s);
+    e = launch_w_split(h->tc, h->total_kchunks, W, h->n_points * q, h->perm, q, n_t, n_ct, h->wmax, h->wsplit, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s) || !prof_begin(h, HMAT_PHASE_NEAR, s, &rec)) return HMAT_ECUDA;
     e = launch_near_tc(h->tc, h->n_tc_work, h->wsplit, h->wmax, h->perm, Y, q, n_t, n_ct, h->status, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;
-    for (const Phase& ph : h->phases) {
-      if (ph.kind == PH_NEAR) continue;
-      const void* X = ph.x == MAT_USER ? (const void*)W : (ph.x == MAT_SKEL_W ? (const void*)h->ws32 : h->us32);
-      void* Yd = ph.y == MAT_USER ? (void*)Y : (ph.y == MAT_SKEL_W ? (void*)h->ws32 : (void*)h->us32);
-      const int64_t* xm = ph.x == MAT_USER ? h->perm : nullptr;
-      const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
-      if (!prof_begin(h, (int32_t)ph.kind, s, &rec)) return HMAT_ECUDA;
-      e = launch_f32_phase(*h, ph, X, ph.x == MAT_USER, xm, Yd, ph.y == MAT_USER, ym, q, s);
-      if (e != cudaSuccess) return cuda_status(e);
-      if (!prof_end(h, rec, s)) return HMAT_ECUDA;
-    }
+    if (cudaStreamWaitEvent(s, h->ev_join, 0) != cudaSuccess) return HMAT_ECUDA;
+    for (const Phase& ph : h->phases)
+      if (ph.kind == PH_DOWN_LEAF && (st = far_launch(ph, s)) != HMAT_OK) return st;
     return HMAT_OK;
   }
 
@@ -777,7 +816,7 @@ extern "C" hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q
   for (const Phase& ph : h->phases) {
     const double* X = ph.x == MAT_USER ? W : (ph.x == MAT_SKEL_W ? h->ws : h->us);
     double* Yd = ph.y == MAT_USER ? Y : (ph.y == MAT_SKEL_W ? h->ws : h->us);
-    const int64_t* xm = ph.x == MAT_USER ? h->perm : nullptr;
+    const int64_t* xm = phase_x_map(*h, ph);
     const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
     if (!prof_begin(h, (int32_t)ph.kind, s, &rec)) return HMAT_ECUDA;
     cudaError_t e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, s);

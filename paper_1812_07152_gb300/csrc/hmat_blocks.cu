@@ -30,7 +30,7 @@ k_eval_blocks(const BlockJob* __restrict__ jobs, const double* __restrict__ pts,
       const double diff = x[k] - y[k];
       r2 = __dadd_rn(r2, __dmul_rn(diff, diff));
     }
-    out[e] = kernel == HMAT_KERNEL_GAUSSIAN ? exp(-r2 / two_h2) : 1.0 / sqrt(r2 + c2);
+    out[r * job.ld + c] = kernel == HMAT_KERNEL_GAUSSIAN ? exp(-r2 / two_h2) : 1.0 / sqrt(r2 + c2);
   }
 }
 

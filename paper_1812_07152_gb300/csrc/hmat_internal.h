@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/hmat.h"
+#include "hmat.h"
 
 namespace hmat {
 
@@ -52,11 +52,17 @@ enum PhaseKind : int32_t {
   PH_DOWN_LEAF = 5   // Y_i += P_i u_i                           (downward pass, leaves)
 };
 
+// How the rows of a phase's X operand are found: directly, through the point
+// permutation (W in the caller's order) or through the coupling row map (the
+// skeleton rows of a target's far partners, concatenated).
+enum XMap : int32_t { XMAP_NONE = 0, XMAP_PERM = 1, XMAP_FAR = 2 };
+
 struct Phase {
   PhaseKind kind;
   int32_t level;
   MatrixKind x;
   MatrixKind y;
+  XMap xmap;
   int64_t tile_begin;  // into the tile array (one array for all phases)
   int64_t n_tiles;
   int32_t max_m;       // largest task height of the launch
@@ -124,6 +130,7 @@ struct Handle {
   double* arena = nullptr;       // packed FP64 blocks (near, basis, coupling)
   int64_t arena_values = 0;
   int64_t* perm = nullptr;       // tree order -> caller order
+  int64_t* far_rows = nullptr;   // coupling row map: per target, its far partners' skeleton rows
   GemmTask* tasks = nullptr;
   GemmEntry* entries = nullptr;
   GemmTile* tiles = nullptr;
@@ -152,6 +159,8 @@ struct Handle {
   float* us32 = nullptr;
   int64_t q32_cap = 0;
   unsigned long long* wmax = nullptr;  // max |W| of the current evaluation (FP64 bits)
+  cudaStream_t aux = nullptr;    // the far chain of the mixed mode runs here, beside the near field
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // per-launch event timing (hmat_profile / hmat_phase_times)
   struct ProfRecord {
@@ -170,6 +179,7 @@ struct Handle {
 // row_off .. of the skeleton point list (skel = 1).
 struct BlockJob {
   int64_t a_off;
+  int64_t ld;        // row stride of the block in the arena
   int64_t row_off;
   int64_t col_off;
   int32_t rows;
@@ -217,6 +227,12 @@ cudaError_t launch_f32_phase(const Handle& h, const Phase& ph, const void* X, bo
 cudaError_t launch_fp64_phase(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map,
                               double* Y, const int64_t* y_map, int64_t q, cudaStream_t stream);
 
+}  // namespace hmat
+
+namespace hmat {
+inline const int64_t* phase_x_map(const Handle& h, const Phase& ph) {
+  return ph.xmap == XMAP_PERM ? h.perm : (ph.xmap == XMAP_FAR ? h.far_rows : nullptr);
+}
 }  // namespace hmat
 
 // The opaque handle of the C ABI is the internal Handle.

@@ -58,7 +58,7 @@ extern "C" hmat_status hmat_eval_noalloc(hmat_t h, const double* W, double* Y, i
   for (const Phase& ph : h->phases) {
     const double* X = ph.x == MAT_USER ? W : (ph.x == MAT_SKEL_W ? ws : us);
     double* Yd = ph.y == MAT_USER ? Y : (ph.y == MAT_SKEL_W ? ws : us);
-    const int64_t* xm = ph.x == MAT_USER ? h->perm : nullptr;
+    const int64_t* xm = phase_x_map(*h, ph);
     const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
     const cudaError_t e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, s);
     if (e != cudaSuccess) return HMAT_ECUDA;
