@@ -206,6 +206,8 @@ void free_device(Handle* h) {
   cudaFree(h->wsplit);
   cudaFree(h->ws32);
   cudaFree(h->us32);
+  cudaFree(h->w32);
+  h->w32 = nullptr;
   cudaFree(h->wmax);
   if (h->aux) cudaStreamDestroy(h->aux);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -368,7 +370,12 @@ hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const
   if ((e = launch_to_f32(h->arena + basis_begin, h->arena32, h->arena_values - basis_begin, 0)) != cudaSuccess)
     return cuda_status(e);
   if ((e = cudaMalloc((void**)&h->wmax, sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
-  if ((e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking)) != cudaSuccess) return cuda_status(e);
+  // the far chain is a chain of short dependent launches beside the long near-field launch:
+  // the highest priority lets its CTAs take SMs as soon as near-field CTAs retire
+  int prio_lo = 0, prio_hi = 0;
+  if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_hi)) != cudaSuccess)
+    return cuda_status(e);
   if ((e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_status(e);
@@ -391,16 +398,21 @@ hmat_status reserve_mixed(Handle* h, int64_t q, int n_t, int n_ct) {
   }
   if (q > h->q32_cap) {
     const size_t n = (size_t)std::max<int64_t>(h->sum_rank, 1) * (size_t)q * sizeof(float);
-    float *ws = nullptr, *us = nullptr;
+    const size_t nw = (size_t)std::max<int64_t>(h->n_points, 1) * (size_t)q * sizeof(float);
+    float *ws = nullptr, *us = nullptr, *w32 = nullptr;
     cudaError_t e = cudaMalloc((void**)&ws, n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&us, n);
-    if (e != cudaSuccess) { cudaFree(ws); cudaGetLastError(); return cuda_status(e); }
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w32, nw);
+    if (e != cudaSuccess) { cudaFree(ws); cudaFree(us); cudaGetLastError(); return cuda_status(e); }
     cudaDeviceSynchronize();
     cudaFree(h->ws32);
     cudaFree(h->us32);
-    h->device_bytes += 2 * (int64_t)n - 2 * std::max<int64_t>(h->sum_rank, 1) * h->q32_cap * (int64_t)sizeof(float);
+    cudaFree(h->w32);
+    const int64_t old = (2 * std::max<int64_t>(h->sum_rank, 1) + std::max<int64_t>(h->n_points, 1)) * h->q32_cap;
+    h->device_bytes += (int64_t)(2 * n + nw) - old * (int64_t)sizeof(float);
     h->ws32 = ws;
     h->us32 = us;
+    h->w32 = w32;
     h->q32_cap = q;
   }
   return HMAT_OK;
@@ -775,19 +787,24 @@ extern "C" hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q
     const int n_ct = (int)n_ct64;
     hmat_status st = reserve_mixed(h, q, n_t, n_ct);
     if (st != HMAT_OK) return st;
-    // the far chain (up, coupling, down to the leaves' skeletons) reads only W: run it on the
-    // auxiliary stream beside the tensor-core near field; the leaf step of the downward pass
-    // adds into Y, so it follows both on the caller's stream
+    // split W (the tensor-core tiles and an FP32 tree-order copy), then run the far chain
+    // (up, coupling, down to the leaves' skeletons) on the auxiliary stream beside the
+    // tensor-core near field; the leaf step of the downward pass adds into Y, so it
+    // follows both on the caller's stream
+    if (!prof_begin(h, HMAT_PHASE_SPLIT, s, &rec)) return HMAT_ECUDA;
+    cudaError_t e = launch_w_split(h->tc, h->total_kchunks, W, h->n_points * q, h->perm, q, n_t, n_ct, h->wmax,
+                                   h->wsplit, h->w32, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!prof_end(h, rec, s)) return HMAT_ECUDA;
     if (cudaEventRecord(h->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(h->aux, h->ev_fork, 0) != cudaSuccess)
       return HMAT_ECUDA;
-    cudaError_t e = cudaSuccess;
     auto far_launch = [&](const Phase& ph, cudaStream_t strm) -> hmat_status {
-      const void* X = ph.x == MAT_USER ? (const void*)W : (ph.x == MAT_SKEL_W ? (const void*)h->ws32 : h->us32);
+      const float* X = ph.x == MAT_USER ? h->w32 : (ph.x == MAT_SKEL_W ? h->ws32 : h->us32);
       void* Yd = ph.y == MAT_USER ? (void*)Y : (ph.y == MAT_SKEL_W ? (void*)h->ws32 : (void*)h->us32);
-      const int64_t* xm = phase_x_map(*h, ph);
+      const int64_t* xm = ph.xmap == XMAP_FAR ? h->far_rows : nullptr;  // the FP32 copy of W is in tree order
       const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
       if (!prof_begin(h, (int32_t)ph.kind, strm, &rec)) return HMAT_ECUDA;
-      e = launch_f32_phase(*h, ph, X, ph.x == MAT_USER, xm, Yd, ph.y == MAT_USER, ym, q, strm);
+      e = launch_f32_phase(*h, ph, X, xm, Yd, ph.y == MAT_USER, ym, q, strm);
       if (e != cudaSuccess) return cuda_status(e);
       return prof_end(h, rec, strm) ? HMAT_OK : HMAT_ECUDA;
     };
@@ -796,10 +813,7 @@ extern "C" hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q
       if ((st = far_launch(ph, h->aux)) != HMAT_OK) return st;
     }
     if (cudaEventRecord(h->ev_join, h->aux) != cudaSuccess) return HMAT_ECUDA;
-    if (!prof_begin(h, HMAT_PHASE_SPLIT, s, &rec)) return HMAT_ECUDA;
-    e = launch_w_split(h->tc, h->total_kchunks, W, h->n_points * q, h->perm, q, n_t, n_ct, h->wmax, h->wsplit, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (!prof_end(h, rec, s) || !prof_begin(h, HMAT_PHASE_NEAR, s, &rec)) return HMAT_ECUDA;
+    if (!prof_begin(h, HMAT_PHASE_NEAR, s, &rec)) return HMAT_ECUDA;
     e = launch_near_tc(h->tc, h->n_tc_work, h->wsplit, h->wmax, h->perm, Y, q, n_t, n_ct, h->status, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;

@@ -155,6 +155,7 @@ struct Handle {
   int64_t arena32_shift = 0;     // FP64-arena offset of arena32[0]
   uint8_t* wsplit = nullptr;     // W as FP16 hi/lo operand tiles (per evaluation)
   int64_t wsplit_cap = 0;        // bytes
+  float* w32 = nullptr;          // FP32 copy of W in tree order (mixed mode)
   float* ws32 = nullptr;         // FP32 skeleton workspaces of the mixed mode
   float* us32 = nullptr;
   int64_t q32_cap = 0;
@@ -215,13 +216,13 @@ cudaError_t launch_tc_pack(const TcPackJob* jobs, int64_t n_jobs, const double* 
 cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t stream);
 cudaError_t launch_w_split(const TcNear& tc, int64_t total_kchunks, const double* W, int64_t n_values,
                            const int64_t* perm, int64_t q, int n_t, int n_ct, unsigned long long* wmax,
-                           uint8_t* wsplit, cudaStream_t stream);
+                           uint8_t* wsplit, float* w32, cudaStream_t stream);
 cudaError_t launch_near_tc(const TcNear& tc, int64_t n_work, const uint8_t* wsplit, const unsigned long long* wmax,
                            const int64_t* perm, double* Y, int64_t q, int n_t, int n_ct, int* status,
                            cudaStream_t stream);
 // FP32 grouped GEMM of one far-field phase of the mixed mode (hmat_far32.cu).
-cudaError_t launch_f32_phase(const Handle& h, const Phase& ph, const void* X, bool x_is_f64, const int64_t* x_map,
-                             void* Y, bool y_is_f64, const int64_t* y_map, int64_t q, cudaStream_t stream);
+cudaError_t launch_f32_phase(const Handle& h, const Phase& ph, const float* X, const int64_t* x_map, void* Y,
+                             bool y_is_f64, const int64_t* y_map, int64_t q, cudaStream_t stream);
 
 // Launch the FP64 grouped GEMM of one phase on `stream`.
 cudaError_t launch_fp64_phase(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map,

@@ -253,35 +253,45 @@ __global__ void __launch_bounds__(256) k_w_absmax(const double* __restrict__ W, 
 }
 
 // One (k-chunk of a source leaf, column tile): 64 rows of W (tree order) x n_t columns
-// -> B-operand tiles: n_t rows (columns of W) x 64 values (rows of W), hi then lo.
+// -> B-operand tiles: n_t rows (columns of W) x 64 values (rows of W), hi then lo,
+// and the same values unscaled in FP32, tree order (the far field's input).
+// A thread owns one column and 8 consecutive rows: one 16-byte chunk of each tile.
+// FP64 arithmetic is 1/64 rate on this GPU, so the split itself is done in FP32
+// after one scaled FP64 -> FP32 conversion (24 bits kept, 22 needed).
 __global__ void __launch_bounds__(256) k_w_split(TcNear tc, const double* __restrict__ W,
                                                  const int64_t* __restrict__ perm, int64_t q, int n_t, int n_ct,
                                                  const unsigned long long* __restrict__ wmax,
-                                                 uint8_t* __restrict__ wsplit) {
-  __shared__ __align__(16) uint8_t sh[2 * kMaxNt * 128];
+                                                 uint8_t* __restrict__ wsplit, float* __restrict__ w32) {
   const int64_t g = blockIdx.x / n_ct;
   const int ct = blockIdx.x % n_ct;
   const int leaf = tc.chunk_leaf[g], c = tc.chunk_c[g];
   const int n_j = tc.leaf_size[leaf];
   const int64_t row0 = tc.leaf_begin[leaf] + (int64_t)c * kTcK;
   const int k_w = scale_exponent(__longlong_as_double((long long)*wmax));
+  const double sd = ldexp(1.0, k_w);
   const int64_t q0 = (int64_t)ct * n_t;
-  __half* hi_s = reinterpret_cast<__half*>(sh);
-  __half* lo_s = reinterpret_cast<__half*>(sh + n_t * 128);
-  for (int x = threadIdx.x; x < kTcK * n_t; x += blockDim.x) {
-    const int k = x / n_t, n = x % n_t;
-    double v = 0.0;
-    if (c * kTcK + k < n_j && q0 + n < q) v = ldexp(W[perm[row0 + k] * q + q0 + n], k_w);
-    __half h, l;
-    split_fp16(v, h, l);
-    const int off = (sw128_chunk(n, k >> 3) + (k & 7) * 2) >> 1;
-    hi_s[off] = h;
-    lo_s[off] = l;
+  uint8_t* hi_t = wsplit + (g * n_ct + ct) * (int64_t)(2 * n_t * 128);
+  uint8_t* lo_t = hi_t + n_t * 128;
+  for (int x = threadIdx.x; x < n_t * 8; x += blockDim.x) {
+    const int kc = x / n_t, n = x % n_t;
+    const int64_t gq = q0 + n;
+    __align__(16) __half hv[8], lv[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int k = kc * 8 + t;
+      float xs = 0.0f;
+      if (c * kTcK + k < n_j && gq < q) {
+        const double v = W[perm[row0 + k] * q + gq];
+        xs = __double2float_rn(v * sd);
+        w32[(row0 + k) * q + gq] = __double2float_rn(v);
+      }
+      hv[t] = __float2half_rn(xs);
+      lv[t] = __float2half_rn(xs - __half2float(hv[t]));
+    }
+    const int off = sw128_chunk(n, kc);
+    *reinterpret_cast<uint4*>(hi_t + off) = *reinterpret_cast<const uint4*>(hv);
+    *reinterpret_cast<uint4*>(lo_t + off) = *reinterpret_cast<const uint4*>(lv);
   }
-  __syncthreads();
-  uint4* dst = reinterpret_cast<uint4*>(wsplit + (g * n_ct + ct) * (int64_t)(2 * n_t * 128));
-  const uint4* src = reinterpret_cast<const uint4*>(sh);
-  for (int x = threadIdx.x; x < 2 * n_t * 8; x += blockDim.x) dst[x] = src[x];
 }
 
 // ------------------------------------------------------------------ the near-field kernel
@@ -546,7 +556,7 @@ cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t
 
 cudaError_t launch_w_split(const TcNear& tc, int64_t total_kchunks, const double* W, int64_t n_values,
                            const int64_t* perm, int64_t q, int n_t, int n_ct, unsigned long long* wmax,
-                           uint8_t* wsplit, cudaStream_t stream) {
+                           uint8_t* wsplit, float* w32, cudaStream_t stream) {
   if (n_t <= 0 || n_t > kMaxNt || n_t % 16 != 0) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(wmax, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
@@ -556,7 +566,7 @@ cudaError_t launch_w_split(const TcNear& tc, int64_t total_kchunks, const double
   const int64_t grid = total_kchunks * n_ct;
   if (grid == 0) return cudaSuccess;
   if (grid > 2147483647LL) return cudaErrorInvalidValue;
-  k_w_split<<<(unsigned)grid, 256, 0, stream>>>(tc, W, perm, q, n_t, n_ct, wmax, wsplit);
+  k_w_split<<<(unsigned)grid, 256, 0, stream>>>(tc, W, perm, q, n_t, n_ct, wmax, wsplit, w32);
   return cudaGetLastError();
 }
 
