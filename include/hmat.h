@@ -257,6 +257,28 @@ hmat_status hmat_measure_fp64_peak(double* gflops);
 hmat_status hmat_eval_noalloc(hmat_t h, const double* W, double* Y, int64_t q, void* stream);
 
 /*
+ * Batches: many HMatrices (uneven sizes, ranks and q) evaluated together. A batch
+ * owns one evaluation context (workspaces) and one CUDA stream per member; the
+ * first hmat_batch_eval with a given set of W, Y pointers and q values captures
+ * every member's evaluation as a parallel branch of one CUDA graph, later calls
+ * with the same arguments replay that graph with a single launch (a call with
+ * other arguments captures a new graph). The same handle may appear more than
+ * once. Handles must outlive the batch and must not be evaluated elsewhere while
+ * one of the batch's graphs runs.
+ *
+ * hmat_batch_create - `count` handles (all on the current device), `mode` is
+ * HMAT_MODE_FP64 or HMAT_MODE_MIXED (every handle loaded with HMAT_LOAD_MIXED).
+ * hmat_batch_eval - Y[i] = K~_i W[i] (device pointers, n_i x q[i], caller order)
+ * for every member, enqueued on `stream`; the first call for a new argument set
+ * allocates workspaces (cudaMalloc, which synchronises the device).
+ */
+typedef struct hmat_batch* hmat_batch_t;
+hmat_status hmat_batch_create(const hmat_t* handles, int count, int mode, hmat_batch_t* out);
+hmat_status hmat_batch_eval(hmat_batch_t b, const double* const* W, double* const* Y, const int64_t* q,
+                            void* stream);
+hmat_status hmat_batch_free(hmat_batch_t b);
+
+/*
  * hmat_status_poll - synchronise `stream` and return the device status word
  * latched by the kernels since the last poll (HMAT_OK when nothing happened),
  * then clear it.

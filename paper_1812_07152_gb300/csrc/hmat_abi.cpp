@@ -196,25 +196,12 @@ void free_device(Handle* h) {
   h->prof.clear();
   for (cudaEvent_t ev : h->event_pool) cudaEventDestroy(ev);
   h->event_pool.clear();
-  cudaFree(h->host_w);
-  cudaFree(h->host_y);
-  h->host_w = nullptr;
-  h->host_y = nullptr;
+  ctx_destroy(h->ctx);
+  h->ctx = nullptr;
   cudaFree(h->tc_tiles);
   cudaFree(h->tc_meta);
   cudaFree(h->arena32);
-  cudaFree(h->wsplit);
-  cudaFree(h->ws32);
-  cudaFree(h->us32);
-  cudaFree(h->w32);
-  h->w32 = nullptr;
-  cudaFree(h->wmax);
-  if (h->aux) cudaStreamDestroy(h->aux);
-  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-  if (h->ev_join) cudaEventDestroy(h->ev_join);
-  h->aux = nullptr; h->ev_fork = nullptr; h->ev_join = nullptr;
-  h->tc_tiles = nullptr; h->tc_meta = nullptr; h->arena32 = nullptr; h->wsplit = nullptr;
-  h->ws32 = nullptr; h->us32 = nullptr; h->wmax = nullptr; h->has_mixed = false;
+  h->tc_tiles = nullptr; h->tc_meta = nullptr; h->arena32 = nullptr; h->has_mixed = false;
   cudaFree(h->arena);
   cudaFree(h->far_rows);
   h->far_rows = nullptr;
@@ -223,10 +210,8 @@ void free_device(Handle* h) {
   cudaFree(h->entries);
   cudaFree(h->tiles);
   cudaFree(h->status);
-  cudaFree(h->ws);
-  cudaFree(h->us);
   h->arena = nullptr; h->perm = nullptr; h->tasks = nullptr; h->entries = nullptr;
-  h->tiles = nullptr; h->status = nullptr; h->ws = nullptr; h->us = nullptr;
+  h->tiles = nullptr; h->status = nullptr;
 }
 
 template <class T>
@@ -239,11 +224,6 @@ cudaError_t upload(T** dst, const std::vector<T>& src, int64_t* bytes) {
   return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-hmat_status cuda_status(cudaError_t e) {
-  if (e == cudaSuccess) return HMAT_OK;
-  if (e == cudaErrorMemoryAllocation) return HMAT_ENOMEM;
-  return HMAT_ECUDA;
-}
 
 
 // Mixed-precision copies of a loaded HMatrix (HMAT_LOAD_MIXED): the near blocks as
@@ -369,80 +349,20 @@ hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const
   h->device_bytes += n32 * (int64_t)sizeof(float);
   if ((e = launch_to_f32(h->arena + basis_begin, h->arena32, h->arena_values - basis_begin, 0)) != cudaSuccess)
     return cuda_status(e);
-  if ((e = cudaMalloc((void**)&h->wmax, sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
-  // the far chain is a chain of short dependent launches beside the long near-field launch:
-  // the highest priority lets its CTAs take SMs as soon as near-field CTAs retire
-  int prio_lo = 0, prio_hi = 0;
-  if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess) return cuda_status(e);
-  if ((e = cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_hi)) != cudaSuccess)
-    return cuda_status(e);
-  if ((e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
-  if ((e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_status(e);
   h->has_mixed = true;
   return HMAT_OK;
 }
 
-// Workspaces of the mixed mode for q columns: W split tiles and FP32 skeleton weights.
-hmat_status reserve_mixed(Handle* h, int64_t q, int n_t, int n_ct) {
-  const int64_t split = h->total_kchunks * n_ct * (int64_t)n_t * 256;
-  if (split > h->wsplit_cap) {
-    uint8_t* p = nullptr;
-    cudaError_t e = cudaMalloc((void**)&p, (size_t)std::max<int64_t>(split, 256));
-    if (e != cudaSuccess) { cudaGetLastError(); return cuda_status(e); }
-    cudaDeviceSynchronize();
-    cudaFree(h->wsplit);
-    h->device_bytes += split - h->wsplit_cap;
-    h->wsplit = p;
-    h->wsplit_cap = split;
-  }
-  if (q > h->q32_cap) {
-    const size_t n = (size_t)std::max<int64_t>(h->sum_rank, 1) * (size_t)q * sizeof(float);
-    const size_t nw = (size_t)std::max<int64_t>(h->n_points, 1) * (size_t)q * sizeof(float);
-    float *ws = nullptr, *us = nullptr, *w32 = nullptr;
-    cudaError_t e = cudaMalloc((void**)&ws, n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&us, n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&w32, nw);
-    if (e != cudaSuccess) { cudaFree(ws); cudaFree(us); cudaGetLastError(); return cuda_status(e); }
-    cudaDeviceSynchronize();
-    cudaFree(h->ws32);
-    cudaFree(h->us32);
-    cudaFree(h->w32);
-    const int64_t old = (2 * std::max<int64_t>(h->sum_rank, 1) + std::max<int64_t>(h->n_points, 1)) * h->q32_cap;
-    h->device_bytes += (int64_t)(2 * n + nw) - old * (int64_t)sizeof(float);
-    h->ws32 = ws;
-    h->us32 = us;
-    h->w32 = w32;
-    h->q32_cap = q;
-  }
-  return HMAT_OK;
-}
-
-// Event records around one launch of the evaluation when profiling is on.
-bool prof_begin(Handle* h, int32_t kind, cudaStream_t s, Handle::ProfRecord* rec) {
-  rec->kind = kind;
-  if (!h->profiling) return true;
-  for (cudaEvent_t* ev : {&rec->start, &rec->stop}) {
-    if (!h->event_pool.empty()) {
-      *ev = h->event_pool.back();
-      h->event_pool.pop_back();
-    } else if (cudaEventCreate(ev) != cudaSuccess) {
-      return false;
-    }
-  }
-  return cudaEventRecord(rec->start, s) == cudaSuccess;
-}
-
-bool prof_end(Handle* h, const Handle::ProfRecord& rec, cudaStream_t s) {
-  if (!h->profiling) return true;
-  if (cudaEventRecord(rec.stop, s) != cudaSuccess) return false;
-  h->prof.push_back(rec);
-  return true;
-}
-
 }  // namespace
 
 namespace hmat {
+
+hmat_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return HMAT_OK;
+  if (e == cudaErrorMemoryAllocation) return HMAT_ENOMEM;
+  return HMAT_ECUDA;
+}
 
 hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flags, hmat_handle** out) {
   *out = nullptr;
@@ -710,6 +630,13 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
       return ms;
     }
   }
+  {
+    hmat_status cs = ctx_create(*h, &h->ctx);
+    if (cs != HMAT_OK) {
+      free_device(h.get());
+      return cs;
+    }
+  }
   *out = h.release();
   return HMAT_OK;
 }
@@ -737,177 +664,6 @@ extern "C" hmat_status hmat_structure(hmat_t h, int64_t* perm, int32_t* rank, in
   return HMAT_OK;
 }
 
-extern "C" hmat_status hmat_reserve(hmat_t h, int64_t q_max) {
-  if (!h || q_max < 0) return HMAT_EINVAL;
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
-  if (dev != h->device) return HMAT_EINVAL;
-  if (q_max <= h->q_cap) return HMAT_OK;
-  const size_t n = (size_t)std::max<int64_t>(h->sum_rank, 1) * (size_t)q_max * sizeof(double);
-  double *ws = nullptr, *us = nullptr;
-  cudaError_t e = cudaMalloc((void**)&ws, n);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&us, n);
-  if (e != cudaSuccess) {
-    cudaFree(ws);
-    cudaGetLastError();
-    return cuda_status(e);
-  }
-  cudaDeviceSynchronize();  // earlier evaluations may still use the old workspace
-  cudaFree(h->ws);
-  cudaFree(h->us);
-  h->device_bytes += (int64_t)(2 * n) - h->ws_bytes;
-  h->ws_bytes = (int64_t)(2 * n);
-  h->ws = ws;
-  h->us = us;
-  h->q_cap = q_max;
-  return HMAT_OK;
-}
-
-extern "C" hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
-  if (!h || q < 0) return HMAT_EINVAL;
-  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
-  if (mode == HMAT_MODE_MIXED && !h->has_mixed) return HMAT_EUNSUPPORTED;
-  if (q == 0 || h->n_points == 0) return HMAT_OK;
-  if (!W || !Y || W == Y) return HMAT_EINVAL;
-  const char* w0 = (const char*)W;
-  const char* y0 = (const char*)Y;
-  const int64_t bytes = h->n_points * q * (int64_t)sizeof(double);
-  if (w0 < y0 + bytes && y0 < w0 + bytes) return HMAT_EINVAL;  // W and Y overlap
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
-  if (dev != h->device) return HMAT_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
-  Handle::ProfRecord rec{};
-
-  if (mode == HMAT_MODE_MIXED) {
-    // near field on the tensor cores, W split first; far field as FP32 grouped GEMMs
-    const int n_t = (int)std::min<int64_t>(128, (q + 15) / 16 * 16);
-    const int64_t n_ct64 = (q + n_t - 1) / n_t;
-    if (n_ct64 > 65535) return HMAT_EUNSUPPORTED;
-    const int n_ct = (int)n_ct64;
-    hmat_status st = reserve_mixed(h, q, n_t, n_ct);
-    if (st != HMAT_OK) return st;
-    // split W (the tensor-core tiles and an FP32 tree-order copy), then run the far chain
-    // (up, coupling, down to the leaves' skeletons) on the auxiliary stream beside the
-    // tensor-core near field; the leaf step of the downward pass adds into Y, so it
-    // follows both on the caller's stream
-    if (!prof_begin(h, HMAT_PHASE_SPLIT, s, &rec)) return HMAT_ECUDA;
-    cudaError_t e = launch_w_split(h->tc, h->total_kchunks, W, h->n_points * q, h->perm, q, n_t, n_ct, h->wmax,
-                                   h->wsplit, h->w32, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (!prof_end(h, rec, s)) return HMAT_ECUDA;
-    if (cudaEventRecord(h->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(h->aux, h->ev_fork, 0) != cudaSuccess)
-      return HMAT_ECUDA;
-    auto far_launch = [&](const Phase& ph, cudaStream_t strm) -> hmat_status {
-      const float* X = ph.x == MAT_USER ? h->w32 : (ph.x == MAT_SKEL_W ? h->ws32 : h->us32);
-      void* Yd = ph.y == MAT_USER ? (void*)Y : (ph.y == MAT_SKEL_W ? (void*)h->ws32 : (void*)h->us32);
-      const int64_t* xm = ph.xmap == XMAP_FAR ? h->far_rows : nullptr;  // the FP32 copy of W is in tree order
-      const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
-      if (!prof_begin(h, (int32_t)ph.kind, strm, &rec)) return HMAT_ECUDA;
-      e = launch_f32_phase(*h, ph, X, xm, Yd, ph.y == MAT_USER, ym, q, strm);
-      if (e != cudaSuccess) return cuda_status(e);
-      return prof_end(h, rec, strm) ? HMAT_OK : HMAT_ECUDA;
-    };
-    for (const Phase& ph : h->phases) {
-      if (ph.kind == PH_NEAR || ph.kind == PH_DOWN_LEAF) continue;
-      if ((st = far_launch(ph, h->aux)) != HMAT_OK) return st;
-    }
-    if (cudaEventRecord(h->ev_join, h->aux) != cudaSuccess) return HMAT_ECUDA;
-    if (!prof_begin(h, HMAT_PHASE_NEAR, s, &rec)) return HMAT_ECUDA;
-    e = launch_near_tc(h->tc, h->n_tc_work, h->wsplit, h->wmax, h->perm, Y, q, n_t, n_ct, h->status, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (!prof_end(h, rec, s)) return HMAT_ECUDA;
-    if (cudaStreamWaitEvent(s, h->ev_join, 0) != cudaSuccess) return HMAT_ECUDA;
-    for (const Phase& ph : h->phases)
-      if (ph.kind == PH_DOWN_LEAF && (st = far_launch(ph, s)) != HMAT_OK) return st;
-    return HMAT_OK;
-  }
-
-  if (q > h->q_cap) {
-    hmat_status st = hmat_reserve(h, q);
-    if (st != HMAT_OK) return st;
-  }
-  for (const Phase& ph : h->phases) {
-    const double* X = ph.x == MAT_USER ? W : (ph.x == MAT_SKEL_W ? h->ws : h->us);
-    double* Yd = ph.y == MAT_USER ? Y : (ph.y == MAT_SKEL_W ? h->ws : h->us);
-    const int64_t* xm = phase_x_map(*h, ph);
-    const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
-    if (!prof_begin(h, (int32_t)ph.kind, s, &rec)) return HMAT_ECUDA;
-    cudaError_t e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (!prof_end(h, rec, s)) return HMAT_ECUDA;
-  }
-  return HMAT_OK;
-}
-
-extern "C" hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
-  if (!h || q < 0) return HMAT_EINVAL;
-  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
-  if (q == 0 || h->n_points == 0) return HMAT_OK;
-  if (!W || !Y) return HMAT_EINVAL;
-  const int64_t values = h->n_points * q;
-  if (values > h->host_cap) {
-    double *w = nullptr, *y = nullptr;
-    cudaError_t e = cudaMalloc((void**)&w, (size_t)values * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&y, (size_t)values * sizeof(double));
-    if (e != cudaSuccess) {
-      cudaFree(w);
-      cudaGetLastError();
-      return cuda_status(e);
-    }
-    cudaDeviceSynchronize();
-    cudaFree(h->host_w);
-    cudaFree(h->host_y);
-    h->device_bytes += 2 * (values - h->host_cap) * (int64_t)sizeof(double);
-    h->host_w = w;
-    h->host_y = y;
-    h->host_cap = values;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = (size_t)values * sizeof(double);
-  cudaError_t e = cudaMemcpyAsync(h->host_w, W, bytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_status(e);
-  hmat_status st = hmat_eval(h, h->host_w, h->host_y, q, mode, stream);
-  if (st != HMAT_OK) return st;
-  e = cudaMemcpyAsync(Y, h->host_y, bytes, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return cuda_status(e);
-}
-
-extern "C" hmat_status hmat_profile(hmat_t h, int enable) {
-  if (!h) return HMAT_EINVAL;
-  for (auto& r : h->prof) {
-    h->event_pool.push_back(r.start);
-    h->event_pool.push_back(r.stop);
-  }
-  h->prof.clear();
-  h->profiling = enable != 0;
-  return HMAT_OK;
-}
-
-extern "C" hmat_status hmat_phase_times(hmat_t h, double* ms, int64_t* launches, int n) {
-  if (!h || n < 0 || (n > 0 && (!ms || !launches))) return HMAT_EINVAL;
-  for (int k = 0; k < n; ++k) {
-    ms[k] = 0.0;
-    launches[k] = 0;
-  }
-  hmat_status st = HMAT_OK;
-  for (auto& r : h->prof) {
-    float t = 0.0f;
-    cudaError_t e = cudaEventSynchronize(r.stop);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.start, r.stop);
-    if (e != cudaSuccess) st = HMAT_ECUDA;
-    if (r.kind < n) {
-      ms[r.kind] += t;
-      launches[r.kind] += 1;
-    }
-    h->event_pool.push_back(r.start);
-    h->event_pool.push_back(r.stop);
-  }
-  h->prof.clear();
-  return st;
-}
-
 extern "C" hmat_status hmat_status_poll(hmat_t h, void* stream) {
   if (!h) return HMAT_EINVAL;
   int word = 0;
@@ -920,8 +676,9 @@ extern "C" hmat_status hmat_status_poll(hmat_t h, void* stream) {
 
 extern "C" hmat_status hmat_info(hmat_t h, int64_t* out, int n_out) {
   if (!h || !out || n_out < 0) return HMAT_EINVAL;
+  const int64_t held = h->device_bytes + (h->ctx ? h->ctx->block_bytes + 16 * h->ctx->host_cap : 0);
   const int64_t vals[9] = {h->n_points, h->levels, h->n_near, h->n_far, h->near_values,
-                           h->basis_values, h->coupling_values, h->sum_rank, h->device_bytes};
+                           h->basis_values, h->coupling_values, h->sum_rank, held};
   for (int i = 0; i < n_out && i < 9; ++i) out[i] = vals[i];
   return HMAT_OK;
 }

@@ -1,0 +1,310 @@
+// Evaluation driver: Y = K~ W for one loaded HMatrix (Section 2.1, "Evaluation").
+//
+// FP64 mode: the phases in order (near field, upward leaves, upward transfers level by
+// level, coupling, downward transfers level by level, downward leaves), each one
+// grouped-GEMM launch per row-tile size on the caller's stream.
+//
+// Mixed mode: W is split into FP16 hi/lo tensor-core tiles (and an FP32 tree-order
+// copy); the near field runs on the tensor cores on the caller's stream while the far
+// chain (upward pass, coupling, downward transfers) runs in FP32 on a high-priority
+// side stream; the downward leaf step, which adds into Y, follows both.
+//
+// The per-evaluation state lives in an EvalContext, so several evaluations of the
+// same HMatrix can be in flight at once (batches, the server).
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "hmat_internal.h"
+
+namespace hmat {
+namespace {
+
+constexpr int64_t kAlignBytes = 256;
+
+int64_t align_up(int64_t x) { return (x + kAlignBytes - 1) / kAlignBytes * kAlignBytes; }
+
+// Columns of W per tensor-core CTA and the number of column tiles for q.
+void mixed_tiles(int64_t q, int* n_t, int64_t* n_ct) {
+  *n_t = (int)std::min<int64_t>(128, (q + 15) / 16 * 16);
+  *n_ct = (q + *n_t - 1) / *n_t;
+}
+
+// Event records around one launch of the evaluation when the handle is profiling.
+bool prof_begin(Handle* h, int32_t kind, cudaStream_t s, Handle::ProfRecord* rec) {
+  rec->kind = kind;
+  if (!h->profiling) return true;
+  for (cudaEvent_t* ev : {&rec->start, &rec->stop}) {
+    if (!h->event_pool.empty()) {
+      *ev = h->event_pool.back();
+      h->event_pool.pop_back();
+    } else if (cudaEventCreate(ev) != cudaSuccess) {
+      return false;
+    }
+  }
+  return cudaEventRecord(rec->start, s) == cudaSuccess;
+}
+
+bool prof_end(Handle* h, const Handle::ProfRecord& rec, cudaStream_t s) {
+  if (!h->profiling) return true;
+  if (cudaEventRecord(rec.stop, s) != cudaSuccess) return false;
+  h->prof.push_back(rec);
+  return true;
+}
+
+hmat_status check_call(const Handle* h, const double* W, const double* Y, int64_t q, int mode) {
+  if (!h || q < 0) return HMAT_EINVAL;
+  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
+  if (mode == HMAT_MODE_MIXED && !h->has_mixed) return HMAT_EUNSUPPORTED;
+  if (q == 0 || h->n_points == 0) return HMAT_OK;
+  if (!W || !Y || W == Y) return HMAT_EINVAL;
+  const char* w0 = (const char*)W;
+  const char* y0 = (const char*)Y;
+  const int64_t bytes = h->n_points * q * (int64_t)sizeof(double);
+  if (w0 < y0 + bytes && y0 < w0 + bytes) return HMAT_EINVAL;  // W and Y overlap
+  if (mode == HMAT_MODE_MIXED) {
+    int n_t;
+    int64_t n_ct;
+    mixed_tiles(q, &n_t, &n_ct);
+    if (n_ct > 65535) return HMAT_EUNSUPPORTED;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
+  if (dev != h->device) return HMAT_EINVAL;
+  return HMAT_OK;
+}
+
+}  // namespace
+
+hmat_status ctx_create(const Handle& h, EvalContext** out) {
+  *out = nullptr;
+  EvalContext* c = new (std::nothrow) EvalContext();
+  if (!c) return HMAT_ENOMEM;
+  if (h.has_mixed) {
+    // the far chain is a chain of short dependent launches beside the long near-field
+    // launch: the highest priority lets its CTAs take SMs as soon as near-field CTAs retire
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      ctx_destroy(c);
+      return cuda_status(e);
+    }
+  }
+  *out = c;
+  return HMAT_OK;
+}
+
+void ctx_destroy(EvalContext* c) {
+  if (!c) return;
+  if (c->aux) cudaStreamSynchronize(c->aux);
+  cudaFree(c->block);
+  cudaFree(c->host_w);
+  cudaFree(c->host_y);
+  if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  delete c;
+}
+
+int64_t ctx_bytes(const Handle& h, int64_t q, int mode) {
+  const int64_t r = std::max<int64_t>(h.sum_rank, 1);
+  if (mode == HMAT_MODE_MIXED) {
+    int n_t;
+    int64_t n_ct;
+    mixed_tiles(q, &n_t, &n_ct);
+    return align_up(sizeof(unsigned long long)) + align_up(h.total_kchunks * n_ct * (int64_t)n_t * 256) +
+           align_up(std::max<int64_t>(h.n_points, 1) * q * 4) + 2 * align_up(r * q * 4);
+  }
+  return 2 * align_up(r * q * 8);
+}
+
+void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* base) {
+  const int64_t r = std::max<int64_t>(h.sum_rank, 1);
+  uint8_t* p = base;
+  auto take = [&](int64_t bytes) {
+    uint8_t* x = p;
+    p += align_up(bytes);
+    return x;
+  };
+  c->ws = c->us = nullptr;
+  c->wmax = nullptr;
+  c->wsplit = nullptr;
+  c->w32 = c->ws32 = c->us32 = nullptr;
+  if (mode == HMAT_MODE_MIXED) {
+    int n_t;
+    int64_t n_ct;
+    mixed_tiles(q, &n_t, &n_ct);
+    c->wmax = (unsigned long long*)take(sizeof(unsigned long long));
+    c->wsplit = take(h.total_kchunks * n_ct * (int64_t)n_t * 256);
+    c->w32 = (float*)take(std::max<int64_t>(h.n_points, 1) * q * 4);
+    c->ws32 = (float*)take(r * q * 4);
+    c->us32 = (float*)take(r * q * 4);
+  } else {
+    c->ws = (double*)take(r * q * 8);
+    c->us = (double*)take(r * q * 8);
+  }
+}
+
+hmat_status ctx_reserve(const Handle& h, EvalContext* c, int64_t q, int mode) {
+  const int64_t need = ctx_bytes(h, q, mode);
+  if (need > c->block_bytes) {
+    uint8_t* p = nullptr;
+    cudaError_t e = cudaMalloc((void**)&p, (size_t)need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+    cudaDeviceSynchronize();  // earlier evaluations may still use the old block
+    cudaFree(c->block);
+    c->block = p;
+    c->block_bytes = need;
+  }
+  ctx_bind(h, c, q, mode, c->block);
+  return HMAT_OK;
+}
+
+hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int64_t q, int mode, cudaStream_t s) {
+  Handle::ProfRecord rec{};
+  hmat_status st = HMAT_OK;
+  cudaError_t e = cudaSuccess;
+  if (mode == HMAT_MODE_MIXED) {
+    int n_t;
+    int64_t n_ct;
+    mixed_tiles(q, &n_t, &n_ct);
+    if (!prof_begin(h, HMAT_PHASE_SPLIT, s, &rec)) return HMAT_ECUDA;
+    e = launch_w_split(h->tc, h->total_kchunks, W, h->n_points * q, h->perm, q, n_t, (int)n_ct, c->wmax, c->wsplit,
+                       c->w32, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!prof_end(h, rec, s)) return HMAT_ECUDA;
+    if (cudaEventRecord(c->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->ev_fork, 0) != cudaSuccess)
+      return HMAT_ECUDA;
+    auto far_launch = [&](const Phase& ph, cudaStream_t strm) -> hmat_status {
+      const float* X = ph.x == MAT_USER ? c->w32 : (ph.x == MAT_SKEL_W ? c->ws32 : c->us32);
+      void* Yd = ph.y == MAT_USER ? (void*)Y : (ph.y == MAT_SKEL_W ? (void*)c->ws32 : (void*)c->us32);
+      const int64_t* xm = ph.xmap == XMAP_FAR ? h->far_rows : nullptr;  // the FP32 copy of W is in tree order
+      const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
+      if (!prof_begin(h, (int32_t)ph.kind, strm, &rec)) return HMAT_ECUDA;
+      e = launch_f32_phase(*h, ph, X, xm, Yd, ph.y == MAT_USER, ym, q, strm);
+      if (e != cudaSuccess) return cuda_status(e);
+      return prof_end(h, rec, strm) ? HMAT_OK : HMAT_ECUDA;
+    };
+    for (const Phase& ph : h->phases) {
+      if (ph.kind == PH_NEAR || ph.kind == PH_DOWN_LEAF) continue;
+      if ((st = far_launch(ph, c->aux)) != HMAT_OK) return st;
+    }
+    if (cudaEventRecord(c->ev_join, c->aux) != cudaSuccess) return HMAT_ECUDA;
+    if (!prof_begin(h, HMAT_PHASE_NEAR, s, &rec)) return HMAT_ECUDA;
+    e = launch_near_tc(h->tc, h->n_tc_work, c->wsplit, c->wmax, h->perm, Y, q, n_t, (int)n_ct, h->status, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!prof_end(h, rec, s)) return HMAT_ECUDA;
+    if (cudaStreamWaitEvent(s, c->ev_join, 0) != cudaSuccess) return HMAT_ECUDA;
+    for (const Phase& ph : h->phases)
+      if (ph.kind == PH_DOWN_LEAF && (st = far_launch(ph, s)) != HMAT_OK) return st;
+    return HMAT_OK;
+  }
+  for (const Phase& ph : h->phases) {
+    const double* X = ph.x == MAT_USER ? W : (ph.x == MAT_SKEL_W ? c->ws : c->us);
+    double* Yd = ph.y == MAT_USER ? Y : (ph.y == MAT_SKEL_W ? c->ws : c->us);
+    const int64_t* xm = phase_x_map(*h, ph);
+    const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
+    if (!prof_begin(h, (int32_t)ph.kind, s, &rec)) return HMAT_ECUDA;
+    e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!prof_end(h, rec, s)) return HMAT_ECUDA;
+  }
+  return HMAT_OK;
+}
+
+}  // namespace hmat
+
+using namespace hmat;
+
+extern "C" hmat_status hmat_reserve(hmat_t h, int64_t q_max) {
+  if (!h || q_max < 0) return HMAT_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
+  if (dev != h->device) return HMAT_EINVAL;
+  if (q_max == 0) return HMAT_OK;
+  const int mode = h->has_mixed && ctx_bytes(*h, q_max, HMAT_MODE_MIXED) > ctx_bytes(*h, q_max, HMAT_MODE_FP64)
+                       ? HMAT_MODE_MIXED
+                       : HMAT_MODE_FP64;
+  return ctx_reserve(*h, h->ctx, q_max, mode);
+}
+
+extern "C" hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
+  hmat_status st = check_call(h, W, Y, q, mode);
+  if (st != HMAT_OK || q == 0 || h->n_points == 0) return st;
+  if ((st = ctx_reserve(*h, h->ctx, q, mode)) != HMAT_OK) return st;
+  return eval_impl(h, h->ctx, W, Y, q, mode, (cudaStream_t)stream);
+}
+
+extern "C" hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
+  if (!h || q < 0) return HMAT_EINVAL;
+  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
+  if (q == 0 || h->n_points == 0) return HMAT_OK;
+  if (!W || !Y) return HMAT_EINVAL;
+  EvalContext* c = h->ctx;
+  const int64_t values = h->n_points * q;
+  if (values > c->host_cap) {
+    double *w = nullptr, *y = nullptr;
+    cudaError_t e = cudaMalloc((void**)&w, (size_t)values * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&y, (size_t)values * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaFree(w);
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+    cudaDeviceSynchronize();
+    cudaFree(c->host_w);
+    cudaFree(c->host_y);
+    c->host_w = w;
+    c->host_y = y;
+    c->host_cap = values;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)values * sizeof(double);
+  cudaError_t e = cudaMemcpyAsync(c->host_w, W, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  hmat_status st = hmat_eval(h, c->host_w, c->host_y, q, mode, stream);
+  if (st != HMAT_OK) return st;
+  e = cudaMemcpyAsync(Y, c->host_y, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e);
+}
+
+extern "C" hmat_status hmat_profile(hmat_t h, int enable) {
+  if (!h) return HMAT_EINVAL;
+  for (auto& r : h->prof) {
+    h->event_pool.push_back(r.start);
+    h->event_pool.push_back(r.stop);
+  }
+  h->prof.clear();
+  h->profiling = enable != 0;
+  return HMAT_OK;
+}
+
+extern "C" hmat_status hmat_phase_times(hmat_t h, double* ms, int64_t* launches, int n) {
+  if (!h || n < 0 || (n > 0 && (!ms || !launches))) return HMAT_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  hmat_status st = HMAT_OK;
+  for (auto& r : h->prof) {
+    float t = 0.0f;
+    cudaError_t e = cudaEventSynchronize(r.stop);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.start, r.stop);
+    if (e != cudaSuccess) st = HMAT_ECUDA;
+    if (r.kind < n) {
+      ms[r.kind] += t;
+      launches[r.kind] += 1;
+    }
+    h->event_pool.push_back(r.start);
+    h->event_pool.push_back(r.stop);
+  }
+  h->prof.clear();
+  return st;
+}

@@ -111,6 +111,27 @@ struct TcNear {
   const int32_t* chunk_c;      // per global k-chunk: its chunk index within the leaf
 };
 
+// The state one evaluation needs besides the read-only HMatrix: the workspaces
+// (carved from one device block for a given q and mode) and, for the mixed mode, a
+// side stream with its fork/join events. A handle owns a default context; a batch
+// or a server owns one per evaluation it keeps in flight.
+struct EvalContext {
+  uint8_t* block = nullptr;      // own workspace block (cudaMalloc); nullptr when bound to external memory
+  int64_t block_bytes = 0;
+  double* ws = nullptr;          // FP64: skeleton weights w and potentials u (sum of ranks x q)
+  double* us = nullptr;
+  unsigned long long* wmax = nullptr;  // mixed: max |W| (FP64 bits)
+  uint8_t* wsplit = nullptr;     // mixed: W as FP16 hi/lo operand tiles
+  float* w32 = nullptr;          // mixed: FP32 copy of W in tree order
+  float* ws32 = nullptr;         // mixed: FP32 skeleton workspaces
+  float* us32 = nullptr;
+  double* host_w = nullptr;      // device copies of W / Y for hmat_eval_host
+  double* host_y = nullptr;
+  int64_t host_cap = 0;          // values
+  cudaStream_t aux = nullptr;    // mixed: the far chain runs here, beside the near field
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+};
+
 struct Handle {
   int device = -1;
   int64_t n_points = 0;
@@ -135,13 +156,6 @@ struct Handle {
   GemmEntry* entries = nullptr;
   GemmTile* tiles = nullptr;
   int* status = nullptr;         // device status word (hmat_status of the first error)
-  double* ws = nullptr;          // skeleton weights w (sum_rank x q_cap)
-  double* us = nullptr;          // skeleton potentials u (sum_rank x q_cap)
-  int64_t q_cap = 0;
-  int64_t ws_bytes = 0;
-  double* host_w = nullptr;      // device copies of W / Y for hmat_eval_host
-  double* host_y = nullptr;
-  int64_t host_cap = 0;          // capacity of host_w / host_y in values
 
   // mixed precision (HMAT_LOAD_MIXED)
   bool has_mixed = false;
@@ -153,15 +167,8 @@ struct Handle {
   int64_t total_kchunks = 0;     // sum over leaves of ceil(n / 64)
   float* arena32 = nullptr;      // FP32 copy of the bases and coupling blocks
   int64_t arena32_shift = 0;     // FP64-arena offset of arena32[0]
-  uint8_t* wsplit = nullptr;     // W as FP16 hi/lo operand tiles (per evaluation)
-  int64_t wsplit_cap = 0;        // bytes
-  float* w32 = nullptr;          // FP32 copy of W in tree order (mixed mode)
-  float* ws32 = nullptr;         // FP32 skeleton workspaces of the mixed mode
-  float* us32 = nullptr;
-  int64_t q32_cap = 0;
-  unsigned long long* wmax = nullptr;  // max |W| of the current evaluation (FP64 bits)
-  cudaStream_t aux = nullptr;    // the far chain of the mixed mode runs here, beside the near field
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
+  struct EvalContext* ctx = nullptr;  // the handle's own evaluation state (hmat_eval)
 
   // per-launch event timing (hmat_profile / hmat_phase_times)
   struct ProfRecord {
@@ -223,6 +230,16 @@ cudaError_t launch_near_tc(const TcNear& tc, int64_t n_work, const uint8_t* wspl
 // FP32 grouped GEMM of one far-field phase of the mixed mode (hmat_far32.cu).
 cudaError_t launch_f32_phase(const Handle& h, const Phase& ph, const float* X, const int64_t* x_map, void* Y,
                              bool y_is_f64, const int64_t* y_map, int64_t q, cudaStream_t stream);
+
+// Evaluation contexts (hmat_eval.cpp).
+hmat_status ctx_create(const Handle& h, EvalContext** out);
+void ctx_destroy(EvalContext* c);
+int64_t ctx_bytes(const Handle& h, int64_t q, int mode);          // workspace bytes of one evaluation
+void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* base);  // carve the workspaces
+hmat_status ctx_reserve(const Handle& h, EvalContext* c, int64_t q, int mode);      // grow the own block
+// Enqueue Y = K~ W on `s` with the workspaces of `c` (bound for q and mode by the caller).
+hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int64_t q, int mode, cudaStream_t s);
+hmat_status cuda_status(cudaError_t e);
 
 // Launch the FP64 grouped GEMM of one phase on `stream`.
 cudaError_t launch_fp64_phase(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map,

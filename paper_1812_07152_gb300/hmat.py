@@ -111,6 +111,11 @@ def library() -> ctypes.CDLL:
         lib.hmat_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.hmat_phase_times.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), _c_i64p, ctypes.c_int]
         lib.hmat_measure_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
+        lib.hmat_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_void_p)]
+        lib.hmat_batch_eval.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p), _c_i64p, ctypes.c_void_p]
+        lib.hmat_batch_free.argtypes = [ctypes.c_void_p]
         lib.hmat_status_poll.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         lib.hmat_info.argtypes = [ctypes.c_void_p, _c_i64p, ctypes.c_int]
         lib.hmat_free.argtypes = [ctypes.c_void_p]
@@ -118,7 +123,7 @@ def library() -> ctypes.CDLL:
         lib.hmat_strerror.restype = ctypes.c_char_p
         for name in ("hmat_load", "hmat_build", "hmat_structure", "hmat_eval", "hmat_reserve", "hmat_status_poll",
                      "hmat_info", "hmat_free", "hmat_eval_host", "hmat_profile", "hmat_phase_times",
-                     "hmat_measure_fp64_peak"):
+                     "hmat_measure_fp64_peak", "hmat_batch_create", "hmat_batch_eval", "hmat_batch_free"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -273,6 +278,26 @@ def hmat_info(handle: int) -> dict:
 
 def hmat_free(handle: int) -> None:
     _check(library().hmat_free(handle), "hmat_free")
+
+
+def hmat_batch_create(handles: Sequence[int], mode: int = HMAT_MODE_FP64) -> int:
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    b = ctypes.c_void_p()
+    _check(library().hmat_batch_create(arr, len(handles), int(mode), ctypes.byref(b)), "hmat_batch_create")
+    return int(b.value)
+
+
+def hmat_batch_eval(batch: int, Ws, Ys, stream=None) -> None:
+    """Y[i] = K~_i W[i] for every member (torch CUDA tensors n_i x q_i), one graph launch."""
+    n = len(Ws)
+    w = (ctypes.c_void_p * n)(*[_ptr(x) for x in Ws])
+    y = (ctypes.c_void_p * n)(*[_ptr(x) for x in Ys])
+    q = (ctypes.c_int64 * n)(*[int(x.shape[1]) for x in Ws])
+    _check(library().hmat_batch_eval(batch, w, y, q, _stream(stream)), "hmat_batch_eval")
+
+
+def hmat_batch_free(batch: int) -> None:
+    _check(library().hmat_batch_free(batch), "hmat_batch_free")
 
 
 class DeviceHMatrix:
