@@ -279,6 +279,48 @@ hmat_status hmat_batch_eval(hmat_batch_t b, const double* const* W, double* cons
 hmat_status hmat_batch_free(hmat_batch_t b);
 
 /*
+ * Serving: a request loop over HMatrices kept resident on the device. Requests
+ * (a matrix, a host W of n x q, a host Y) are queued by hmat_server_submit and
+ * dispatched by a host thread: a request is admitted when one of `slots` CUDA
+ * streams is free and the device memory it needs (its workspaces and the device
+ * copies of W and Y) fits, with the memory of the requests in flight, within
+ * `memory_budget` bytes. Requests on the same matrix that wait together are run
+ * as one evaluation with their W columns side by side (up to `max_q` columns),
+ * which reads each stored block once for all of them (continuous batching);
+ * requests in different slots overlap on the device. Results are those of
+ * hmat_eval on each request alone: bitwise in FP64 mode (every column of Y
+ * depends only on the same column of W, summed in the same order), within the
+ * mode's accuracy in the mixed mode (W's power-of-two scale is taken over the
+ * merged columns). Workspace comes from a stream-ordered memory pool. Served
+ * handles must not be evaluated or profiled elsewhere while the server runs.
+ *
+ * hmat_server_submit - W and Y are pinned host buffers (cudaHostAlloc,
+ * cudaHostRegister) or device buffers, n x q row-major, valid until the request
+ * completes (pageable host memory: HMAT_EINVAL, as its copies would stall the
+ * dispatcher); *id identifies the request. Returns HMAT_ENOMEM when the request
+ * alone exceeds the memory budget, HMAT_EINVAL when q > max_q.
+ * hmat_server_wait - wait for request `id` (timeout_ms < 0: no limit); returns
+ * its status, HMAT_ETIMEOUT if it has not completed in time. A completed request
+ * is forgotten once waited on (waiting again: HMAT_EINVAL).
+ * hmat_server_stats - out[0] completed requests, out[1] p50 and out[2] p99
+ * latency in ms (submit to result in host memory), out[3] mean requests per
+ * evaluation, out[4] evaluations, out[5] peak device bytes in flight.
+ */
+typedef struct hmat_server* hmat_server_t;
+typedef struct {
+  int slots;                /* evaluations in flight at once (>= 1) */
+  int64_t memory_budget;    /* device bytes of the requests in flight (> 0) */
+  int64_t max_q;            /* columns of one merged evaluation (>= 1) */
+  int mode;                 /* HMAT_MODE_FP64 or HMAT_MODE_MIXED */
+} hmat_server_params;
+hmat_status hmat_server_create(const hmat_t* handles, int count, const hmat_server_params* params,
+                               hmat_server_t* out);
+hmat_status hmat_server_submit(hmat_server_t s, int matrix, const double* W, double* Y, int64_t q, int64_t* id);
+hmat_status hmat_server_wait(hmat_server_t s, int64_t id, int timeout_ms);
+hmat_status hmat_server_stats(hmat_server_t s, double* out, int n);
+hmat_status hmat_server_free(hmat_server_t s);
+
+/*
  * hmat_status_poll - synchronise `stream` and return the device status word
  * latched by the kernels since the last poll (HMAT_OK when nothing happened),
  * then clear it.

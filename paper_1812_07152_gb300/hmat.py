@@ -84,6 +84,11 @@ class HmatBuildParams(ctypes.Structure):
     ]
 
 
+class HmatServerParams(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("memory_budget", ctypes.c_int64), ("max_q", ctypes.c_int64),
+                ("mode", ctypes.c_int)]
+
+
 class HmatError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {hmat_strerror(status)} (status {status})")
@@ -116,6 +121,13 @@ def library() -> ctypes.CDLL:
         lib.hmat_batch_eval.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_void_p), _c_i64p, ctypes.c_void_p]
         lib.hmat_batch_free.argtypes = [ctypes.c_void_p]
+        lib.hmat_server_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                           ctypes.POINTER(HmatServerParams), ctypes.POINTER(ctypes.c_void_p)]
+        lib.hmat_server_submit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int64, _c_i64p]
+        lib.hmat_server_wait.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
+        lib.hmat_server_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        lib.hmat_server_free.argtypes = [ctypes.c_void_p]
         lib.hmat_status_poll.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         lib.hmat_info.argtypes = [ctypes.c_void_p, _c_i64p, ctypes.c_int]
         lib.hmat_free.argtypes = [ctypes.c_void_p]
@@ -123,7 +135,9 @@ def library() -> ctypes.CDLL:
         lib.hmat_strerror.restype = ctypes.c_char_p
         for name in ("hmat_load", "hmat_build", "hmat_structure", "hmat_eval", "hmat_reserve", "hmat_status_poll",
                      "hmat_info", "hmat_free", "hmat_eval_host", "hmat_profile", "hmat_phase_times",
-                     "hmat_measure_fp64_peak", "hmat_batch_create", "hmat_batch_eval", "hmat_batch_free"):
+                     "hmat_measure_fp64_peak", "hmat_batch_create", "hmat_batch_eval", "hmat_batch_free",
+                     "hmat_server_create", "hmat_server_submit", "hmat_server_wait", "hmat_server_stats",
+                     "hmat_server_free"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -298,6 +312,39 @@ def hmat_batch_eval(batch: int, Ws, Ys, stream=None) -> None:
 
 def hmat_batch_free(batch: int) -> None:
     _check(library().hmat_batch_free(batch), "hmat_batch_free")
+
+
+def hmat_server_create(handles: Sequence[int], slots: int, memory_budget: int, max_q: int,
+                       mode: int = HMAT_MODE_FP64) -> int:
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    p = HmatServerParams(int(slots), int(memory_budget), int(max_q), int(mode))
+    sv = ctypes.c_void_p()
+    _check(library().hmat_server_create(arr, len(handles), ctypes.byref(p), ctypes.byref(sv)), "hmat_server_create")
+    return int(sv.value)
+
+
+def hmat_server_submit(server: int, matrix: int, W, Y) -> int:
+    """Queue Y = K~_matrix W; W and Y are pinned CPU (or CUDA) tensors of n x q. Returns the request id."""
+    rid = ctypes.c_int64()
+    _check(library().hmat_server_submit(server, int(matrix), _ptr(W), _ptr(Y), int(W.shape[1]), ctypes.byref(rid)),
+           "hmat_server_submit")
+    return int(rid.value)
+
+
+def hmat_server_wait(server: int, request: int, timeout_ms: int = -1) -> int:
+    """Status of a request once it has completed (HMAT_ETIMEOUT if not within timeout_ms)."""
+    return int(library().hmat_server_wait(server, int(request), int(timeout_ms)))
+
+
+def hmat_server_stats(server: int) -> dict:
+    out = (ctypes.c_double * 6)()
+    _check(library().hmat_server_stats(server, out, 6), "hmat_server_stats")
+    keys = ("completed", "p50_ms", "p99_ms", "requests_per_evaluation", "evaluations", "peak_bytes")
+    return dict(zip(keys, [float(v) for v in out]))
+
+
+def hmat_server_free(server: int) -> None:
+    _check(library().hmat_server_free(server), "hmat_server_free")
 
 
 class DeviceHMatrix:
