@@ -44,6 +44,11 @@ def parse_args():
     ap.add_argument("--cpu-baseline", choices=["auto", "off"], default="auto")
     ap.add_argument("--mixed", choices=["on", "off"], default="on",
                     help="also time the mixed-precision tensor-core mode on the same HMatrix")
+    ap.add_argument("--batch", choices=["on", "off"], default="on",
+                    help="also time the batched mode: 64 HMatrices of uneven N, d, kernel, leaf size and q")
+    ap.add_argument("--serve", choices=["short", "full", "off"], default="short",
+                    help="also run the serving mode: a Poisson request stream on resident HMatrices "
+                         "(short: 4 matrices N = 16K..128K, 6 s; full: 8 matrices N = 16K..1M, 2000 req/s, 60 s)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
     return ap.parse_args()
 
@@ -276,6 +281,10 @@ def run_gpu(args, dist: Dist) -> None:
         line["mixed"] = mixed
     dev.close()
 
+    if args.batch == "on":
+        line["batch"] = run_batch(args, dist)
+    if args.serve != "off":
+        line["serving"] = run_serving(args, dist)
     if dist.rank == 0 and dist.world == 1 and args.cpu_baseline == "auto":
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     if dist.rank == 0:
@@ -328,6 +337,112 @@ def run_mixed(args, dev, W, Y64, q, info, stream, dist) -> dict:
             "error_vs_fp64": err, "dtype": "f16 hi+lo split, f32 accumulate",
             "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
             "gpu_launches": sum(c for _, c in phases.values()), "roofline": roof}
+
+
+def run_batch(args, dist) -> dict:
+    """Batched mode: 64 independent HMatrices (N log-uniform in [1024, 32768], d 3/8, Gaussian / inverse
+    multiquadric, leaf 64-256, tol 1e-5, q uniform in 1..64) evaluated in one CUDA-graph launch, against the
+    same evaluations issued one hmat_eval at a time."""
+    import torch
+    import paper_1812_07152_gb300 as hp
+    from workloads import batch_workloads, make_points, normal_rhs
+    ws = batch_workloads(64)
+    t0 = time.perf_counter()
+    handles = [hp.hmat_build(make_points(w), flags=hp.HMAT_LOAD_MIXED, **build_params(w)) for w in ws]
+    t_build = time.perf_counter() - t0
+    Ws = [torch.from_numpy(normal_rhs(w.n, w.q, w.rhs_seed)).cuda() for w in ws]
+    Ys = [torch.empty_like(W) for W in Ws]
+    cols = sum(w.q for w in ws)
+    stream = torch.cuda.current_stream()
+    out = {"matrices": len(ws), "columns_per_step": cols, "n_total": sum(w.n for w in ws),
+           "inspector_s": round(t_build, 2), "unit": "cols/s"}
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    for name, mode in (("fp64", hp.HMAT_MODE_FP64), ("mixed", hp.HMAT_MODE_MIXED)):
+        b = hp.hmat_batch_create(handles, mode)
+        ms_graph = dist.max(timed(lambda: hp.hmat_batch_eval(b, Ws, Ys, stream)))
+        ms_loop = dist.max(timed(lambda: [hp.hmat_eval(h, W, Y, W.shape[1], mode, stream)
+                                          for h, W, Y in zip(handles, Ws, Ys)]))
+        hp.hmat_batch_free(b)
+        out[name] = {"value": round(dist.world * cols / (ms_graph / 1e3), 1), "ms_per_step": round(ms_graph, 4),
+                     "one_call_per_matrix_value": round(dist.world * cols / (ms_loop / 1e3), 1),
+                     "one_call_per_matrix_ms": round(ms_loop, 4)}
+    for h in handles:
+        hp.hmat_free(h)
+    return out
+
+
+def run_serving(args, dist) -> dict:
+    """Serving mode: resident HMatrices (d = 3 uniform points, Gaussian h = 0.5, tol 1e-6, leaf 256), a Poisson
+    stream of requests of q uniform in 1..256 on a random matrix, mixed precision, memory-bounded admission and
+    continuous batching; p50/p99 latency from submit to the result in pinned host memory."""
+    import numpy as np
+    import torch
+    import paper_1812_07152_gb300 as hp
+    from workloads import make_points, serving_workloads
+    if args.serve == "full":
+        ws, rate, seconds = serving_workloads(), 2000.0, 60.0
+    else:
+        ws, rate, seconds = serving_workloads((16384, 32768, 65536, 131072)), 1000.0, 6.0
+    t0 = time.perf_counter()
+    handles = [hp.hmat_build(make_points(w), flags=hp.HMAT_LOAD_MIXED, **build_params(w)) for w in ws]
+    t_build = time.perf_counter() - t0
+    q_max = 256
+    rng = np.random.default_rng(7)
+    # one pinned W per matrix (read-only, shared by its requests) and a ring of pinned Y buffers
+    Wp = [torch.from_numpy(rng.standard_normal((w.n, q_max))).pin_memory() for w in ws]
+    ring = 16
+    Yp = [[torch.empty((w.n, q_max), dtype=torch.float64).pin_memory() for _ in range(ring)] for w in ws]
+    budget = 48 << 30
+    sv = hp.hmat_server_create(handles, slots=4, memory_budget=budget, max_q=4 * q_max, mode=hp.HMAT_MODE_MIXED)
+    ring_ids = [[None] * ring for _ in ws]
+    ring_pos = [0] * len(ws)
+    t_start = time.perf_counter()
+    t_next = t_start
+    submitted = cols = 0
+    while True:
+        t_next += rng.exponential(1.0 / rate)
+        if t_next - t_start > seconds:
+            break
+        now = time.perf_counter()
+        if t_next > now:
+            time.sleep(t_next - now)
+        m = int(rng.integers(0, len(ws)))
+        q = int(rng.integers(1, q_max + 1))
+        k = ring_pos[m]
+        ring_pos[m] = (k + 1) % ring
+        if ring_ids[m][k] is not None:  # the ring slot's previous request must be done before its Y is reused
+            hp.hmat_server_wait(sv, ring_ids[m][k])
+        ring_ids[m][k] = hp.hmat_server_submit(sv, m, Wp[m][:, :q], Yp[m][k][:, :q])
+        submitted += 1
+        cols += q
+    for ids in ring_ids:
+        for rid in ids:
+            if rid is not None:
+                hp.hmat_server_wait(sv, rid)
+    elapsed = time.perf_counter() - t_start
+    st = hp.hmat_server_stats(sv)
+    hp.hmat_server_free(sv)
+    for h in handles:
+        hp.hmat_free(h)
+    return {"matrices": [w.n for w in ws], "offered_req_per_s": rate, "seconds": seconds,
+            "requests": submitted, "value": round(cols / elapsed, 1), "unit": "cols/s",
+            "req_per_s": round(submitted / elapsed, 1), "p50_ms": round(st["p50_ms"], 3),
+            "p99_ms": round(st["p99_ms"], 3), "requests_per_evaluation": round(st["requests_per_evaluation"], 3),
+            "peak_device_bytes": int(st["peak_bytes"]), "memory_budget": budget, "slots": 4,
+            "mode": "mixed", "inspector_s": round(t_build, 2)}
 
 
 def w_rows(info) -> int:

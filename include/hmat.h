@@ -295,8 +295,8 @@ hmat_status hmat_batch_free(hmat_batch_t b);
  * handles must not be evaluated or profiled elsewhere while the server runs.
  *
  * hmat_server_submit - W and Y are pinned host buffers (cudaHostAlloc,
- * cudaHostRegister) or device buffers, n x q row-major, valid until the request
- * completes (pageable host memory: HMAT_EINVAL, as its copies would stall the
+ * cudaHostRegister) or device buffers, n x q row-major with row strides ldw and
+ * ldy (>= q, in values), valid until the request completes (pageable host memory: HMAT_EINVAL, as its copies would stall the
  * dispatcher); *id identifies the request. Returns HMAT_ENOMEM when the request
  * alone exceeds the memory budget, HMAT_EINVAL when q > max_q.
  * hmat_server_wait - wait for request `id` (timeout_ms < 0: no limit); returns
@@ -315,7 +315,8 @@ typedef struct {
 } hmat_server_params;
 hmat_status hmat_server_create(const hmat_t* handles, int count, const hmat_server_params* params,
                                hmat_server_t* out);
-hmat_status hmat_server_submit(hmat_server_t s, int matrix, const double* W, double* Y, int64_t q, int64_t* id);
+hmat_status hmat_server_submit(hmat_server_t s, int matrix, const double* W, int64_t ldw, double* Y, int64_t ldy,
+                               int64_t q, int64_t* id);
 hmat_status hmat_server_wait(hmat_server_t s, int64_t id, int timeout_ms);
 hmat_status hmat_server_stats(hmat_server_t s, double* out, int n);
 hmat_status hmat_server_free(hmat_server_t s);

@@ -24,6 +24,7 @@ struct Request {
   int matrix = 0;
   const double* W = nullptr;
   double* Y = nullptr;
+  int64_t ldw = 0, ldy = 0;
   int64_t q = 0;
   Clock::time_point submitted;
   bool done = false;
@@ -93,7 +94,7 @@ hmat_status hmat_server::launch(Slot& sl, int matrix, const std::vector<int64_t>
   int64_t col = 0;
   for (int64_t id : ids) {
     const Request& r = requests[id];
-    e = cudaMemcpy2DAsync(dW + col, (size_t)q_total * 8, r.W, (size_t)r.q * 8, (size_t)r.q * 8, (size_t)n,
+    e = cudaMemcpy2DAsync(dW + col, (size_t)q_total * 8, r.W, (size_t)r.ldw * 8, (size_t)r.q * 8, (size_t)n,
                           cudaMemcpyDefault, s);
     if (e != cudaSuccess) break;
     col += r.q;
@@ -107,7 +108,7 @@ hmat_status hmat_server::launch(Slot& sl, int matrix, const std::vector<int64_t>
   for (int64_t id : ids) {
     if (st != HMAT_OK) break;
     const Request& r = requests[id];
-    e = cudaMemcpy2DAsync(r.Y, (size_t)r.q * 8, dY + col, (size_t)q_total * 8, (size_t)r.q * 8, (size_t)n,
+    e = cudaMemcpy2DAsync(r.Y, (size_t)r.ldy * 8, dY + col, (size_t)q_total * 8, (size_t)r.q * 8, (size_t)n,
                           cudaMemcpyDefault, s);
     st = cuda_status(e);
     col += r.q;
@@ -266,9 +267,10 @@ bool copyable(const void* p) {
 
 }  // namespace
 
-extern "C" hmat_status hmat_server_submit(hmat_server_t sv, int matrix, const double* W, double* Y, int64_t q,
-                                          int64_t* id) {
-  if (!sv || !id || matrix < 0 || matrix >= (int)sv->handles.size() || q < 1 || !W || !Y) return HMAT_EINVAL;
+extern "C" hmat_status hmat_server_submit(hmat_server_t sv, int matrix, const double* W, int64_t ldw, double* Y,
+                                          int64_t ldy, int64_t q, int64_t* id) {
+  if (!sv || !id || matrix < 0 || matrix >= (int)sv->handles.size() || q < 1 || !W || !Y || ldw < q || ldy < q)
+    return HMAT_EINVAL;
   if (q > sv->params.max_q || !copyable(W) || !copyable(Y)) return HMAT_EINVAL;
   if (sv->need(matrix, q) > sv->params.memory_budget) return HMAT_ENOMEM;
   std::lock_guard<std::mutex> lk(sv->mu);
@@ -278,6 +280,8 @@ extern "C" hmat_status hmat_server_submit(hmat_server_t sv, int matrix, const do
   r.matrix = matrix;
   r.W = W;
   r.Y = Y;
+  r.ldw = ldw;
+  r.ldy = ldy;
   r.q = q;
   r.submitted = Clock::now();
   sv->requests[r.id] = r;

@@ -123,8 +123,8 @@ def library() -> ctypes.CDLL:
         lib.hmat_batch_free.argtypes = [ctypes.c_void_p]
         lib.hmat_server_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                            ctypes.POINTER(HmatServerParams), ctypes.POINTER(ctypes.c_void_p)]
-        lib.hmat_server_submit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                                           ctypes.c_int64, _c_i64p]
+        lib.hmat_server_submit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, _c_i64p]
         lib.hmat_server_wait.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
         lib.hmat_server_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         lib.hmat_server_free.argtypes = [ctypes.c_void_p]
@@ -324,10 +324,13 @@ def hmat_server_create(handles: Sequence[int], slots: int, memory_budget: int, m
 
 
 def hmat_server_submit(server: int, matrix: int, W, Y) -> int:
-    """Queue Y = K~_matrix W; W and Y are pinned CPU (or CUDA) tensors of n x q. Returns the request id."""
+    """Queue Y = K~_matrix W; W and Y are pinned CPU (or CUDA) tensors of n x q whose rows are contiguous
+    (column slices of a wider tensor are fine). Returns the request id."""
+    if W.stride(1) != 1 or Y.stride(1) != 1 or tuple(W.shape) != tuple(Y.shape):
+        raise ValueError("W and Y must be n x q with contiguous rows")
     rid = ctypes.c_int64()
-    _check(library().hmat_server_submit(server, int(matrix), _ptr(W), _ptr(Y), int(W.shape[1]), ctypes.byref(rid)),
-           "hmat_server_submit")
+    _check(library().hmat_server_submit(server, int(matrix), _ptr(W), int(W.stride(0)), _ptr(Y), int(Y.stride(0)),
+                                        int(W.shape[1]), ctypes.byref(rid)), "hmat_server_submit")
     return int(rid.value)
 
 
