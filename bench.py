@@ -268,7 +268,8 @@ def run_gpu(args, dist: Dist) -> None:
             "bound": "alu", "kernel": "k_fp64_grouped_gemm (near field)",
             "launches_per_eval": near_launches // args.steps,
             "achieved": round(achieved_tflops, 4), "peak": round(peak_gflops / 1e3, 4), "unit": "TFLOP/s",
-            "frac": round(achieved_tflops / (peak_gflops / 1e3), 4), "traffic": None,
+            "frac": round(achieved_tflops / (peak_gflops / 1e3), 4),
+            "traffic": measured_traffic("fp64_near", info["near_values"]),
             "peak_source": "FP64 DFMA loop measured in this run (hmat_measure_fp64_peak); nominal 1.25",
             "step_bytes": bytes_step, "step_hbm_bound_ms": round(bytes_step / 6797.2e9 * 1e3, 3),
         },
@@ -330,7 +331,8 @@ def run_mixed(args, dev, W, Y64, q, info, stream, dist) -> dict:
     else:
         roof = {"bound": "hbm", "achieved": round(alg_bytes / (near_ms / 1e3) / 1e9, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s"}
-    roof.update({"frac": round(roof["achieved"] / roof["peak"], 4), "traffic": None,
+    roof.update({"frac": round(roof["achieved"] / roof["peak"], 4),
+                 "traffic": measured_traffic("mixed_near", nv), "algorithmic_bytes": alg_bytes,
                  "kernel": "k_near_tc (tcgen05 near field)", "peak_source": peaks["source"],
                  "t_tensor_ms": round(t_tensor, 4), "t_hbm_ms": round(t_hbm, 4)})
     return {"value": round(dist.world * q / (ms / 1e3), 3), "unit": "cols/s", "ms_per_step": round(ms, 4),
@@ -443,6 +445,24 @@ def run_serving(args, dist) -> dict:
             "p99_ms": round(st["p99_ms"], 3), "requests_per_evaluation": round(st["requests_per_evaluation"], 3),
             "peak_device_bytes": int(st["peak_bytes"]), "memory_budget": budget, "slots": 4,
             "mode": "mixed", "inspector_s": round(t_build, 2)}
+
+
+def measured_traffic(key: str, near_values: int):
+    """DRAM bytes per launch of a kernel, from the ncu capture recorded in profiles/traffic.json,
+    scaled by the stored near values; None when the kernel's sources changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[key]
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest()[:16] != rec["source_sha256_16"]:
+            return None
+        return int(rec["dram_bytes_per_near_value"] * near_values)
+    except Exception:
+        return None
 
 
 def w_rows(info) -> int:
