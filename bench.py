@@ -85,6 +85,13 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def aggregate(dist: "Dist", columns_per_rank: int, ms_local: float) -> tuple:
+    """Whole-job throughput: the columns all ranks processed over the slowest rank's time per step.
+    Every rank evaluates its own replica of the problem (no collective on the data path)."""
+    ms = dist.max(ms_local)
+    return dist.world * columns_per_rank / (ms / 1e3), ms
+
+
 # ----------------------------------------------------------------------------- clocks during the timed region
 
 CLOCK_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -210,10 +217,9 @@ def run_gpu(args, dist: Dist) -> None:
     ms_local = e0.elapsed_time(e1) / args.steps
     phases = hp.hmat_phase_times(dev.handle)
     hp.hmat_profile(dev.handle, False)
-    ms = dist.max(ms_local)
+    value, ms = aggregate(dist, q, ms_local)
     if dev.poll() != hp.HMAT_OK:
         raise RuntimeError("device status error during the timed steps")
-    value = dist.world * q / (ms / 1e3)
 
     mixed = run_mixed(args, dev, W, Y, q, info, stream, dist) if args.mixed == "on" else None
 
