@@ -467,6 +467,29 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
       ph.n_tiles = (int64_t)tiles.size() - ph.tile_begin;
       if (ph.n_tiles > 0) h->phases.push_back(ph);
     }
+    // the FP32 far field of the mixed mode splits each task's K over warp groups, so a
+    // phase of long-K tasks (coupling: hundreds of partners) is bound by its longest task:
+    // one launch of 16-row tiles for all its tasks; the other phases (short K) keep one
+    // launch per row-tile size; the near field runs on tensor cores, not here
+    if (kind == PH_NEAR) return;
+    if (kind != PH_COUPLING) {
+      for (const Phase& p : h->phases)
+        if (p.kind == kind && p.level == level) h->phases32.push_back(p);
+      return;
+    }
+    Phase ph{kind, level, x, y, xmap, (int64_t)tiles.size(), 0, 0, 16};
+    std::vector<std::pair<int64_t, GemmTile>> list;
+    for (int32_t t : task_ids) {
+      const GemmTask& tk = tasks[t];
+      int64_t kk = 0;
+      for (int32_t e = tk.e_begin; e < tk.e_end; ++e) kk += entries[e].k;
+      ph.max_m = std::max(ph.max_m, tk.m);
+      for (int32_t m0 = 0; m0 < tk.m; m0 += 16) list.push_back({std::max<int64_t>(kk, 1), GemmTile{t, m0}});
+    }
+    std::stable_sort(list.begin(), list.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (auto& p : list) tiles.push_back(p.second);
+    ph.n_tiles = (int64_t)tiles.size() - ph.tile_begin;
+    if (ph.n_tiles > 0) h->phases32.push_back(ph);
   };
   auto new_task = [&](int64_t out_row, int64_t m, int accumulate) -> int32_t {
     tasks.push_back(GemmTask{out_row, (int32_t)m, (int32_t)entries.size(), (int32_t)entries.size(), accumulate});

@@ -191,8 +191,8 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
       if (e != cudaSuccess) return cuda_status(e);
       return prof_end(h, rec, strm) ? HMAT_OK : HMAT_ECUDA;
     };
-    for (const Phase& ph : h->phases) {
-      if (ph.kind == PH_NEAR || ph.kind == PH_DOWN_LEAF) continue;
+    for (const Phase& ph : h->phases32) {
+      if (ph.kind == PH_DOWN_LEAF) continue;
       if ((st = far_launch(ph, c->aux)) != HMAT_OK) return st;
     }
     if (cudaEventRecord(c->ev_join, c->aux) != cudaSuccess) return HMAT_ECUDA;
@@ -201,7 +201,7 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;
     if (cudaStreamWaitEvent(s, c->ev_join, 0) != cudaSuccess) return HMAT_ECUDA;
-    for (const Phase& ph : h->phases)
+    for (const Phase& ph : h->phases32)
       if (ph.kind == PH_DOWN_LEAF && (st = far_launch(ph, s)) != HMAT_OK) return st;
     return HMAT_OK;
   }

@@ -9,6 +9,8 @@ namespace hmat {
 
 cudaError_t launch_f32_phase(const Handle& h, const Phase& ph, const float* X, const int64_t* x_map, void* Y,
                              bool y_is_f64, const int64_t* y_map, int64_t q, cudaStream_t stream) {
+  // the FP32 arena starts at the bases: near blocks have no FP32 copy
+  if (ph.kind == PH_NEAR) return cudaErrorInvalidValue;
   if (y_is_f64)
     return gemm::launch_phase_f32<double>(h, ph, h.arena32, h.arena32_shift, X, x_map, (double*)Y, y_map, q, stream);
   return gemm::launch_phase_f32<float>(h, ph, h.arena32, h.arena32_shift, X, x_map, (float*)Y, y_map, q, stream);

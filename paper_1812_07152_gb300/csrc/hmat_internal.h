@@ -145,7 +145,8 @@ struct Handle {
 
   std::vector<int64_t> begin, size, skel_off, perm_host, near_ptr, far_ptr;
   std::vector<int32_t> rank, near_idx, far_idx;
-  std::vector<Phase> phases;
+  std::vector<Phase> phases;      // FP64 mode: one launch per row-tile size of every phase
+  std::vector<Phase> phases32;    // mixed far field (coupling: one split-K launch of 16-row tiles)
 
   // device
   double* arena = nullptr;       // packed FP64 blocks (near, basis, coupling)

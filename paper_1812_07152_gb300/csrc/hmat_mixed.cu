@@ -10,17 +10,19 @@
 //    subnormal lo for values down to 2^-16 of the maximum;
 //  * Y_i = sum_j (Dh Wh + Dh Wl + Dl Wh), the dropped Dl Wl term is 2^-22 relative;
 //  * the tensor core's FP32 accumulator truncates (rounds toward zero, measured on
-//    this GPU), so the dominant Dh Wh product is accumulated in TMEM for one near
-//    block only and then drained by the epilogue warps into a compensated FP32
+//    this GPU), so the dominant Dh Wh product is accumulated in TMEM for two near
+//    blocks only and then drained by the epilogue warps into a compensated FP32
 //    (hi, lo) pair per output (hi in registers, lo in TMEM columns 384..511); the
 //    two small cross terms (2^-11 of the result) accumulate over the whole near
 //    list in a second TMEM accumulator.
 //
 // Operands are packed once (D at load, W per evaluation) in the canonical K-major
 // 128-byte-swizzled tcgen05 layout, so one cp.async.bulk (TMA) copy per tile lands
-// it in shared memory. Warp roles: warp 0 issues the bulk copies, warp 1 issues the
-// MMAs (one thread) and owns the TMEM allocation, warps 2..9 drain the accumulators
-// and write Y. All waits are bounded; on a timeout the kernel records
+// it in shared memory. Warp roles: warp 0 issues the bulk copies of the D tiles and
+// warp 10 those of the W tiles (bulk copies issued by one thread are processed about
+// one at a time, ~0.2 us each, so two issuers nearly double the copy rate), warp 1
+// issues the MMAs (one thread) and owns the TMEM allocation, warps 2..9 drain the
+// accumulators and write Y. All waits are bounded; on a timeout the kernel records
 // HMAT_ETIMEOUT in the status word, lets its own copies and MMAs finish, frees its
 // TMEM and returns.
 #include <cuda_fp16.h>
@@ -33,11 +35,12 @@ namespace {
 
 constexpr int kStages = 3;
 constexpr int kStageBytes = 65536;           // A hi+lo (32 KB) + B hi+lo (<= 32 KB)
-constexpr int kTcThreads = 320;              // warp 0 copies, warp 1 MMAs, warps 2..9 epilogue
+constexpr int kTcThreads = 352;              // warps 0/10 copies, warp 1 MMAs, warps 2..9 epilogue
 constexpr int kMaxNt = 128;                  // columns of W per CTA (MMA N)
 constexpr uint32_t kTmemCols = 512;          // main[0], main[1], cross, compensation terms
 constexpr uint64_t kWaitNs = 2000000000ull;  // give up a wait after 2 s
 constexpr int kScaleTop = 13;                // scaled maxima land in [2^13, 2^14)
+constexpr int kDrainBlocks = 2;              // near blocks accumulated in TMEM between two drains
 
 // ------------------------------------------------------------------ PTX helpers
 
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
       done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
-  __shared__ volatile int issued, consumed;
+  __shared__ volatile int issued_a, issued_b, consumed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TcTile work = a.tc.work[blockIdx.x / a.n_ct];
@@ -327,7 +330,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&full_bar[s]), 2);  // the D and the W producer each arrive once per stage
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -337,7 +340,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
     mbar_init(smem_u32(&cfull_bar), 1);
     mbar_init(smem_u32(&done_bar), 1);
     abort_flag = 0;
-    issued = 0;
+    issued_a = 0;
+    issued_b = 0;
     consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -355,9 +359,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
     atomicCAS(a.status, 0, (int)HMAT_ETIMEOUT);
   };
 
-  if (warp == 0) {
-    // ---- producer: one bulk copy of the D tile pair and one of the W tile pair per k-chunk
+  if (warp == 0 || warp == 10) {
+    // ---- producers: warp 0 copies the D tile pair, warp 10 the W tile pair of every k-chunk
     if (lane == 0) {
+      const bool is_d = warp == 0;
       int it = 0;
       bool ok = true;
       for (int64_t e = e0; e < e1 && ok; ++e) {
@@ -374,11 +379,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
             break;
           }
           const uint32_t st = smem_u32(smem + s * kStageBytes);
-          mbar_expect_tx(smem_u32(&full_bar[s]), a_bytes + b_bytes);
-          bulk_g2s(st, abase + (int64_t)c * a_bytes, a_bytes, smem_u32(&full_bar[s]));
-          bulk_g2s(st + a_bytes, a.wsplit + ((g0 + c) * a.n_ct + ct) * (int64_t)b_bytes, b_bytes,
-                   smem_u32(&full_bar[s]));
-          issued = it + 1;
+          if (is_d) {
+            mbar_expect_tx(smem_u32(&full_bar[s]), a_bytes);
+            bulk_g2s(st, abase + (int64_t)c * a_bytes, a_bytes, smem_u32(&full_bar[s]));
+            issued_a = it + 1;
+          } else {
+            mbar_expect_tx(smem_u32(&full_bar[s]), b_bytes);
+            bulk_g2s(st + a_bytes, a.wsplit + ((g0 + c) * a.n_ct + ct) * (int64_t)b_bytes, b_bytes,
+                     smem_u32(&full_bar[s]));
+            issued_b = it + 1;
+          }
         }
       }
     }
@@ -387,13 +397,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
     if (lane == 0) {
       const uint32_t idesc = idesc_f16(kTcRows, a.n_t);
       const uint32_t cross = tmem + 256;
+      int nb = 0;  // near blocks with data
+      for (int64_t e = e0; e < e1; ++e) nb += a.tc.leaf_kc[a.tc.near_idx[e]] > 0;
       int it = 0, blk = 0;
       bool ok = true;
       for (int64_t e = e0; e < e1 && ok; ++e) {
         const int kc = a.tc.leaf_kc[a.tc.near_idx[e]];
         if (kc == 0) continue;
-        const int b = blk & 1, rb = blk >> 1;
-        if (rb > 0 && !mbar_wait(smem_u32(&mempty_bar[b]), (rb - 1) & 1, &abort_flag)) {
+        const int grp = blk / kDrainBlocks, b = grp & 1, rb = grp >> 1;
+        const bool first_of_group = blk % kDrainBlocks == 0;
+        if (first_of_group && rb > 0 && !mbar_wait(smem_u32(&mempty_bar[b]), (rb - 1) & 1, &abort_flag)) {
           fail();
           ok = false;
           break;
@@ -414,7 +427,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t o = kk * 32;
-            mma_f16(main_acc, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc, (c | kk) ? 1u : 0u);
+            mma_f16(main_acc, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc,
+                    (first_of_group && c == 0 && kk == 0) ? 0u : 1u);
             mma_f16(cross, desc_sw128(a_hi + o), desc_sw128(b_lo + o), idesc, (it | kk) ? 1u : 0u);
             mma_f16(cross, desc_sw128(a_lo + o), desc_sw128(b_hi + o), idesc, 1u);
           }
@@ -422,8 +436,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
           consumed = it + 1;
         }
         if (!ok) break;
-        mma_commit(smem_u32(&mfull_bar[b]));
         ++blk;
+        if (blk % kDrainBlocks == 0 || blk == nb) mma_commit(smem_u32(&mfull_bar[b]));
       }
       if (ok && blk > 0) mma_commit(smem_u32(&cfull_bar));
       mma_commit(smem_u32(&done_bar));
@@ -431,7 +445,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
       while (!mbar_try(smem_u32(&done_bar), 0) && gtimer() - t0 < kWaitNs) {
       }
     }
-  } else {
+  } else if (warp >= 2 && warp <= 9) {
     // ---- epilogue: warp w drains TMEM lanes 32*(w%4).. of column half (w-2)/4
     const int eq = warp & 3, half = (warp - 2) >> 2;
     const uint32_t lane_base = (uint32_t)(eq * 32) << 16;
@@ -446,11 +460,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) tmem_st16(comp + cc * 16, z);
     }
+    int nb = 0;  // near blocks with data, drained kDrainBlocks at a time
+    for (int64_t e = e0; e < e1; ++e) nb += a.tc.leaf_kc[a.tc.near_idx[e]] > 0;
+    const int n_groups = (nb + kDrainBlocks - 1) / kDrainBlocks;
     int blk = 0;
     bool ok = true;
-    for (int64_t e = e0; e < e1; ++e) {
-      if (a.tc.leaf_kc[a.tc.near_idx[e]] == 0) continue;
-      const int b = blk & 1, rb = blk >> 1;
+    for (int grp = 0; grp < n_groups; ++grp) {
+      const int b = grp & 1, rb = grp >> 1;
       // every lane must agree before the warp-collective TMEM loads
       if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&mfull_bar[b]), rb & 1, &abort_flag))) {
         if (lane == 0) fail();
@@ -469,7 +485,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&mempty_bar[b]));
-      ++blk;
+      blk += kDrainBlocks;
     }
     bool have_cross = false;
     if (ok && blk > 0) {
@@ -511,7 +527,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
   fence_before();
   __syncthreads();
   if (abort_flag && threadIdx.x == 0) {
-    // let the bulk copies this CTA issued land before its shared memory goes away
+    // let the bulk copies this CTA issued land before its shared memory goes away (a stage
+    // whose second copy was never issued cannot complete: its wait ends at the time limit)
+    const int issued = issued_a > issued_b ? issued_a : issued_b;
     for (int it = consumed; it < issued; ++it) {
       const uint64_t t0 = gtimer();
       while (!mbar_try(smem_u32(&full_bar[it % kStages]), (it / kStages) & 1) && gtimer() - t0 < kWaitNs) {
