@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--serve", choices=["short", "full", "off"], default="short",
                     help="also run the serving mode: a Poisson request stream on resident HMatrices "
                          "(short: 4 matrices N = 16K..128K, 6 s; full: 8 matrices N = 16K..1M, 2000 req/s, 60 s)")
+    ap.add_argument("--precision", choices=["on", "off"], default="on",
+                    help="time the precision-mode recipe (N=262144 inverse multiquadric, q=512), FP64 vs mixed")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
     return ap.parse_args()
 
@@ -193,6 +195,9 @@ def run_gpu(args, dist: Dist) -> None:
     Y = torch.empty_like(W)
     dev.reserve(q)
     stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    tune = hp.hmat_autotune(dev.handle, q, hp.HMAT_MODE_FP64, stream)
+    tune["seconds"] = round(time.perf_counter() - t0, 2)
 
     for _ in range(args.warmup):
         hp.hmat_eval(dev.handle, W, Y, q, hp.HMAT_MODE_FP64, stream)
@@ -283,10 +288,15 @@ def run_gpu(args, dist: Dist) -> None:
                 "d2h_bytes_per_step": int(Y_host.numel() * 8)},
         "gpu_launches": launches,
         "clocks": clk,
+        "autotune": {"fp64": tune},
     }
     if mixed is not None:
+        line["autotune"]["mixed"] = mixed.pop("autotune")
         line["mixed"] = mixed
     dev.close()
+
+    if args.precision == "on":
+        line["precision"] = run_precision(args, dist)
 
     if args.batch == "on":
         line["batch"] = run_batch(args, dist)
@@ -305,6 +315,9 @@ def run_mixed(args, dev, W, Y64, q, info, stream, dist) -> dict:
     import torch
     import paper_1812_07152_gb300 as hp
     Ym = torch.empty_like(W)
+    t0 = time.perf_counter()
+    tune = hp.hmat_autotune(dev.handle, q, hp.HMAT_MODE_MIXED, stream)
+    tune["seconds"] = round(time.perf_counter() - t0, 2)
     for _ in range(args.warmup):
         hp.hmat_eval(dev.handle, W, Ym, q, hp.HMAT_MODE_MIXED, stream)
     torch.cuda.synchronize()
@@ -344,7 +357,53 @@ def run_mixed(args, dev, W, Y64, q, info, stream, dist) -> dict:
     return {"value": round(dist.world * q / (ms / 1e3), 3), "unit": "cols/s", "ms_per_step": round(ms, 4),
             "error_vs_fp64": err, "dtype": "f16 hi+lo split, f32 accumulate",
             "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
-            "gpu_launches": sum(c for _, c in phases.values()), "roofline": roof}
+            "gpu_launches": sum(c for _, c in phases.values()), "roofline": roof, "autotune": tune}
+
+
+def run_precision(args, dist) -> dict:
+    """Precision mode on its own recipe: N = 262144 uniform points in [0,1]^3, inverse multiquadric
+    1/sqrt(r^2 + 0.01), geometric admissibility, leaf 256, ID tol 1e-7, q = 512. The mixed form (FP16 hi+lo
+    tensor-core near field, FP32 far field, FP64 output sums) against the FP64 form on the same GPU; its error
+    is measured against this run's FP64 result."""
+    import torch
+    import paper_1812_07152_gb300 as hp
+    from workloads import WORKLOADS, make_points, normal_rhs
+    w = WORKLOADS["h2_imq3d_n262144"]
+    t0 = time.perf_counter()
+    dev = hp.DeviceHMatrix.build(make_points(w), flags=hp.HMAT_LOAD_MIXED, **build_params(w))
+    t_build = time.perf_counter() - t0
+    info = dev.info
+    q = w.q
+    W = torch.from_numpy(normal_rhs(w.n, q, w.rhs_seed)).cuda()
+    Y64 = torch.empty_like(W)
+    Ym = torch.empty_like(W)
+    stream = torch.cuda.current_stream()
+    dev.reserve(q)
+    out = {"workload": w.name, "n": w.n, "q": q, "kernel": f"{w.kernel} {w.kernel_param}", "leaf_size": w.leaf_size,
+           "tol": w.tol, "max_rank": w.max_rank, "near_values": info["near_values"], "sum_rank": info["sum_rank"],
+           "inspector_s": round(t_build, 2), "unit": "cols/s"}
+    tunes = {}
+    for name, mode, Y, steps in (("fp64", hp.HMAT_MODE_FP64, Y64, 2), ("mixed", hp.HMAT_MODE_MIXED, Ym, args.steps)):
+        tunes[name] = hp.hmat_autotune(dev.handle, q, mode, stream)
+        hp.hmat_eval(dev.handle, W, Y, q, mode, stream)          # warm-up (FP64 takes about a second)
+        torch.cuda.synchronize()
+        dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            hp.hmat_eval(dev.handle, W, Y, q, mode, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = dist.max(e0.elapsed_time(e1) / steps)
+        if dev.poll() != hp.HMAT_OK:
+            raise RuntimeError(f"device status error in the precision-mode {name} steps")
+        out[name] = {"value": round(dist.world * q / (ms / 1e3), 2), "ms_per_step": round(ms, 4), "steps": steps}
+    out["mixed"]["error_vs_fp64"] = float(torch.linalg.norm(Ym - Y64) / torch.linalg.norm(Y64))
+    out["mixed_over_fp64"] = round(out["mixed"]["value"] / out["fp64"]["value"], 2)
+    out["autotune"] = tunes
+    dev.close()
+    return out
 
 
 def run_batch(args, dist) -> dict:
@@ -380,11 +439,21 @@ def run_batch(args, dist) -> dict:
 
     for name, mode in (("fp64", hp.HMAT_MODE_FP64), ("mixed", hp.HMAT_MODE_MIXED)):
         b = hp.hmat_batch_create(handles, mode)
+        ms_default = dist.max(timed(lambda: hp.hmat_batch_eval(b, Ws, Ys, stream)))
+        # autotuned tile shapes per member (bitwise the same results); the next batch call re-captures
+        t0 = time.perf_counter()
+        for h, w in zip(handles, ws):
+            hp.hmat_autotune(h, w.q, mode, stream)
+        t_tune = time.perf_counter() - t0
+        hp.hmat_batch_free(b)
+        b = hp.hmat_batch_create(handles, mode)
         ms_graph = dist.max(timed(lambda: hp.hmat_batch_eval(b, Ws, Ys, stream)))
         ms_loop = dist.max(timed(lambda: [hp.hmat_eval(h, W, Y, W.shape[1], mode, stream)
                                           for h, W, Y in zip(handles, Ws, Ys)]))
         hp.hmat_batch_free(b)
         out[name] = {"value": round(dist.world * cols / (ms_graph / 1e3), 1), "ms_per_step": round(ms_graph, 4),
+                     "untuned_value": round(dist.world * cols / (ms_default / 1e3), 1),
+                     "untuned_ms": round(ms_default, 4), "autotune_s": round(t_tune, 2),
                      "one_call_per_matrix_value": round(dist.world * cols / (ms_loop / 1e3), 1),
                      "one_call_per_matrix_ms": round(ms_loop, 4)}
     for h in handles:

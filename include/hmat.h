@@ -257,6 +257,37 @@ hmat_status hmat_measure_fp64_peak(double* gflops);
 hmat_status hmat_eval_noalloc(hmat_t h, const double* W, double* Y, int64_t q, void* stream);
 
 /*
+ * hmat_autotune - choose the tile shapes of h's evaluations with q columns in
+ * `mode` by timing candidates on the device (CUDA events on `stream`); later
+ * hmat_eval, hmat_eval_host, hmat_eval_noalloc, batch and server evaluations of h
+ * with that q and mode use them. FP64 mode: per launch of the evaluation (one per
+ * phase of Section 2.1's evaluation and row-tile size), the column tile of the
+ * grouped GEMM (1 to 64 columns) among those that pad less than half a tile; a long
+ * launch is timed on its longest tiles. Mixed mode: the column width of the
+ * tensor-core near-field CTAs (fewer, wider tiles copy each near block fewer
+ * times; more, narrower ones fill more SMs on a matrix with few leaves). Every
+ * candidate sums each output in the same order, so results are bitwise those of
+ * an untuned evaluation.
+ *
+ * Synchronous: allocates private W, Y and workspaces (cudaMalloc), runs the
+ * candidates on `stream`, frees them and returns. Must not run while another
+ * thread evaluates h (the choice table is not locked). A call for a (q, mode)
+ * already tuned replaces the earlier choice. `report` (may be NULL) receives the
+ * number of launches tuned, the summed time of those launches with the default and
+ * with the chosen shapes (ms; a long launch timed on a prefix counts at full
+ * length, scaled by its tile count) and the chosen near-field width in columns.
+ */
+typedef struct {
+  int64_t q;
+  int32_t mode;
+  int32_t launches_tuned;
+  double default_ms;
+  double tuned_ms;
+  int32_t near_cols;
+} hmat_tune_report;
+hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream, hmat_tune_report* report);
+
+/*
  * Batches: many HMatrices (uneven sizes, ranks and q) evaluated together. A batch
  * owns one evaluation context (workspaces) and one CUDA stream per member; the
  * first hmat_batch_eval with a given set of W, Y pointers and q values captures
@@ -327,6 +358,17 @@ hmat_status hmat_server_free(hmat_server_t s);
  * then clear it.
  */
 hmat_status hmat_status_poll(hmat_t h, void* stream);
+
+/*
+ * hmat_selftest_timeout - failure-detection self-test (no counterpart in the
+ * paper). Enqueues on `stream` one device wait, through the bounded-wait routine
+ * of the tensor-core near-field kernel, on a barrier that nothing completes; after
+ * limit_ns nanoseconds (0 < limit_ns <= 10 s, else HMAT_EINVAL) the wait gives up
+ * and latches HMAT_ETIMEOUT in h's status word, as a stuck evaluation would, so the
+ * next hmat_status_poll returns HMAT_ETIMEOUT. The wait holds no copy, MMA or
+ * tensor memory, so the CUDA context stays usable afterwards.
+ */
+hmat_status hmat_selftest_timeout(hmat_t h, int64_t limit_ns, void* stream);
 
 /* hmat_info - sizes of the loaded HMatrix: out[0] = n_points, out[1] = levels,
  * out[2] = near entries, out[3] = far entries, out[4] = stored near values,

@@ -32,7 +32,7 @@ def _sources() -> List[str]:
 
 def _digest(files: List[str], flags: List[str]) -> str:
     h = hashlib.sha256()
-    for f in sorted(files + [os.path.join(CSRC, x) for x in os.listdir(CSRC) if x.endswith(".h")]
+    for f in sorted(files + [os.path.join(CSRC, x) for x in os.listdir(CSRC) if x.endswith((".h", ".cuh"))]
                     + [os.path.join(ROOT, "include", x) for x in os.listdir(os.path.join(ROOT, "include"))]):
         h.update(f.encode())
         with open(f, "rb") as fh:

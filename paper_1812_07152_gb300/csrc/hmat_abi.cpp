@@ -697,6 +697,14 @@ extern "C" hmat_status hmat_status_poll(hmat_t h, void* stream) {
   return (hmat_status)word;
 }
 
+extern "C" hmat_status hmat_selftest_timeout(hmat_t h, int64_t limit_ns, void* stream) {
+  if (!h || limit_ns <= 0 || limit_ns > 10000000000LL) return HMAT_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
+  if (dev != h->device) return HMAT_EINVAL;
+  return cuda_status(launch_wait_selftest(h->status, (uint64_t)limit_ns, (cudaStream_t)stream));
+}
+
 extern "C" hmat_status hmat_info(hmat_t h, int64_t* out, int n_out) {
   if (!h || !out || n_out < 0) return HMAT_EINVAL;
   const int64_t held = h->device_bytes + (h->ctx ? h->ctx->block_bytes + 16 * h->ctx->host_cap : 0);

@@ -24,12 +24,6 @@ constexpr int64_t kAlignBytes = 256;
 
 int64_t align_up(int64_t x) { return (x + kAlignBytes - 1) / kAlignBytes * kAlignBytes; }
 
-// Columns of W per tensor-core CTA and the number of column tiles for q.
-void mixed_tiles(int64_t q, int* n_t, int64_t* n_ct) {
-  *n_t = (int)std::min<int64_t>(128, (q + 15) / 16 * 16);
-  *n_ct = (q + *n_t - 1) / *n_t;
-}
-
 // Event records around one launch of the evaluation when the handle is profiling.
 bool prof_begin(Handle* h, int32_t kind, cudaStream_t s, Handle::ProfRecord* rec) {
   rec->kind = kind;
@@ -62,12 +56,7 @@ hmat_status check_call(const Handle* h, const double* W, const double* Y, int64_
   const char* y0 = (const char*)Y;
   const int64_t bytes = h->n_points * q * (int64_t)sizeof(double);
   if (w0 < y0 + bytes && y0 < w0 + bytes) return HMAT_EINVAL;  // W and Y overlap
-  if (mode == HMAT_MODE_MIXED) {
-    int n_t;
-    int64_t n_ct;
-    mixed_tiles(q, &n_t, &n_ct);
-    if (n_ct > 65535) return HMAT_EUNSUPPORTED;
-  }
+  if (mode == HMAT_MODE_MIXED && (q + 127) / 128 > 65535) return HMAT_EUNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
   if (dev != h->device) return HMAT_EINVAL;
@@ -75,6 +64,38 @@ hmat_status check_call(const Handle* h, const double* W, const double* Y, int64_
 }
 
 }  // namespace
+
+// Tensor-core column tiles: n_ct tiles of n_t columns (a multiple of 16, at most 128)
+// cover q. The default is the fewest tiles, balanced; the tuner also tries one and two
+// more tiles (more CTAs when a matrix has few leaves).
+std::vector<int> mixed_nt_candidates(int64_t q) {
+  std::vector<int> out;
+  const int64_t base = std::max<int64_t>((q + 127) / 128, 1);
+  for (int64_t n_ct : {base, base + 1, base + 2}) {
+    const int64_t per = (q + n_ct - 1) / n_ct;
+    const int n_t = (int)std::max<int64_t>(16, (per + 15) / 16 * 16);
+    if (std::find(out.begin(), out.end(), n_t) == out.end()) out.push_back(n_t);
+  }
+  return out;
+}
+
+int64_t mixed_cols_bound(int64_t q) {
+  int64_t best = 0;
+  for (int n_t : mixed_nt_candidates(q)) best = std::max<int64_t>(best, (q + n_t - 1) / n_t * n_t);
+  return best;
+}
+
+const TuneEntry* find_tuned(const Handle& h, int64_t q, int mode) {
+  for (const TuneEntry& t : h.tuned)
+    if (t.q == q && t.mode == mode) return &t;
+  return nullptr;
+}
+
+void mixed_tiles(const Handle& h, int64_t q, int* n_t, int64_t* n_ct) {
+  const TuneEntry* t = find_tuned(h, q, HMAT_MODE_MIXED);
+  *n_t = t && t->n_t > 0 ? t->n_t : mixed_nt_candidates(q)[0];
+  *n_ct = (q + *n_t - 1) / *n_t;
+}
 
 hmat_status ctx_create(const Handle& h, EvalContext** out) {
   *out = nullptr;
@@ -112,10 +133,7 @@ void ctx_destroy(EvalContext* c) {
 int64_t ctx_bytes(const Handle& h, int64_t q, int mode) {
   const int64_t r = std::max<int64_t>(h.sum_rank, 1);
   if (mode == HMAT_MODE_MIXED) {
-    int n_t;
-    int64_t n_ct;
-    mixed_tiles(q, &n_t, &n_ct);
-    return align_up(sizeof(unsigned long long)) + align_up(h.total_kchunks * n_ct * (int64_t)n_t * 256) +
+    return align_up(sizeof(unsigned long long)) + align_up(h.total_kchunks * mixed_cols_bound(q) * 256) +
            align_up(std::max<int64_t>(h.n_points, 1) * q * 4) + 2 * align_up(r * q * 4);
   }
   return 2 * align_up(r * q * 8);
@@ -134,11 +152,8 @@ void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* bas
   c->wsplit = nullptr;
   c->w32 = c->ws32 = c->us32 = nullptr;
   if (mode == HMAT_MODE_MIXED) {
-    int n_t;
-    int64_t n_ct;
-    mixed_tiles(q, &n_t, &n_ct);
     c->wmax = (unsigned long long*)take(sizeof(unsigned long long));
-    c->wsplit = take(h.total_kchunks * n_ct * (int64_t)n_t * 256);
+    c->wsplit = take(h.total_kchunks * mixed_cols_bound(q) * 256);
     c->w32 = (float*)take(std::max<int64_t>(h.n_points, 1) * q * 4);
     c->ws32 = (float*)take(r * q * 4);
     c->us32 = (float*)take(r * q * 4);
@@ -173,7 +188,7 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
   if (mode == HMAT_MODE_MIXED) {
     int n_t;
     int64_t n_ct;
-    mixed_tiles(q, &n_t, &n_ct);
+    mixed_tiles(*h, q, &n_t, &n_ct);
     if (!prof_begin(h, HMAT_PHASE_SPLIT, s, &rec)) return HMAT_ECUDA;
     e = launch_w_split(h->tc, h->total_kchunks, W, h->n_points * q, h->perm, q, n_t, (int)n_ct, c->wmax, c->wsplit,
                        c->w32, s);
@@ -205,13 +220,16 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
       if (ph.kind == PH_DOWN_LEAF && (st = far_launch(ph, s)) != HMAT_OK) return st;
     return HMAT_OK;
   }
-  for (const Phase& ph : h->phases) {
+  const TuneEntry* tuned = find_tuned(*h, q, HMAT_MODE_FP64);
+  for (size_t i = 0; i < h->phases.size(); ++i) {
+    const Phase& ph = h->phases[i];
     const double* X = ph.x == MAT_USER ? W : (ph.x == MAT_SKEL_W ? c->ws : c->us);
     double* Yd = ph.y == MAT_USER ? Y : (ph.y == MAT_SKEL_W ? c->ws : c->us);
     const int64_t* xm = phase_x_map(*h, ph);
     const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
+    const int shape = tuned && i < tuned->shape.size() ? tuned->shape[i] : -1;
     if (!prof_begin(h, (int32_t)ph.kind, s, &rec)) return HMAT_ECUDA;
-    e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, s);
+    e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, shape, -1, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;
   }

@@ -14,15 +14,23 @@ namespace hmat {
 namespace gemm {
 
 constexpr int BK = 16;   // depth of one operand chunk
-constexpr int TM = 4;    // outputs per thread: TM rows x TN columns
+constexpr int TM = 4;    // FP32 kernel: outputs per thread, TM rows x TN columns
 constexpr int TN = 4;
 
-// BM rows (the launch's tile_rows) x BN right-hand-side columns per CTA.
-template <int BM, int BN>
+// FP64 kernel column tiles: BN right-hand-side columns per CTA, each thread holding
+// CTM rows x CTN columns of the output tile. The narrow shapes (BN < 16) serve small
+// q, where a 16-wide tile would spend most DFMAs on padding columns. Every shape
+// sums each output over the same depth order, so all give bitwise the same result.
+constexpr int kColShapes = 7;
+constexpr int kColBN[kColShapes] = {1, 2, 4, 8, 16, 32, 64};
+
+// BM rows (the launch's tile_rows) x BN columns per CTA, CTM x CTN outputs per thread.
+template <int BM, int BN, int CTM, int CTN>
 struct Cfg {
-  static constexpr int kThreads = (BM / TM) * (BN / TN);
-  static constexpr int kAPer = BM * BK / kThreads;  // A values loaded per thread per chunk
-  static constexpr int kXPer = BN * BK / kThreads;  // X values loaded per thread per chunk
+  static constexpr int kThreads = (BM / CTM) * (BN / CTN);
+  static constexpr int kAPer = BM * BK / kThreads;                   // A values loaded per thread per chunk
+  static constexpr int kXPer = (BN * BK + kThreads - 1) / kThreads;  // X values (the last ones guarded)
+  static_assert(BM * BK % kThreads == 0, "whole A chunk per thread");
 };
 
 __device__ __forceinline__ int64_t map_row(const int64_t* __restrict__ m, int64_t r) { return m ? m[r] : r; }
@@ -34,14 +42,15 @@ __device__ __forceinline__ int64_t map_row(const int64_t* __restrict__ m, int64_
 // TA: stored block type, TX / TY: input / output matrix types, TC: the type of the
 // products and sums. Entry offsets index the FP64 arena; a_shift maps them into an
 // arena that holds only the values from a_shift on (the FP32 far-field copy).
-template <typename TA, typename TX, typename TY, typename TC, int BM, int BN>
-__global__ void __launch_bounds__(Cfg<BM, BN>::kThreads)
+template <typename TA, typename TX, typename TY, typename TC, int BM, int BN, int CTM, int CTN>
+__global__ void __launch_bounds__(Cfg<BM, BN, CTM, CTN>::kThreads)
 k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
                const GemmEntry* __restrict__ entries, const TA* __restrict__ arena, int64_t a_shift,
                const TX* X, const int64_t* __restrict__ x_map,
                TY* Y, const int64_t* __restrict__ y_map, int64_t q, int n_col_tiles) {
-  using C = Cfg<BM, BN>;
+  using C = Cfg<BM, BN, CTM, CTN>;
   constexpr int NT = C::kThreads;
+  constexpr int TM = CTM, TN = CTN;
   constexpr int CX = BN / TN;  // threads along the columns
   __shared__ TC As[2][BK][BM + 1];
   __shared__ TC Xs[2][BK][BN];
@@ -85,7 +94,7 @@ k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ 
       const int gk = kk0 + k;
       const int64_t gq = q0 + n;
       TC v = TC(0);
-      if (gk < en.k && gq < q) v = (TC)X[map_row(x_map, en.x_row + gk) * q + gq];
+      if (idx < BN * BK && gk < en.k && gq < q) v = (TC)X[map_row(x_map, en.x_row + gk) * q + gq];
       rx[t] = v;
     }
   };
@@ -100,7 +109,7 @@ k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ 
 #pragma unroll
     for (int t = 0; t < C::kXPer; ++t) {
       const int idx = tid + t * NT;
-      Xs[buf][idx / BN][idx % BN] = rx[t];
+      if (idx < BN * BK) Xs[buf][idx / BN][idx % BN] = rx[t];
     }
   };
 
@@ -145,35 +154,57 @@ k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ 
   }
 }
 
-template <typename TA, typename TX, typename TY, typename TC, int BM, int BN>
-cudaError_t launch(const Handle& h, const Phase& ph, const TA* arena, int64_t a_shift, const TX* X,
+template <typename TA, typename TX, typename TY, typename TC, int BM, int BN, int CTM, int CTN>
+cudaError_t launch(const Handle& h, const Phase& ph, int64_t n_tiles, const TA* arena, int64_t a_shift, const TX* X,
                    const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q, cudaStream_t s) {
   const int64_t n_col = (q + BN - 1) / BN;
-  const int64_t blocks = ph.n_tiles * n_col;
+  const int64_t blocks = n_tiles * n_col;
   if (blocks > 2147483647LL) return cudaErrorInvalidValue;
-  k_grouped_gemm<TA, TX, TY, TC, BM, BN><<<(unsigned)blocks, Cfg<BM, BN>::kThreads, 0, s>>>(
+  k_grouped_gemm<TA, TX, TY, TC, BM, BN, CTM, CTN><<<(unsigned)blocks, Cfg<BM, BN, CTM, CTN>::kThreads, 0, s>>>(
       h.tiles + ph.tile_begin, h.tasks, h.entries, arena, a_shift, X, x_map, Y, y_map, q, (int)n_col);
   return cudaGetLastError();
 }
 
-// One launch of a phase: the tile-row class of the launch picks BM, q picks BN.
-template <typename TA, typename TX, typename TY, typename TC>
-cudaError_t launch_phase(const Handle& h, const Phase& ph, const TA* arena, int64_t a_shift, const TX* X,
-                         const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q, cudaStream_t s) {
-  if (ph.n_tiles == 0 || q == 0) return cudaSuccess;
-  if (q > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
-#define HMAT_GEMM_BN(BMV)                                                                              \
-  if (q <= 16) return launch<TA, TX, TY, TC, BMV, 16>(h, ph, arena, a_shift, X, x_map, Y, y_map, q, s); \
-  if (q <= 32) return launch<TA, TX, TY, TC, BMV, 32>(h, ph, arena, a_shift, X, x_map, Y, y_map, q, s); \
-  return launch<TA, TX, TY, TC, BMV, 64>(h, ph, arena, a_shift, X, x_map, Y, y_map, q, s);
-  switch (ph.tile_rows) {
-    case 16: { HMAT_GEMM_BN(16) }
-    case 32: { HMAT_GEMM_BN(32) }
-    default: { HMAT_GEMM_BN(64) }
-  }
-#undef HMAT_GEMM_BN
+// The column shape used when none was tuned: the narrowest tile that holds q.
+inline int default_col_shape(int64_t q) {
+  for (int c = 0; c < kColShapes; ++c)
+    if (kColBN[c] >= q) return c;
+  return kColShapes - 1;
 }
 
+// One launch of a phase: the tile-row class of the launch picks BM, `shape` (an index
+// into kColBN, or -1 for the default) the column tile. `n_tiles` (at most the phase's)
+// limits the launch to the first tiles of the phase, the longest ones (the tuner times
+// such prefixes of long phases).
+template <typename TA, typename TX, typename TY, typename TC>
+cudaError_t launch_phase(const Handle& h, const Phase& ph, int shape, int64_t n_tiles, const TA* arena,
+                         int64_t a_shift, const TX* X, const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q,
+                         cudaStream_t s) {
+  if (n_tiles < 0 || n_tiles > ph.n_tiles) n_tiles = ph.n_tiles;
+  if (n_tiles == 0 || q == 0) return cudaSuccess;
+  if (q > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+  if (shape < 0) shape = default_col_shape(q);
+  if (shape >= kColShapes) return cudaErrorInvalidValue;
+#define HMAT_GEMM_L(BMV, BNV, TMV, TNV) \
+  return launch<TA, TX, TY, TC, BMV, BNV, TMV, TNV>(h, ph, n_tiles, arena, a_shift, X, x_map, Y, y_map, q, s)
+#define HMAT_GEMM_BN(BMV)                      \
+  switch (shape) {                             \
+    case 0: HMAT_GEMM_L(BMV, 1, 1, 1);         \
+    case 1: HMAT_GEMM_L(BMV, 2, 1, 1);         \
+    case 2: HMAT_GEMM_L(BMV, 4, 2, 1);         \
+    case 3: HMAT_GEMM_L(BMV, 8, 2, 2);         \
+    case 4: HMAT_GEMM_L(BMV, 16, 4, 4);        \
+    case 5: HMAT_GEMM_L(BMV, 32, 4, 4);        \
+    default: HMAT_GEMM_L(BMV, 64, 4, 4);       \
+  }
+  switch (ph.tile_rows) {
+    case 16: HMAT_GEMM_BN(16)
+    case 32: HMAT_GEMM_BN(32)
+    default: HMAT_GEMM_BN(64)
+  }
+#undef HMAT_GEMM_BN
+#undef HMAT_GEMM_L
+}
 
 // FP32 variant for the far field of the mixed mode. FP32 arithmetic is 64x faster
 // than FP64 on GB300, so these launches are bound by memory latency along each

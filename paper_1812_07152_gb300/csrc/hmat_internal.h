@@ -132,6 +132,16 @@ struct EvalContext {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
+// Tile shapes chosen by hmat_autotune for one (q, mode) of a handle. Every choice
+// gives bitwise the same result as the default; only the time differs.
+struct TuneEntry {
+  int64_t q = 0;
+  int mode = 0;
+  std::vector<int8_t> shape;   // FP64: column shape (index into kColBN) per entry of Handle::phases
+  int n_t = 0;                 // mixed: columns per tensor-core CTA
+  double default_ms = 0, tuned_ms = 0;
+};
+
 struct Handle {
   int device = -1;
   int64_t n_points = 0;
@@ -170,6 +180,7 @@ struct Handle {
   int64_t arena32_shift = 0;     // FP64-arena offset of arena32[0]
 
   struct EvalContext* ctx = nullptr;  // the handle's own evaluation state (hmat_eval)
+  std::vector<TuneEntry> tuned;       // hmat_autotune results, one per (q, mode)
 
   // per-launch event timing (hmat_profile / hmat_phase_times)
   struct ProfRecord {
@@ -228,6 +239,8 @@ cudaError_t launch_w_split(const TcNear& tc, int64_t total_kchunks, const double
 cudaError_t launch_near_tc(const TcNear& tc, int64_t n_work, const uint8_t* wsplit, const unsigned long long* wmax,
                            const int64_t* perm, double* Y, int64_t q, int n_t, int n_ct, int* status,
                            cudaStream_t stream);
+// One bounded wait that nothing completes: sets HMAT_ETIMEOUT in *status after limit_ns.
+cudaError_t launch_wait_selftest(int* status, uint64_t limit_ns, cudaStream_t stream);
 // FP32 grouped GEMM of one far-field phase of the mixed mode (hmat_far32.cu).
 cudaError_t launch_f32_phase(const Handle& h, const Phase& ph, const float* X, const int64_t* x_map, void* Y,
                              bool y_is_f64, const int64_t* y_map, int64_t q, cudaStream_t stream);
@@ -242,9 +255,22 @@ hmat_status ctx_reserve(const Handle& h, EvalContext* c, int64_t q, int mode);  
 hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int64_t q, int mode, cudaStream_t s);
 hmat_status cuda_status(cudaError_t e);
 
-// Launch the FP64 grouped GEMM of one phase on `stream`.
+// Launch the FP64 grouped GEMM of one phase on `stream`: column shape `shape` (-1:
+// the default for q), the first `n_tiles` tiles of the phase (-1: all).
 cudaError_t launch_fp64_phase(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map,
-                              double* Y, const int64_t* y_map, int64_t q, cudaStream_t stream);
+                              double* Y, const int64_t* y_map, int64_t q, int shape, int64_t n_tiles,
+                              cudaStream_t stream);
+int fp64_default_shape(int64_t q);
+int fp64_shape_columns(int shape);
+
+// Tensor-core column tiling of the mixed mode (hmat_eval.cpp): the candidate widths
+// for q (multiples of 16, at most 128; the first is the default), the widest
+// workspace any of them needs (columns = n_ct * n_t), and the width an evaluation
+// uses (the tuned one when there is one).
+std::vector<int> mixed_nt_candidates(int64_t q);
+int64_t mixed_cols_bound(int64_t q);
+void mixed_tiles(const Handle& h, int64_t q, int* n_t, int64_t* n_ct);
+const TuneEntry* find_tuned(const Handle& h, int64_t q, int mode);
 
 }  // namespace hmat
 

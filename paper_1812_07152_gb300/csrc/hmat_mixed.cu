@@ -66,9 +66,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase of `bar` with the given parity; false after kWaitNs or when
+// Wait for the phase of `bar` with the given parity; false after limit_ns or when
 // another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t limit_ns = kWaitNs) {
   uint64_t t0 = 0;
   for (uint32_t i = 0;; ++i) {
     if (mbar_try(bar, parity)) return true;
@@ -76,7 +77,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
       if (*abort_flag) return false;
       const uint64_t t = gtimer();
       if (t0 == 0) t0 = t;
-      else if (t - t0 > kWaitNs) return false;
+      else if (t - t0 > limit_ns) return false;
     }
   }
 }
@@ -543,6 +544,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
   }
 }
 
+// Failure-detection self-test: one thread waits, through the routine every wait of
+// k_near_tc uses, on a barrier that nothing arrives at; the wait gives up after
+// limit_ns and the status word gets HMAT_ETIMEOUT as a stuck evaluation would set it.
+// No copy or MMA is in flight, so returning is all the clean-up there is.
+__global__ void k_wait_selftest(int* status, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x != 0) return;
+  mbar_init(smem_u32(&bar), 1);
+  abort_flag = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(smem_u32(&bar), 0, &abort_flag, limit_ns)) atomicCAS(status, 0, (int)HMAT_ETIMEOUT);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -585,6 +600,11 @@ cudaError_t launch_w_split(const TcNear& tc, int64_t total_kchunks, const double
   if (grid == 0) return cudaSuccess;
   if (grid > 2147483647LL) return cudaErrorInvalidValue;
   k_w_split<<<(unsigned)grid, 256, 0, stream>>>(tc, W, perm, q, n_t, n_ct, wmax, wsplit, w32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(int* status, uint64_t limit_ns, cudaStream_t stream) {
+  k_wait_selftest<<<1, 32, 0, stream>>>(status, limit_ns);
   return cudaGetLastError();
 }
 

@@ -55,12 +55,15 @@ extern "C" hmat_status hmat_eval_noalloc(hmat_t h, const double* W, double* Y, i
   double* ws = base;
   double* us = base + half;
   cudaStream_t s = (cudaStream_t)stream;
-  for (const Phase& ph : h->phases) {
+  const TuneEntry* tuned = find_tuned(*h, q, HMAT_MODE_FP64);
+  for (size_t i = 0; i < h->phases.size(); ++i) {
+    const Phase& ph = h->phases[i];
     const double* X = ph.x == MAT_USER ? W : (ph.x == MAT_SKEL_W ? ws : us);
     double* Yd = ph.y == MAT_USER ? Y : (ph.y == MAT_SKEL_W ? ws : us);
     const int64_t* xm = phase_x_map(*h, ph);
     const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
-    const cudaError_t e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, s);
+    const int shape = tuned && i < tuned->shape.size() ? tuned->shape[i] : -1;
+    const cudaError_t e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, shape, -1, s);
     if (e != cudaSuccess) return HMAT_ECUDA;
   }
   return HMAT_OK;

@@ -89,6 +89,11 @@ class HmatServerParams(ctypes.Structure):
                 ("mode", ctypes.c_int)]
 
 
+class HmatTuneReport(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int64), ("mode", ctypes.c_int32), ("launches_tuned", ctypes.c_int32),
+                ("default_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double), ("near_cols", ctypes.c_int32)]
+
+
 class HmatError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {hmat_strerror(status)} (status {status})")
@@ -131,13 +136,16 @@ def library() -> ctypes.CDLL:
         lib.hmat_status_poll.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         lib.hmat_info.argtypes = [ctypes.c_void_p, _c_i64p, ctypes.c_int]
         lib.hmat_free.argtypes = [ctypes.c_void_p]
+        lib.hmat_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.POINTER(HmatTuneReport)]
+        lib.hmat_selftest_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         lib.hmat_strerror.argtypes = [ctypes.c_int]
         lib.hmat_strerror.restype = ctypes.c_char_p
         for name in ("hmat_load", "hmat_build", "hmat_structure", "hmat_eval", "hmat_reserve", "hmat_status_poll",
                      "hmat_info", "hmat_free", "hmat_eval_host", "hmat_profile", "hmat_phase_times",
                      "hmat_measure_fp64_peak", "hmat_batch_create", "hmat_batch_eval", "hmat_batch_free",
                      "hmat_server_create", "hmat_server_submit", "hmat_server_wait", "hmat_server_stats",
-                     "hmat_server_free"):
+                     "hmat_server_free", "hmat_autotune", "hmat_selftest_timeout"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -273,6 +281,15 @@ def hmat_measure_fp64_peak() -> float:
     return float(g.value)
 
 
+def hmat_autotune(handle: int, q: int, mode: int = HMAT_MODE_FP64, stream=None) -> dict:
+    """Time the tile-shape candidates for (q, mode) on the device and keep the fastest
+    for later evaluations of the handle; returns the call's report."""
+    rep = HmatTuneReport()
+    _check(library().hmat_autotune(handle, int(q), int(mode), _stream(stream), ctypes.byref(rep)), "hmat_autotune")
+    return {"q": int(rep.q), "mode": int(rep.mode), "launches_tuned": int(rep.launches_tuned),
+            "default_ms": float(rep.default_ms), "tuned_ms": float(rep.tuned_ms), "near_cols": int(rep.near_cols)}
+
+
 def hmat_reserve(handle: int, q_max: int) -> None:
     _check(library().hmat_reserve(handle, int(q_max)), "hmat_reserve")
 
@@ -280,6 +297,12 @@ def hmat_reserve(handle: int, q_max: int) -> None:
 def hmat_status_poll(handle: int, stream=None) -> int:
     """Synchronise the stream and return (and clear) the device status word."""
     return int(library().hmat_status_poll(handle, _stream(stream)))
+
+
+def hmat_selftest_timeout(handle: int, limit_ns: int, stream=None) -> None:
+    """Enqueue one bounded device wait that runs out after limit_ns and latches
+    HMAT_ETIMEOUT in the handle's status word (read it with hmat_status_poll)."""
+    _check(library().hmat_selftest_timeout(handle, int(limit_ns), _stream(stream)), "hmat_selftest_timeout")
 
 
 def hmat_info(handle: int) -> dict:

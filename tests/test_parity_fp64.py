@@ -50,6 +50,8 @@ CASES = [
     ("h2_imq3d_n262144", 5000, 65, (("leaf_size", 40),)),       # deeper tree, q one past a tile
     ("hss_uniform3d_n2048", 1000, 1, ()),                       # q = 1
     ("hss_uniform3d_n2048", 777, 3, (("leaf_size", 50),)),      # q = 3, odd sizes
+    ("h2_gmm8d_n65536", 4096, 2, ()),                           # q = 2 (2-column tiles)
+    ("h2_imq3d_n262144", 3000, 8, ()),                          # q = 8 (8-column tiles)
     ("h2_imq3d_n262144", 2500, 17, (("admissibility", "none"),)),          # all near
     ("hss_uniform3d_n2048", 1500, 20, (("tol", 0.0), ("max_rank", 10 ** 6))),  # rank = |rows|
     ("hss_uniform3d_n2048", 1200, 9, (("tol", 1.0),)),          # every rank 0: far field vanishes
