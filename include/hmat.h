@@ -373,7 +373,10 @@ hmat_status hmat_selftest_timeout(hmat_t h, int64_t limit_ns, void* stream);
 /* hmat_info - sizes of the loaded HMatrix: out[0] = n_points, out[1] = levels,
  * out[2] = near entries, out[3] = far entries, out[4] = stored near values,
  * out[5] = stored basis values, out[6] = stored coupling values,
- * out[7] = sum of ranks, out[8] = device bytes held by the handle. */
+ * out[7] = sum of ranks, out[8] = device bytes held by the handle,
+ * out[9] = engine of the mixed mode's coupling reduction: 0 no mixed copy, 1 FP32
+ * CUDA cores, 2 tensor cores (chosen at load: tensor cores when the stored coupling
+ * values fill at least a quarter of the padded 128 x 64 tiles they would occupy). */
 hmat_status hmat_info(hmat_t h, int64_t* out, int n_out);
 
 /* hmat_free - release every device and host resource of the handle (synchronises the device). */

@@ -188,6 +188,12 @@ class Uploader {
   int cur_ = 0;
 };
 
+void free_tc(TcProduct* p) {
+  cudaFree(p->tiles);
+  cudaFree(p->meta);
+  *p = TcProduct{};
+}
+
 void free_device(Handle* h) {
   for (auto& r : h->prof) {
     h->event_pool.push_back(r.start);
@@ -198,10 +204,10 @@ void free_device(Handle* h) {
   h->event_pool.clear();
   ctx_destroy(h->ctx);
   h->ctx = nullptr;
-  cudaFree(h->tc_tiles);
-  cudaFree(h->tc_meta);
+  free_tc(&h->tc_near);
+  free_tc(&h->tc_far);
   cudaFree(h->arena32);
-  h->tc_tiles = nullptr; h->tc_meta = nullptr; h->arena32 = nullptr; h->has_mixed = false;
+  h->arena32 = nullptr; h->has_mixed = false;
   cudaFree(h->arena);
   cudaFree(h->far_rows);
   h->far_rows = nullptr;
@@ -226,82 +232,90 @@ cudaError_t upload(T** dst, const std::vector<T>& src, int64_t* bytes) {
 
 
 
-// Mixed-precision copies of a loaded HMatrix (HMAT_LOAD_MIXED): the near blocks as
-// FP16 hi/lo tensor-core tiles (packed on the device from the FP64 arena, one scale
-// exponent per 128-row m-tile of a target leaf) and the bases and coupling blocks
-// (the arena from basis_begin on) as FP32.
-hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const std::vector<int64_t>& near_off,
-                        int64_t basis_begin) {
-  const int64_t nl = v.n_leaves, fl = v.first_leaf;
-  std::vector<int32_t> leaf_size(nl), leaf_kc(nl), mt_base(nl + 1);
-  std::vector<int64_t> leaf_begin(nl), leaf_kcum(nl + 1), near_ptr(d->near_ptr, d->near_ptr + nl + 1);
-  std::vector<int32_t> near_idx(d->near_idx, d->near_idx + v.n_near);
+// Host description of one tensor-core product family (see TcLists): a CSR list of
+// (target, source) blocks over one node index space and where each block sits in
+// the FP64 arena.
+struct TcSpec {
+  int64_t n_nodes = 0;
+  std::vector<int64_t> ptr;      // per target: CSR into the entries (n_nodes + 1)
+  std::vector<int32_t> idx;      // per entry: source node
+  std::vector<int64_t> blk_off;  // per entry: arena offset of the block's (row 0, column 0)
+  std::vector<int32_t> blk_ld;   // per entry: row stride of the block
+  std::vector<int32_t> size;     // per node: rows
+  std::vector<int64_t> begin;    // per node: first row
+  std::vector<char> target;      // per node: gets (target, m-tile) work items
+};
+
+// Packs one product family on the device: per-m-tile scale exponents, then the hi/lo
+// tile pairs of every (entry, m-tile of its target, k-chunk of its source), and
+// uploads the metadata and the (target, m-tile) work list, longest lists first.
+hmat_status build_tc(Handle* h, const TcSpec& sp, TcProduct* out) {
+  const int64_t nn = sp.n_nodes;
+  std::vector<int32_t> kc(nn), mt_base(nn + 1), n_mt(nn);
+  std::vector<int64_t> kcum(nn + 1);
   mt_base[0] = 0;
-  leaf_kcum[0] = 0;
-  for (int64_t i = 0; i < nl; ++i) {
-    leaf_size[i] = (int32_t)h->size[fl + i];
-    leaf_begin[i] = h->begin[fl + i];
-    leaf_kc[i] = (leaf_size[i] + kTcK - 1) / kTcK;
-    mt_base[i + 1] = mt_base[i] + (leaf_size[i] + kTcRows - 1) / kTcRows;
-    leaf_kcum[i + 1] = leaf_kcum[i] + leaf_kc[i];
+  kcum[0] = 0;
+  for (int64_t i = 0; i < nn; ++i) {
+    kc[i] = (sp.size[i] + kTcK - 1) / kTcK;
+    n_mt[i] = sp.target[i] ? (sp.size[i] + kTcRows - 1) / kTcRows : 0;
+    mt_base[i + 1] = mt_base[i] + n_mt[i];
+    kcum[i + 1] = kcum[i] + kc[i];
   }
-  const int64_t n_mtiles = mt_base[nl];
-  h->total_kchunks = leaf_kcum[nl];
-  std::vector<int32_t> mtile_leaf(n_mtiles), mtile_mt(n_mtiles), chunk_leaf(h->total_kchunks), chunk_c(h->total_kchunks);
-  for (int64_t i = 0; i < nl; ++i) {
-    for (int32_t m = 0; m < mt_base[i + 1] - mt_base[i]; ++m) {
-      mtile_leaf[mt_base[i] + m] = (int32_t)i;
+  const int64_t n_mtiles = mt_base[nn];
+  out->n_chunks = kcum[nn];
+  std::vector<int32_t> mtile_node(n_mtiles), mtile_mt(n_mtiles), chunk_node(out->n_chunks), chunk_c(out->n_chunks);
+  for (int64_t i = 0; i < nn; ++i) {
+    for (int32_t m = 0; m < n_mt[i]; ++m) {
+      mtile_node[mt_base[i] + m] = (int32_t)i;
       mtile_mt[mt_base[i] + m] = m;
     }
-    for (int32_t c = 0; c < leaf_kc[i]; ++c) {
-      chunk_leaf[leaf_kcum[i] + c] = (int32_t)i;
-      chunk_c[leaf_kcum[i] + c] = c;
+    for (int32_t c = 0; c < kc[i]; ++c) {
+      chunk_node[kcum[i] + c] = (int32_t)i;
+      chunk_c[kcum[i] + c] = c;
     }
   }
-  // tile pairs per near entry: m-tiles of the target x k-chunks of the source
-  std::vector<int64_t> a_off(v.n_near);
+  const int64_t n_entries = sp.ptr[nn];
+  std::vector<int64_t> a_off(n_entries, 0);
   std::vector<TcPackJob> jobs;
   int64_t bytes = 0;
-  for (int64_t i = 0; i < nl; ++i)
-    for (int64_t e = near_ptr[i]; e < near_ptr[i + 1]; ++e) {
-      const int32_t j = near_idx[e];
-      const int32_t n_mt = mt_base[i + 1] - mt_base[i];
+  for (int64_t i = 0; i < nn; ++i)
+    for (int64_t e = sp.ptr[i]; e < sp.ptr[i + 1]; ++e) {
+      const int32_t j = sp.idx[e];
       a_off[e] = bytes;
-      for (int32_t m = 0; m < n_mt; ++m)
-        for (int32_t c = 0; c < leaf_kc[j]; ++c)
-          jobs.push_back(TcPackJob{bytes + ((int64_t)m * leaf_kc[j] + c) * 2 * kTcTileBytes, near_off[e], leaf_size[i],
-                                   leaf_size[j], m * kTcRows, c * kTcK, mt_base[i] + m, 0});
-      bytes += (int64_t)n_mt * leaf_kc[j] * 2 * kTcTileBytes;
+      for (int32_t m = 0; m < n_mt[i]; ++m)
+        for (int32_t c = 0; c < kc[j]; ++c)
+          jobs.push_back(TcPackJob{bytes + ((int64_t)m * kc[j] + c) * 2 * kTcTileBytes, sp.blk_off[e], sp.size[i],
+                                   sp.size[j], m * kTcRows, c * kTcK, mt_base[i] + m, sp.blk_ld[e]});
+      bytes += (int64_t)n_mt[i] * kc[j] * 2 * kTcTileBytes;
     }
-  // (leaf, m-tile) work items, the longest near lists first
   std::vector<std::pair<int64_t, TcTile>> work;
-  for (int64_t i = 0; i < nl; ++i) {
+  for (int64_t i = 0; i < nn; ++i) {
     int64_t cost = 0;
-    for (int64_t e = near_ptr[i]; e < near_ptr[i + 1]; ++e) cost += leaf_kc[near_idx[e]];
-    for (int32_t m = 0; m < mt_base[i + 1] - mt_base[i]; ++m) work.push_back({cost, TcTile{(int32_t)i, m}});
+    for (int64_t e = sp.ptr[i]; e < sp.ptr[i + 1]; ++e) cost += kc[sp.idx[e]];
+    for (int32_t m = 0; m < n_mt[i]; ++m) work.push_back({cost, TcTile{(int32_t)i, m}});
   }
   std::stable_sort(work.begin(), work.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
   std::vector<TcTile> work_list;
   for (auto& w : work) work_list.push_back(w.second);
-  h->n_tc_work = (int64_t)work_list.size();
+  out->n_work = (int64_t)work_list.size();
 
   // one allocation for the permanent metadata
   struct Part { const void* src; size_t bytes; void** dst; };
-  int64_t* d_a_off; int64_t* d_near_ptr; int32_t* d_near_idx; int32_t* d_kc; int64_t* d_kcum; int64_t* d_begin;
-  int32_t* d_size; int32_t* d_mt_base; int32_t* d_scale; TcTile* d_work; int32_t* d_chunk_leaf; int32_t* d_chunk_c;
+  int64_t* d_a_off; int64_t* d_ptr; int32_t* d_idx; int32_t* d_kc; int64_t* d_kcum; int64_t* d_begin;
+  int32_t* d_size; int32_t* d_mt_base; int32_t* d_scale; TcTile* d_work; int32_t* d_chunk_node; int32_t* d_chunk_c;
   std::vector<int32_t> scale_zero(std::max<int64_t>(n_mtiles, 1), 0);
   Part parts[] = {
       {a_off.data(), a_off.size() * 8, (void**)&d_a_off},
-      {near_ptr.data(), near_ptr.size() * 8, (void**)&d_near_ptr},
-      {near_idx.data(), near_idx.size() * 4, (void**)&d_near_idx},
-      {leaf_kc.data(), leaf_kc.size() * 4, (void**)&d_kc},
-      {leaf_kcum.data(), leaf_kcum.size() * 8, (void**)&d_kcum},
-      {leaf_begin.data(), leaf_begin.size() * 8, (void**)&d_begin},
-      {leaf_size.data(), leaf_size.size() * 4, (void**)&d_size},
+      {sp.ptr.data(), sp.ptr.size() * 8, (void**)&d_ptr},
+      {sp.idx.data(), sp.idx.size() * 4, (void**)&d_idx},
+      {kc.data(), kc.size() * 4, (void**)&d_kc},
+      {kcum.data(), kcum.size() * 8, (void**)&d_kcum},
+      {sp.begin.data(), sp.begin.size() * 8, (void**)&d_begin},
+      {sp.size.data(), sp.size.size() * 4, (void**)&d_size},
       {mt_base.data(), mt_base.size() * 4, (void**)&d_mt_base},
       {scale_zero.data(), scale_zero.size() * 4, (void**)&d_scale},
       {work_list.data(), work_list.size() * sizeof(TcTile), (void**)&d_work},
-      {chunk_leaf.data(), chunk_leaf.size() * 4, (void**)&d_chunk_leaf},
+      {chunk_node.data(), chunk_node.size() * 4, (void**)&d_chunk_node},
       {chunk_c.data(), chunk_c.size() * 4, (void**)&d_chunk_c},
   };
   size_t total = 0;
@@ -309,7 +323,7 @@ hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const
   uint8_t* meta = nullptr;
   cudaError_t e = cudaMalloc((void**)&meta, total);
   if (e != cudaSuccess) return cuda_status(e);
-  h->tc_meta = meta;
+  out->meta = meta;
   h->device_bytes += (int64_t)total;
   size_t o = 0;
   for (auto& p : parts) {
@@ -318,36 +332,97 @@ hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const
       return cuda_status(e);
     o += (p.bytes + 255) / 256 * 256 + 256;
   }
-  h->tc = TcNear{nullptr, d_a_off, d_near_ptr, d_near_idx, d_kc, d_kcum, d_begin, d_size, d_mt_base, d_scale,
-                 d_work, d_chunk_leaf, d_chunk_c};
+  out->dev = TcLists{nullptr, d_a_off, d_ptr, d_idx, d_kc, d_kcum, d_begin, d_size, d_mt_base, d_scale,
+                     d_work, d_chunk_node, d_chunk_c};
 
   // tiles: scale exponents, then the packed hi/lo pairs
-  if ((e = cudaMalloc((void**)&h->tc_tiles, (size_t)std::max<int64_t>(bytes, 256))) != cudaSuccess)
+  if ((e = cudaMalloc((void**)&out->tiles, (size_t)std::max<int64_t>(bytes, 256))) != cudaSuccess)
     return cuda_status(e);
-  h->tc_bytes = bytes;
+  out->tile_bytes = bytes;
   h->device_bytes += bytes;
-  h->tc.tiles = h->tc_tiles;
-  int64_t* d_near_off = nullptr; int32_t* d_mleaf = nullptr; int32_t* d_mmt = nullptr; TcPackJob* d_jobs = nullptr;
+  out->dev.tiles = out->tiles;
+  int64_t* d_blk_off = nullptr; int32_t* d_blk_ld = nullptr; int32_t* d_mnode = nullptr; int32_t* d_mmt = nullptr;
+  TcPackJob* d_jobs = nullptr;
   int64_t scratch = 0;
-  e = upload(&d_near_off, near_off, &scratch);
-  if (e == cudaSuccess) e = upload(&d_mleaf, mtile_leaf, &scratch);
+  e = upload(&d_blk_off, sp.blk_off, &scratch);
+  if (e == cudaSuccess) e = upload(&d_blk_ld, sp.blk_ld, &scratch);
+  if (e == cudaSuccess) e = upload(&d_mnode, mtile_node, &scratch);
   if (e == cudaSuccess) e = upload(&d_mmt, mtile_mt, &scratch);
   if (e == cudaSuccess) e = upload(&d_jobs, jobs, &scratch);
-  if (e == cudaSuccess) e = launch_tc_scale(h->tc, d_near_off, h->arena, nl, n_mtiles, d_mleaf, d_mmt, d_scale, 0);
-  if (e == cudaSuccess) e = launch_tc_pack(d_jobs, (int64_t)jobs.size(), h->arena, d_scale, h->tc_tiles, 0);
+  if (e == cudaSuccess) e = launch_tc_scale(out->dev, d_blk_off, d_blk_ld, h->arena, n_mtiles, d_mnode, d_mmt, d_scale, 0);
+  if (e == cudaSuccess) e = launch_tc_pack(d_jobs, (int64_t)jobs.size(), h->arena, d_scale, out->tiles, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  cudaFree(d_near_off);
-  cudaFree(d_mleaf);
+  cudaFree(d_blk_off);
+  cudaFree(d_blk_ld);
+  cudaFree(d_mnode);
   cudaFree(d_mmt);
   cudaFree(d_jobs);
-  if (e != cudaSuccess) return cuda_status(e);
+  return e == cudaSuccess ? HMAT_OK : cuda_status(e);
+}
 
-  // FP32 copy of the bases and coupling blocks
+// Mixed-precision copies of a loaded HMatrix (HMAT_LOAD_MIXED): the near blocks and
+// the coupling blocks as FP16 hi/lo tensor-core tiles (packed on the device from the
+// FP64 arena, one scale exponent per 128-row m-tile of a target) and the bases (the
+// arena from basis_begin to coupling_begin) as FP32.
+hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const std::vector<int64_t>& near_off,
+                        const std::vector<int64_t>& far_task_off, const std::vector<int64_t>& far_off,
+                        const std::vector<int64_t>& far_k, int64_t basis_begin, int64_t coupling_begin) {
+  const int64_t nl = v.n_leaves, fl = v.first_leaf;
+  {  // near field: targets and sources are the leaves
+    TcSpec sp;
+    sp.n_nodes = nl;
+    sp.ptr.assign(d->near_ptr, d->near_ptr + nl + 1);
+    sp.idx.assign(d->near_idx, d->near_idx + v.n_near);
+    sp.size.resize(nl);
+    sp.begin.resize(nl);
+    sp.target.assign(nl, 1);
+    for (int64_t i = 0; i < nl; ++i) {
+      sp.size[i] = (int32_t)h->size[fl + i];
+      sp.begin[i] = h->begin[fl + i];
+    }
+    sp.blk_off = near_off;
+    sp.blk_ld.resize(v.n_near);
+    for (int64_t e = 0; e < v.n_near; ++e) sp.blk_ld[e] = sp.size[sp.idx[e]];
+    hmat_status st = build_tc(h, sp, &h->tc_near);
+    if (st != HMAT_OK) return st;
+  }
+  if (h->tc_coupling) {  // coupling: targets are the nodes with a basis, sources their
+                        // far partners; B_ab is the column slice of B_a starting at far_off
+    TcSpec sp;
+    const int64_t nn = v.n_nodes;
+    sp.n_nodes = nn;
+    sp.ptr.assign(d->far_ptr, d->far_ptr + nn + 1);
+    sp.idx.assign(d->far_idx, d->far_idx + v.n_far);
+    sp.size.resize(nn);
+    sp.begin.resize(nn);
+    sp.target.assign(nn, 0);
+    for (int64_t a = 0; a < nn; ++a) {
+      sp.size[a] = h->rank[a];
+      sp.begin[a] = h->skel_off[a];
+      sp.target[a] = a >= 1 && h->rank[a] > 0;
+    }
+    sp.blk_off.assign(v.n_far, 0);
+    sp.blk_ld.assign(v.n_far, 1);
+    for (int64_t a = 0; a < nn; ++a) {
+      if (far_task_off[a] < 0) continue;
+      for (int64_t e = d->far_ptr[a]; e < d->far_ptr[a + 1]; ++e) {
+        sp.blk_off[e] = far_task_off[a] + far_off[e];
+        sp.blk_ld[e] = (int32_t)far_k[a];
+      }
+    }
+    hmat_status st = build_tc(h, sp, &h->tc_far);
+    if (st != HMAT_OK) return st;
+  }
+
+  // FP32 copy of the bases (the upward and downward passes), and of the coupling
+  // blocks when the coupling runs in FP32
+  cudaError_t e;
   h->arena32_shift = basis_begin;
-  const int64_t n32 = std::max<int64_t>(h->arena_values - basis_begin, 1);
+  const int64_t end32 = h->tc_coupling ? coupling_begin : h->arena_values;
+  const int64_t n32 = std::max<int64_t>(end32 - basis_begin, 1);
   if ((e = cudaMalloc((void**)&h->arena32, (size_t)n32 * sizeof(float))) != cudaSuccess) return cuda_status(e);
   h->device_bytes += n32 * (int64_t)sizeof(float);
-  if ((e = launch_to_f32(h->arena + basis_begin, h->arena32, h->arena_values - basis_begin, 0)) != cudaSuccess)
+  if ((e = launch_to_f32(h->arena + basis_begin, h->arena32, end32 - basis_begin, 0)) != cudaSuccess)
     return cuda_status(e);
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_status(e);
   h->has_mixed = true;
@@ -415,6 +490,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     h->basis_values += cnt;
     off = align_up(off + cnt, kAlignValues);
   }
+  const int64_t coupling_region_begin = off;
   // coupling: the blocks of one target node side by side, B_a = [B_ab1 | B_ab2 | ...]
   // (s_a x K_a, K_a = sum of the partners' ranks), so the far-field reduction of a
   // node is one product B_a [w_b1; w_b2; ...] whose right operand is gathered through
@@ -436,6 +512,20 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     off = align_up(off + cnt, kAlignValues);
   }
   h->arena_values = std::max<int64_t>(off, 1);
+
+  // ---- mixed mode: coupling on the tensor cores when the 128 x 64 tiles are well
+  // filled (ranks of about 64 and more); small ranks would leave most of every tile
+  // padding, and then the FP32 grouped GEMM on the CUDA cores is faster
+  if (flags & HMAT_LOAD_MIXED) {
+    double padded = 0.0;
+    for (int64_t a = 1; a < v.n_nodes; ++a) {
+      if (h->rank[a] == 0) continue;
+      const double rows = (double)((h->rank[a] + kTcRows - 1) / kTcRows * kTcRows);
+      for (int64_t e = d->far_ptr[a]; e < d->far_ptr[a + 1]; ++e)
+        padded += rows * (double)((h->rank[d->far_idx[e]] + kTcK - 1) / kTcK * kTcK);
+    }
+    h->tc_coupling = padded > 0.0 && (double)h->coupling_values >= kTcCouplingFill * padded;
+  }
 
   // ---- work lists
   std::vector<GemmTask> tasks;
@@ -467,11 +557,12 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
       ph.n_tiles = (int64_t)tiles.size() - ph.tile_begin;
       if (ph.n_tiles > 0) h->phases.push_back(ph);
     }
-    // the FP32 far field of the mixed mode splits each task's K over warp groups, so a
-    // phase of long-K tasks (coupling: hundreds of partners) is bound by its longest task:
-    // one launch of 16-row tiles for all its tasks; the other phases (short K) keep one
-    // launch per row-tile size; the near field runs on tensor cores, not here
-    if (kind == PH_NEAR) return;
+    // The mixed mode runs the upward and downward passes as FP32 launches of the same
+    // tiles; the near field runs on the tensor cores, and so does the coupling when
+    // its tiles fill well. The FP32 kernel splits each task's K over warp groups, so
+    // an FP32 coupling (long K: hundreds of partners) is bound by its longest task:
+    // one launch of 16-row tiles for all its tasks, longest K first.
+    if (kind == PH_NEAR || (kind == PH_COUPLING && h->tc_coupling)) return;
     if (kind != PH_COUPLING) {
       for (const Phase& p : h->phases)
         if (p.kind == kind && p.level == level) h->phases32.push_back(p);
@@ -647,7 +738,8 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
   std::vector<int> zero(1, 0);
   if ((e = upload(&h->status, zero, &h->device_bytes)) != cudaSuccess) return fail(e);
   if (flags & HMAT_LOAD_MIXED) {
-    hmat_status ms = build_mixed(h.get(), d, v, near_off, basis_region_begin);
+    hmat_status ms = build_mixed(h.get(), d, v, near_off, far_task_off, far_off, far_k, basis_region_begin,
+                                 coupling_region_begin);
     if (ms != HMAT_OK) {
       free_device(h.get());
       return ms;
@@ -708,9 +800,10 @@ extern "C" hmat_status hmat_selftest_timeout(hmat_t h, int64_t limit_ns, void* s
 extern "C" hmat_status hmat_info(hmat_t h, int64_t* out, int n_out) {
   if (!h || !out || n_out < 0) return HMAT_EINVAL;
   const int64_t held = h->device_bytes + (h->ctx ? h->ctx->block_bytes + 16 * h->ctx->host_cap : 0);
-  const int64_t vals[9] = {h->n_points, h->levels, h->n_near, h->n_far, h->near_values,
-                           h->basis_values, h->coupling_values, h->sum_rank, held};
-  for (int i = 0; i < n_out && i < 9; ++i) out[i] = vals[i];
+  const int64_t engine = !h->has_mixed ? 0 : (h->tc_coupling ? 2 : 1);
+  const int64_t vals[10] = {h->n_points, h->levels, h->n_near, h->n_far, h->near_values,
+                            h->basis_values, h->coupling_values, h->sum_rank, held, engine};
+  for (int i = 0; i < n_out && i < 10; ++i) out[i] = vals[i];
   return HMAT_OK;
 }
 

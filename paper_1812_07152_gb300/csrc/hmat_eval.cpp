@@ -133,7 +133,9 @@ void ctx_destroy(EvalContext* c) {
 int64_t ctx_bytes(const Handle& h, int64_t q, int mode) {
   const int64_t r = std::max<int64_t>(h.sum_rank, 1);
   if (mode == HMAT_MODE_MIXED) {
-    return align_up(sizeof(unsigned long long)) + align_up(h.total_kchunks * mixed_cols_bound(q) * 256) +
+    const int64_t cols = mixed_cols_bound(q);
+    return 2 * align_up(sizeof(unsigned long long)) + align_up(h.tc_near.n_chunks * cols * 256) +
+           align_up(h.tc_far.n_chunks * cols * 256) +
            align_up(std::max<int64_t>(h.n_points, 1) * q * 4) + 2 * align_up(r * q * 4);
   }
   return 2 * align_up(r * q * 8);
@@ -148,12 +150,15 @@ void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* bas
     return x;
   };
   c->ws = c->us = nullptr;
-  c->wmax = nullptr;
-  c->wsplit = nullptr;
+  c->wmax = c->smax = nullptr;
+  c->wsplit = c->ssplit = nullptr;
   c->w32 = c->ws32 = c->us32 = nullptr;
   if (mode == HMAT_MODE_MIXED) {
+    const int64_t cols = mixed_cols_bound(q);
     c->wmax = (unsigned long long*)take(sizeof(unsigned long long));
-    c->wsplit = take(h.total_kchunks * mixed_cols_bound(q) * 256);
+    c->wsplit = take(h.tc_near.n_chunks * cols * 256);
+    c->smax = (unsigned long long*)take(sizeof(unsigned long long));
+    c->ssplit = take(h.tc_far.n_chunks * cols * 256);
     c->w32 = (float*)take(std::max<int64_t>(h.n_points, 1) * q * 4);
     c->ws32 = (float*)take(r * q * 4);
     c->us32 = (float*)take(r * q * 4);
@@ -190,8 +195,7 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
     int64_t n_ct;
     mixed_tiles(*h, q, &n_t, &n_ct);
     if (!prof_begin(h, HMAT_PHASE_SPLIT, s, &rec)) return HMAT_ECUDA;
-    e = launch_w_split(h->tc, h->total_kchunks, W, h->n_points * q, h->perm, q, n_t, (int)n_ct, c->wmax, c->wsplit,
-                       c->w32, s);
+    e = launch_split_f64(h->tc_near, W, h->n_points * q, h->perm, q, n_t, (int)n_ct, c->wmax, c->wsplit, c->w32, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;
     if (cudaEventRecord(c->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->ev_fork, 0) != cudaSuccess)
@@ -206,13 +210,27 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
       if (e != cudaSuccess) return cuda_status(e);
       return prof_end(h, rec, strm) ? HMAT_OK : HMAT_ECUDA;
     };
-    for (const Phase& ph : h->phases32) {
-      if (ph.kind == PH_DOWN_LEAF) continue;
-      if ((st = far_launch(ph, c->aux)) != HMAT_OK) return st;
+    // far chain on the side stream: upward pass, coupling (on the tensor cores after
+    // splitting the skeleton weights, or in FP32), downward transfers
+    for (const Phase& ph : h->phases32)
+      if (ph.kind == PH_UP_LEAF || ph.kind == PH_UP_TRANS || ph.kind == PH_COUPLING)
+        if ((st = far_launch(ph, c->aux)) != HMAT_OK) return st;
+    if (h->tc_coupling && h->tc_far.n_work > 0) {
+      if (!prof_begin(h, HMAT_PHASE_SPLIT, c->aux, &rec)) return HMAT_ECUDA;
+      e = launch_split_f32(h->tc_far, c->ws32, std::max<int64_t>(h->sum_rank, 1) * q, q, n_t, (int)n_ct, c->smax,
+                           c->ssplit, c->aux);
+      if (e != cudaSuccess) return cuda_status(e);
+      if (!prof_end(h, rec, c->aux)) return HMAT_ECUDA;
+      if (!prof_begin(h, HMAT_PHASE_COUPLING, c->aux, &rec)) return HMAT_ECUDA;
+      e = launch_tc_far(h->tc_far, c->ssplit, c->smax, c->us32, q, n_t, (int)n_ct, h->status, c->aux);
+      if (e != cudaSuccess) return cuda_status(e);
+      if (!prof_end(h, rec, c->aux)) return HMAT_ECUDA;
     }
+    for (const Phase& ph : h->phases32)
+      if (ph.kind == PH_DOWN_TRANS && (st = far_launch(ph, c->aux)) != HMAT_OK) return st;
     if (cudaEventRecord(c->ev_join, c->aux) != cudaSuccess) return HMAT_ECUDA;
     if (!prof_begin(h, HMAT_PHASE_NEAR, s, &rec)) return HMAT_ECUDA;
-    e = launch_near_tc(h->tc, h->n_tc_work, c->wsplit, c->wmax, h->perm, Y, q, n_t, (int)n_ct, h->status, s);
+    e = launch_tc_near(h->tc_near, c->wsplit, c->wmax, h->perm, Y, q, n_t, (int)n_ct, h->status, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;
     if (cudaStreamWaitEvent(s, c->ev_join, 0) != cudaSuccess) return HMAT_ECUDA;

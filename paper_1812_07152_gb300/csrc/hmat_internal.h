@@ -69,46 +69,65 @@ struct Phase {
   int32_t tile_rows;   // rows per CTA tile of this launch (16, 32 or 64)
 };
 
-// Mixed-precision near field (tensor cores). The near blocks of a target leaf are
-// cut into m-tiles of 128 rows and k-chunks of 64 columns; each (m-tile, k-chunk) is
-// stored as an FP16 hi tile and an FP16 lo tile (hi = fp16(x), lo = fp16(x - hi),
-// x = the value times 2^scale of its m-tile), 128 rows x 128 bytes each in the
-// canonical K-major 128-byte-swizzled layout of a tcgen05 operand, so one bulk copy
-// lands a tile in shared memory ready for the MMA.
+// Mixed-precision products on the tensor cores: the near field (targets = leaves,
+// blocks D_ij) and the coupling reduction (targets = tree nodes, blocks B_ab). A
+// target's blocks are cut into m-tiles of 128 rows and k-chunks of 64 columns; each
+// (m-tile, k-chunk) is stored as an FP16 hi tile and an FP16 lo tile (hi = fp16(x),
+// lo = fp16(x - hi), x = the value times 2^scale of its m-tile), 128 rows x 128
+// bytes each in the canonical K-major 128-byte-swizzled layout of a tcgen05 operand,
+// so one bulk copy lands a tile in shared memory ready for the MMA. The right-hand
+// operand (W for the near field, the skeleton weights w for the coupling) is split
+// the same way per evaluation, per (source k-chunk, column tile).
 constexpr int kTcRows = 128;        // rows per m-tile (MMA M)
 constexpr int kTcK = 64;            // FP16 values per k-chunk row (128 bytes)
 constexpr int kTcTileBytes = kTcRows * kTcK * 2;   // one FP16 tile: 16 KB
+// The mixed mode puts the coupling on the tensor cores when the stored coupling values
+// fill at least this fraction of the padded 128 x 64 tiles they occupy.
+constexpr double kTcCouplingFill = 0.25;
 
 struct TcTile {
-  int32_t leaf;  // leaf-local id
-  int32_t mt;    // m-tile of the leaf
+  int32_t node;  // target (leaf-local id for the near field, tree node for the coupling)
+  int32_t mt;    // m-tile of the target
 };
 
-// One (near entry, m-tile, k-chunk) tile pair to pack from the FP64 arena.
+// One (entry, m-tile, k-chunk) tile pair to pack from the FP64 arena.
 struct TcPackJob {
   int64_t dst;        // byte offset of the hi tile (the lo tile follows)
-  int64_t src;        // FP64 arena offset of the block
-  int32_t rows, cols; // block shape n_i x n_j
+  int64_t src;        // FP64 arena offset of the block's (row 0, column 0)
+  int32_t rows, cols; // block shape
   int32_t r0, k0;     // first row / column of the tile inside the block
   int32_t scale_idx;  // index of the m-tile's scale exponent
-  int32_t pad;
+  int32_t ld;         // row stride of the block in the arena
 };
 
-// Device-side description of the mixed near field, passed by value to its kernels.
-struct TcNear {
+// Device-side description of one tensor-core product family, passed by value to its
+// kernels. Targets and sources share one index space ("nodes"): rows of node n are
+// begin[n] .. begin[n] + size[n] - 1 of the output (as a target) and of the
+// right-hand side (as a source).
+struct TcLists {
   const uint8_t* tiles;        // packed hi/lo tiles
-  const int64_t* a_off;        // per near entry: byte offset of its (m-tile 0, chunk 0) pair
-  const int64_t* near_ptr;     // per leaf (leaf-local), CSR
-  const int32_t* near_idx;     // per entry: source leaf (leaf-local)
-  const int32_t* leaf_kc;      // per leaf: k-chunks = ceil(n / 64)
-  const int64_t* leaf_kcum;    // per leaf: k-chunks of the preceding leaves
-  const int64_t* leaf_begin;   // per leaf: first tree-order point
-  const int32_t* leaf_size;    // per leaf: points
-  const int32_t* mt_base;      // per leaf: index of its first m-tile scale
-  const int32_t* scale;        // per m-tile: scale exponent of D
-  const TcTile* work;          // (leaf, m-tile) work items, longest first
-  const int32_t* chunk_leaf;   // per global k-chunk: its leaf
-  const int32_t* chunk_c;      // per global k-chunk: its chunk index within the leaf
+  const int64_t* a_off;        // per entry: byte offset of its (m-tile 0, chunk 0) pair
+  const int64_t* ptr;          // per target: CSR into the entries
+  const int32_t* idx;          // per entry: its source node
+  const int32_t* kc;           // per node: k-chunks = ceil(size / 64)
+  const int64_t* kcum;         // per node: k-chunks of the preceding nodes
+  const int64_t* begin;        // per node: first row
+  const int32_t* size;         // per node: rows
+  const int32_t* mt_base;      // per node: index of its first m-tile scale
+  const int32_t* scale;        // per m-tile: scale exponent of the blocks
+  const TcTile* work;          // (target, m-tile) work items, longest lists first
+  const int32_t* chunk_node;   // per global k-chunk: its node
+  const int32_t* chunk_c;      // per global k-chunk: its chunk index within the node
+};
+
+// Host-side owner of one product family.
+struct TcProduct {
+  TcLists dev{};
+  uint8_t* tiles = nullptr;
+  int64_t tile_bytes = 0;
+  void* meta = nullptr;        // one allocation for the TcLists arrays
+  int64_t n_work = 0;          // (target, m-tile) work items
+  int64_t n_chunks = 0;        // source k-chunks
 };
 
 // The state one evaluation needs besides the read-only HMatrix: the workspaces
@@ -122,6 +141,8 @@ struct EvalContext {
   double* us = nullptr;
   unsigned long long* wmax = nullptr;  // mixed: max |W| (FP64 bits)
   uint8_t* wsplit = nullptr;     // mixed: W as FP16 hi/lo operand tiles
+  unsigned long long* smax = nullptr;  // mixed: max |w| of the skeleton weights (FP64 bits)
+  uint8_t* ssplit = nullptr;     // mixed: skeleton weights as FP16 hi/lo operand tiles
   float* w32 = nullptr;          // mixed: FP32 copy of W in tree order
   float* ws32 = nullptr;         // mixed: FP32 skeleton workspaces
   float* us32 = nullptr;
@@ -156,7 +177,7 @@ struct Handle {
   std::vector<int64_t> begin, size, skel_off, perm_host, near_ptr, far_ptr;
   std::vector<int32_t> rank, near_idx, far_idx;
   std::vector<Phase> phases;      // FP64 mode: one launch per row-tile size of every phase
-  std::vector<Phase> phases32;    // mixed far field (coupling: one split-K launch of 16-row tiles)
+  std::vector<Phase> phases32;    // mixed mode: the upward and downward passes in FP32
 
   // device
   double* arena = nullptr;       // packed FP64 blocks (near, basis, coupling)
@@ -170,13 +191,11 @@ struct Handle {
 
   // mixed precision (HMAT_LOAD_MIXED)
   bool has_mixed = false;
-  uint8_t* tc_tiles = nullptr;   // FP16 hi/lo near tiles
-  int64_t tc_bytes = 0;
-  void* tc_meta = nullptr;       // one allocation for the TcNear arrays
-  TcNear tc{};
-  int64_t n_tc_work = 0;         // (leaf, m-tile) work items
-  int64_t total_kchunks = 0;     // sum over leaves of ceil(n / 64)
-  float* arena32 = nullptr;      // FP32 copy of the bases and coupling blocks
+  TcProduct tc_near;             // near field D_ij on the tensor cores
+  TcProduct tc_far;              // coupling B_ab on the tensor cores (when tc_coupling)
+  bool tc_coupling = false;      // mixed coupling engine: tensor cores, else FP32 CUDA cores
+  float* arena32 = nullptr;      // FP32 copy of the bases (and of the coupling blocks when
+                                 // the coupling runs in FP32)
   int64_t arena32_shift = 0;     // FP64-arena offset of arena32[0]
 
   struct EvalContext* ctx = nullptr;  // the handle's own evaluation state (hmat_eval)
@@ -227,18 +246,27 @@ cudaError_t launch_eval_blocks(const BlockJob* jobs, int64_t n_jobs, const doubl
                                cudaStream_t stream);
 
 // Mixed mode: load-time packing and per-evaluation kernels (hmat_mixed.cu).
-cudaError_t launch_tc_scale(const TcNear& tc, const int64_t* near_off, const double* arena, int64_t n_leaves,
-                            int64_t n_mtiles, const int32_t* mtile_leaf, const int32_t* mtile_mt, int32_t* scale_out,
+cudaError_t launch_tc_scale(const TcLists& tc, const int64_t* blk_off, const int32_t* blk_ld, const double* arena,
+                            int64_t n_mtiles, const int32_t* mtile_node, const int32_t* mtile_mt, int32_t* scale_out,
                             cudaStream_t stream);
 cudaError_t launch_tc_pack(const TcPackJob* jobs, int64_t n_jobs, const double* arena, const int32_t* scale,
                            uint8_t* tiles, cudaStream_t stream);
 cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t stream);
-cudaError_t launch_w_split(const TcNear& tc, int64_t total_kchunks, const double* W, int64_t n_values,
-                           const int64_t* perm, int64_t q, int n_t, int n_ct, unsigned long long* wmax,
-                           uint8_t* wsplit, float* w32, cudaStream_t stream);
-cudaError_t launch_near_tc(const TcNear& tc, int64_t n_work, const uint8_t* wsplit, const unsigned long long* wmax,
+// Right-hand operand split: X (n_values values, row-major with q columns; FP64 rows
+// through perm for the near field, FP32 rows in node order for the coupling) ->
+// hi/lo tiles per (source k-chunk, column tile); x32 (may be null) gets the FP32
+// tree-order copy of an FP64 X.
+cudaError_t launch_split_f64(const TcProduct& p, const double* X, int64_t n_values, const int64_t* perm, int64_t q,
+                             int n_t, int n_ct, unsigned long long* xmax, uint8_t* out, float* x32,
+                             cudaStream_t stream);
+cudaError_t launch_split_f32(const TcProduct& p, const float* X, int64_t n_values, int64_t q, int n_t, int n_ct,
+                             unsigned long long* xmax, uint8_t* out, cudaStream_t stream);
+// Y (FP64, rows through perm) = near field; or U (FP32, node rows) = coupling.
+cudaError_t launch_tc_near(const TcProduct& p, const uint8_t* bsplit, const unsigned long long* bmax,
                            const int64_t* perm, double* Y, int64_t q, int n_t, int n_ct, int* status,
                            cudaStream_t stream);
+cudaError_t launch_tc_far(const TcProduct& p, const uint8_t* bsplit, const unsigned long long* bmax, float* U,
+                          int64_t q, int n_t, int n_ct, int* status, cudaStream_t stream);
 // One bounded wait that nothing completes: sets HMAT_ETIMEOUT in *status after limit_ns.
 cudaError_t launch_wait_selftest(int* status, uint64_t limit_ns, cudaStream_t stream);
 // FP32 grouped GEMM of one far-field phase of the mixed mode (hmat_far32.cu).

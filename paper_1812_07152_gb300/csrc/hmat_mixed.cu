@@ -1,30 +1,30 @@
-// Mixed-precision near field on the tcgen05 tensor cores (HMAT_MODE_MIXED).
+// Mixed-precision products on the tcgen05 tensor cores (HMAT_MODE_MIXED): the
+// near-field reduction Y_i = sum_j D_ij W_j and the far-field coupling reduction
+// u_a = sum_b B_ab w_b (Section 2.1, "Evaluation"). Both are lists of dense
+// contractions per target, so one kernel serves both:
 //
-// The near-field reduction Y_i = sum_j D_ij W_j (Section 2.1, "Evaluation") is a
-// chain of dense contractions, so it runs on the 5th-generation tensor cores:
-//
-//  * D and W are split into two FP16 terms, x ~= hi + lo with hi = fp16(x) and
-//    lo = fp16(x - hi), after a power-of-two scaling that puts the largest |value|
-//    of a D m-tile (128 rows of one target leaf, over its whole near list) and of
-//    W into [2^13, 2^14): 22 significant bits per value, no overflow, no
+//  * A (D or B) and X (W or w) are split into two FP16 terms, x ~= hi + lo with
+//    hi = fp16(x) and lo = fp16(x - hi), after a power-of-two scaling that puts the
+//    largest |value| of an A m-tile (128 rows of one target, over its whole list) and
+//    of X into [2^13, 2^14): 22 significant bits per value, no overflow, no
 //    subnormal lo for values down to 2^-16 of the maximum;
-//  * Y_i = sum_j (Dh Wh + Dh Wl + Dl Wh), the dropped Dl Wl term is 2^-22 relative;
+//  * Y_t = sum_s (Ah Xh + Ah Xl + Al Xh), the dropped Al Xl term is 2^-22 relative;
 //  * the tensor core's FP32 accumulator truncates (rounds toward zero, measured on
-//    this GPU), so the dominant Dh Wh product is accumulated in TMEM for two near
-//    blocks only and then drained by the epilogue warps into a compensated FP32
-//    (hi, lo) pair per output (hi in registers, lo in TMEM columns 384..511); the
-//    two small cross terms (2^-11 of the result) accumulate over the whole near
-//    list in a second TMEM accumulator.
+//    this GPU), so the dominant Ah Xh product is accumulated in TMEM for two blocks
+//    only and then drained by the epilogue warps into a compensated FP32 (hi, lo)
+//    pair per output (hi in registers, lo in TMEM columns 384..511); the two small
+//    cross terms (2^-11 of the result) accumulate over the whole list in a second
+//    TMEM accumulator.
 //
-// Operands are packed once (D at load, W per evaluation) in the canonical K-major
+// Operands are packed once (A at load, X per evaluation) in the canonical K-major
 // 128-byte-swizzled tcgen05 layout, so one cp.async.bulk (TMA) copy per tile lands
-// it in shared memory. Warp roles: warp 0 issues the bulk copies of the D tiles and
-// warp 10 those of the W tiles (bulk copies issued by one thread are processed about
+// it in shared memory. Warp roles: warp 0 issues the bulk copies of the A tiles and
+// warp 10 those of the X tiles (bulk copies issued by one thread are processed about
 // one at a time, ~0.2 us each, so two issuers nearly double the copy rate), warp 1
 // issues the MMAs (one thread) and owns the TMEM allocation, warps 2..9 drain the
-// accumulators and write Y. All waits are bounded; on a timeout the kernel records
-// HMAT_ETIMEOUT in the status word, lets its own copies and MMAs finish, frees its
-// TMEM and returns.
+// accumulators and write the output. All waits are bounded; on a timeout the kernel
+// records HMAT_ETIMEOUT in the status word, lets its own copies and MMAs finish,
+// frees its TMEM and returns.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -196,27 +196,33 @@ __device__ double block_max_d(double v) {
 
 // ------------------------------------------------------------------ load-time packing
 
-// Scale exponent of one m-tile: the largest |D| over the tile's rows of every near block.
-__global__ void __launch_bounds__(256) k_tc_scale(TcNear tc, const int64_t* __restrict__ near_off,
-                                                  const double* __restrict__ arena,
-                                                  const int32_t* __restrict__ mtile_leaf,
+// Scale exponent of one m-tile: the largest |value| over the tile's rows of every
+// block of the target's list.
+__global__ void __launch_bounds__(256) k_tc_scale(TcLists tc, const int64_t* __restrict__ blk_off,
+                                                  const int32_t* __restrict__ blk_ld, const double* __restrict__ arena,
+                                                  const int32_t* __restrict__ mtile_node,
                                                   const int32_t* __restrict__ mtile_mt, int32_t* __restrict__ out) {
   const int t = blockIdx.x;
-  const int leaf = mtile_leaf[t], mt = mtile_mt[t];
-  const int n_i = tc.leaf_size[leaf];
+  const int node = mtile_node[t], mt = mtile_mt[t];
+  const int n_i = tc.size[node];
   const int r0 = mt * kTcRows, r1 = min(n_i, r0 + kTcRows);
   double m = 0.0;
-  for (int64_t e = tc.near_ptr[leaf]; e < tc.near_ptr[leaf + 1]; ++e) {
-    const int n_j = tc.leaf_size[tc.near_idx[e]];
-    const double* D = arena + near_off[e] + (int64_t)r0 * n_j;
+  for (int64_t e = tc.ptr[node]; e < tc.ptr[node + 1]; ++e) {
+    const int n_j = tc.size[tc.idx[e]];
+    if (n_j == 0) continue;
+    const double* B = arena + blk_off[e];
+    const int64_t ld = blk_ld[e];
     const int64_t cnt = (int64_t)(r1 - r0) * n_j;
-    for (int64_t x = threadIdx.x; x < cnt; x += blockDim.x) m = fmax(m, fabs(D[x]));
+    for (int64_t x = threadIdx.x; x < cnt; x += blockDim.x) {
+      const int64_t r = r0 + x / n_j, c = x % n_j;
+      m = fmax(m, fabs(B[r * ld + c]));
+    }
   }
   m = block_max_d(m);
   if (threadIdx.x == 0) out[t] = scale_exponent(m);
 }
 
-// One (near entry, m-tile, k-chunk): scaled FP64 values -> FP16 hi and lo SW128 tiles.
+// One (entry, m-tile, k-chunk): scaled FP64 values -> FP16 hi and lo SW128 tiles.
 __global__ void __launch_bounds__(256) k_tc_pack(const TcPackJob* __restrict__ jobs, const double* __restrict__ arena,
                                                  const int32_t* __restrict__ scale, uint8_t* __restrict__ tiles) {
   const TcPackJob job = jobs[blockIdx.x];
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(256) k_tc_pack(const TcPackJob* __restrict__ j
     for (int t = 0; t < 8; ++t) {
       const int gk = job.k0 + ck * 8 + t;
       double x = 0.0;
-      if (gr < job.rows && gk < job.cols) x = ldexp(arena[job.src + (int64_t)gr * job.cols + gk], k);
+      if (gr < job.rows && gk < job.cols) x = ldexp(arena[job.src + (int64_t)gr * job.ld + gk], k);
       split_fp16(x, hv[t], lv[t]);
     }
     const int off = sw128_chunk(r, ck);
@@ -247,34 +253,39 @@ __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst
 
 // ------------------------------------------------------------------ per-evaluation W split
 
-__global__ void __launch_bounds__(256) k_w_absmax(const double* __restrict__ W, int64_t n,
-                                                  unsigned long long* __restrict__ out) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t n,
+                                                unsigned long long* __restrict__ out) {
   double m = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    m = fmax(m, fabs(W[i]));
+    m = fmax(m, fabs((double)X[i]));
   m = block_max_d(m);
   if (threadIdx.x == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-// One (k-chunk of a source leaf, column tile): 64 rows of W (tree order) x n_t columns
-// -> B-operand tiles: n_t rows (columns of W) x 64 values (rows of W), hi then lo,
-// and the same values unscaled in FP32, tree order (the far field's input).
-// A thread owns one column and 8 consecutive rows: one 16-byte chunk of each tile.
-// FP64 arithmetic is 1/64 rate on this GPU, so the split itself is done in FP32
-// after one scaled FP64 -> FP32 conversion (24 bits kept, 22 needed).
-__global__ void __launch_bounds__(256) k_w_split(TcNear tc, const double* __restrict__ W,
-                                                 const int64_t* __restrict__ perm, int64_t q, int n_t, int n_ct,
-                                                 const unsigned long long* __restrict__ wmax,
-                                                 uint8_t* __restrict__ wsplit, float* __restrict__ w32) {
+// One (source k-chunk, column tile): 64 rows of X x n_t columns -> B-operand tiles:
+// n_t rows (columns of X) x 64 values (rows of X), hi then lo. The near field's X is
+// W (FP64, caller order, rows through perm); there the same values also go unscaled
+// into x32, the FP32 tree-order copy the far field reads. The coupling's X is the
+// FP32 skeleton weights in node order. A thread owns one column and 8 consecutive
+// rows: one 16-byte chunk of each tile. FP64 arithmetic is 1/64 rate on this GPU, so
+// the split itself is done in FP32 after one scaled conversion (24 bits kept, 22
+// needed); the scale is a power of two, so scaling an FP32 value is exact.
+template <typename T>
+__global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__ X, const int64_t* __restrict__ perm,
+                                               int64_t q, int n_t, int n_ct,
+                                               const unsigned long long* __restrict__ xmax,
+                                               uint8_t* __restrict__ out, float* __restrict__ x32) {
   const int64_t g = blockIdx.x / n_ct;
   const int ct = blockIdx.x % n_ct;
-  const int leaf = tc.chunk_leaf[g], c = tc.chunk_c[g];
-  const int n_j = tc.leaf_size[leaf];
-  const int64_t row0 = tc.leaf_begin[leaf] + (int64_t)c * kTcK;
-  const int k_w = scale_exponent(__longlong_as_double((long long)*wmax));
-  const double sd = ldexp(1.0, k_w);
+  const int node = tc.chunk_node[g], c = tc.chunk_c[g];
+  const int n_j = tc.size[node];
+  const int64_t row0 = tc.begin[node] + (int64_t)c * kTcK;
+  const int k_x = scale_exponent(__longlong_as_double((long long)*xmax));
+  const double sd = ldexp(1.0, k_x);
+  const float sf = (float)sd;
   const int64_t q0 = (int64_t)ct * n_t;
-  uint8_t* hi_t = wsplit + (g * n_ct + ct) * (int64_t)(2 * n_t * 128);
+  uint8_t* hi_t = out + (g * n_ct + ct) * (int64_t)(2 * n_t * 128);
   uint8_t* lo_t = hi_t + n_t * 128;
   for (int x = threadIdx.x; x < n_t * 8; x += blockDim.x) {
     const int kc = x / n_t, n = x % n_t;
@@ -285,9 +296,14 @@ __global__ void __launch_bounds__(256) k_w_split(TcNear tc, const double* __rest
       const int k = kc * 8 + t;
       float xs = 0.0f;
       if (c * kTcK + k < n_j && gq < q) {
-        const double v = W[perm[row0 + k] * q + gq];
-        xs = __double2float_rn(v * sd);
-        w32[(row0 + k) * q + gq] = __double2float_rn(v);
+        const int64_t src = perm ? perm[row0 + k] : row0 + k;
+        const T v = X[src * q + gq];
+        if constexpr (sizeof(T) == 8) {
+          xs = __double2float_rn((double)v * sd);
+          if (x32) x32[(row0 + k) * q + gq] = __double2float_rn((double)v);
+        } else {
+          xs = (float)v * sf;
+        }
       }
       hv[t] = __float2half_rn(xs);
       lv[t] = __float2half_rn(xs - __half2float(hv[t]));
@@ -298,21 +314,26 @@ __global__ void __launch_bounds__(256) k_w_split(TcNear tc, const double* __rest
   }
 }
 
-// ------------------------------------------------------------------ the near-field kernel
+// ------------------------------------------------------------------ the tensor-core product kernel
 
-struct NearTcArgs {
-  TcNear tc;
-  const uint8_t* wsplit;
-  const unsigned long long* wmax;
-  const int64_t* perm;
-  double* Y;
+struct TcArgs {
+  TcLists tc;
+  const uint8_t* bsplit;            // right-hand operand tiles (k_split)
+  const unsigned long long* bmax;   // max |X| of the right-hand side (FP64 bits)
+  const int64_t* perm;              // near field: tree order -> caller order of Y's rows
+  void* Y;                          // near field: double (caller order); coupling: float (node rows)
   int64_t q;
   int n_t;
   int n_ct;
   int* status;
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
+// Y_t = sum over the list of target t of A_ts X_s, for one (target, m-tile, column
+// tile). kFar = false: the near field (A = D, X = W, Y FP64 in caller order);
+// kFar = true: the coupling reduction (A = B, X = skeleton weights w, Y = the FP32
+// skeleton potentials u, written in node order).
+template <bool kFar>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], mfull_bar[2], mempty_bar[2], cfull_bar,
@@ -324,8 +345,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TcTile work = a.tc.work[blockIdx.x / a.n_ct];
   const int ct = blockIdx.x % a.n_ct;
-  const int leaf = work.leaf, mt = work.mt;
-  const int64_t e0 = a.tc.near_ptr[leaf], e1 = a.tc.near_ptr[leaf + 1];
+  const int tgt = work.node, mt = work.mt;
+  const int64_t e0 = a.tc.ptr[tgt], e1 = a.tc.ptr[tgt + 1];
   const uint32_t b_bytes = 2u * (uint32_t)a.n_t * 128u;
   const uint32_t a_bytes = 2u * kTcTileBytes;
 
@@ -361,17 +382,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
   };
 
   if (warp == 0 || warp == 10) {
-    // ---- producers: warp 0 copies the D tile pair, warp 10 the W tile pair of every k-chunk
+    // ---- producers: warp 0 copies the A tile pair, warp 10 the X tile pair of every k-chunk
     if (lane == 0) {
       const bool is_d = warp == 0;
       int it = 0;
       bool ok = true;
       for (int64_t e = e0; e < e1 && ok; ++e) {
-        const int j = a.tc.near_idx[e];
-        const int kc = a.tc.leaf_kc[j];
+        const int j = a.tc.idx[e];
+        const int kc = a.tc.kc[j];
         if (kc == 0) continue;
         const uint8_t* abase = a.tc.tiles + a.tc.a_off[e] + (int64_t)mt * kc * a_bytes;
-        const int64_t g0 = a.tc.leaf_kcum[j];
+        const int64_t g0 = a.tc.kcum[j];
         for (int c = 0; c < kc; ++c, ++it) {
           const int s = it % kStages, r = it / kStages;
           if (r > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (r - 1) & 1, &abort_flag)) {
@@ -386,7 +407,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
             issued_a = it + 1;
           } else {
             mbar_expect_tx(smem_u32(&full_bar[s]), b_bytes);
-            bulk_g2s(st + a_bytes, a.wsplit + ((g0 + c) * a.n_ct + ct) * (int64_t)b_bytes, b_bytes,
+            bulk_g2s(st + a_bytes, a.bsplit + ((g0 + c) * a.n_ct + ct) * (int64_t)b_bytes, b_bytes,
                      smem_u32(&full_bar[s]));
             issued_b = it + 1;
           }
@@ -394,16 +415,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
       }
     }
   } else if (warp == 1) {
-    // ---- MMA issuer: main[b] = Dh*Wh for one near block, cross += Dh*Wl + Dl*Wh
+    // ---- MMA issuer: main[b] = Ah*Xh over kDrainBlocks blocks, cross += Ah*Xl + Al*Xh
     if (lane == 0) {
       const uint32_t idesc = idesc_f16(kTcRows, a.n_t);
       const uint32_t cross = tmem + 256;
-      int nb = 0;  // near blocks with data
-      for (int64_t e = e0; e < e1; ++e) nb += a.tc.leaf_kc[a.tc.near_idx[e]] > 0;
+      int nb = 0;  // blocks with data
+      for (int64_t e = e0; e < e1; ++e) nb += a.tc.kc[a.tc.idx[e]] > 0;
       int it = 0, blk = 0;
       bool ok = true;
       for (int64_t e = e0; e < e1 && ok; ++e) {
-        const int kc = a.tc.leaf_kc[a.tc.near_idx[e]];
+        const int kc = a.tc.kc[a.tc.idx[e]];
         if (kc == 0) continue;
         const int grp = blk / kDrainBlocks, b = grp & 1, rb = grp >> 1;
         const bool first_of_group = blk % kDrainBlocks == 0;
@@ -461,8 +482,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) tmem_st16(comp + cc * 16, z);
     }
-    int nb = 0;  // near blocks with data, drained kDrainBlocks at a time
-    for (int64_t e = e0; e < e1; ++e) nb += a.tc.leaf_kc[a.tc.near_idx[e]] > 0;
+    int nb = 0;  // blocks with data, drained kDrainBlocks at a time
+    for (int64_t e = e0; e < e1; ++e) nb += a.tc.kc[a.tc.idx[e]] > 0;
     const int n_groups = (nb + kDrainBlocks - 1) / kDrainBlocks;
     int blk = 0;
     bool ok = true;
@@ -499,11 +520,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
       }
     }
     const int row = mt * kTcRows + eq * 32 + lane;
-    const bool write = ok && row < a.tc.leaf_size[leaf];
-    const int k_d = a.tc.scale[a.tc.mt_base[leaf] + mt];
-    const int k_w = scale_exponent(__longlong_as_double((long long)*a.wmax));
-    const double sc = ldexp(1.0, -(k_d + k_w));
-    double* dst = a.Y + (write ? a.perm[a.tc.leaf_begin[leaf] + row] * a.q : 0);
+    const bool write = ok && row < a.tc.size[tgt];
+    const int k_a = a.tc.scale[a.tc.mt_base[tgt] + mt];
+    const int k_x = scale_exponent(__longlong_as_double((long long)*a.bmax));
+    const double sc = ldexp(1.0, -(k_a + k_x));
+    const int64_t out_row = write ? (kFar ? a.tc.begin[tgt] + row : a.perm[a.tc.begin[tgt] + row]) : 0;
     const int64_t c0 = (int64_t)ct * a.n_t + half * 64;
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
@@ -519,8 +540,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_near_tc(const NearTcArgs a) {
       for (int j = 0; j < 16; ++j) {
         const int col = cc * 16 + j;
         const int64_t gc = c0 + col;
-        if (write && half * 64 + col < a.n_t && gc < a.q)
-          dst[gc] = ((double)hi[col] + (double)l[j] + (double)v[j]) * sc;
+        if (write && half * 64 + col < a.n_t && gc < a.q) {
+          const double y = ((double)hi[col] + (double)l[j] + (double)v[j]) * sc;
+          if constexpr (kFar)
+            static_cast<float*>(a.Y)[out_row * a.q + gc] = (float)y;
+          else
+            static_cast<double*>(a.Y)[out_row * a.q + gc] = y;
+        }
       }
     }
   }
@@ -562,13 +588,12 @@ __global__ void k_wait_selftest(int* status, uint64_t limit_ns) {
 
 // ------------------------------------------------------------------ launchers
 
-cudaError_t launch_tc_scale(const TcNear& tc, const int64_t* near_off, const double* arena, int64_t n_leaves,
-                            int64_t n_mtiles, const int32_t* mtile_leaf, const int32_t* mtile_mt, int32_t* scale_out,
+cudaError_t launch_tc_scale(const TcLists& tc, const int64_t* blk_off, const int32_t* blk_ld, const double* arena,
+                            int64_t n_mtiles, const int32_t* mtile_node, const int32_t* mtile_mt, int32_t* scale_out,
                             cudaStream_t stream) {
-  (void)n_leaves;
   if (n_mtiles == 0) return cudaSuccess;
   if (n_mtiles > 2147483647LL) return cudaErrorInvalidValue;
-  k_tc_scale<<<(unsigned)n_mtiles, 256, 0, stream>>>(tc, near_off, arena, mtile_leaf, mtile_mt, scale_out);
+  k_tc_scale<<<(unsigned)n_mtiles, 256, 0, stream>>>(tc, blk_off, blk_ld, arena, mtile_node, mtile_mt, scale_out);
   return cudaGetLastError();
 }
 
@@ -587,39 +612,65 @@ cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_w_split(const TcNear& tc, int64_t total_kchunks, const double* W, int64_t n_values,
-                           const int64_t* perm, int64_t q, int n_t, int n_ct, unsigned long long* wmax,
-                           uint8_t* wsplit, float* w32, cudaStream_t stream) {
+namespace {
+
+template <typename T>
+cudaError_t launch_split(const TcProduct& p, const T* X, int64_t n_values, const int64_t* perm, int64_t q, int n_t,
+                         int n_ct, unsigned long long* xmax, uint8_t* out, float* x32, cudaStream_t stream) {
   if (n_t <= 0 || n_t > kMaxNt || n_t % 16 != 0) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(wmax, 0, sizeof(unsigned long long), stream);
+  cudaError_t e = cudaMemsetAsync(xmax, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   const int64_t blocks = std::min<int64_t>((n_values + 255) / 256, 152 * 8);
-  k_w_absmax<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, stream>>>(W, n_values, wmax);
+  k_absmax<T><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, stream>>>(X, n_values, xmax);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int64_t grid = total_kchunks * n_ct;
+  const int64_t grid = p.n_chunks * n_ct;
   if (grid == 0) return cudaSuccess;
   if (grid > 2147483647LL) return cudaErrorInvalidValue;
-  k_w_split<<<(unsigned)grid, 256, 0, stream>>>(tc, W, perm, q, n_t, n_ct, wmax, wsplit, w32);
+  k_split<T><<<(unsigned)grid, 256, 0, stream>>>(p.dev, X, perm, q, n_t, n_ct, xmax, out, x32);
   return cudaGetLastError();
+}
+
+template <bool kFar>
+cudaError_t launch_tc(const TcProduct& p, const uint8_t* bsplit, const unsigned long long* bmax, const int64_t* perm,
+                      void* Y, int64_t q, int n_t, int n_ct, int* status, cudaStream_t stream) {
+  if (p.n_work == 0) return cudaSuccess;
+  if (n_t <= 0 || n_t > kMaxNt || n_t % 16 != 0) return cudaErrorInvalidValue;
+  const int64_t grid = p.n_work * n_ct;
+  if (grid > 2147483647LL) return cudaErrorInvalidValue;
+  const int smem = kStages * kStageBytes + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_tc<kFar>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  TcArgs args{p.dev, bsplit, bmax, perm, Y, q, n_t, n_ct, status};
+  k_tc<kFar><<<(unsigned)grid, kTcThreads, smem, stream>>>(args);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_split_f64(const TcProduct& p, const double* X, int64_t n_values, const int64_t* perm, int64_t q,
+                             int n_t, int n_ct, unsigned long long* xmax, uint8_t* out, float* x32,
+                             cudaStream_t stream) {
+  return launch_split<double>(p, X, n_values, perm, q, n_t, n_ct, xmax, out, x32, stream);
+}
+
+cudaError_t launch_split_f32(const TcProduct& p, const float* X, int64_t n_values, int64_t q, int n_t, int n_ct,
+                             unsigned long long* xmax, uint8_t* out, cudaStream_t stream) {
+  return launch_split<float>(p, X, n_values, nullptr, q, n_t, n_ct, xmax, out, nullptr, stream);
+}
+
+cudaError_t launch_tc_near(const TcProduct& p, const uint8_t* bsplit, const unsigned long long* bmax,
+                           const int64_t* perm, double* Y, int64_t q, int n_t, int n_ct, int* status,
+                           cudaStream_t stream) {
+  return launch_tc<false>(p, bsplit, bmax, perm, Y, q, n_t, n_ct, status, stream);
+}
+
+cudaError_t launch_tc_far(const TcProduct& p, const uint8_t* bsplit, const unsigned long long* bmax, float* U,
+                          int64_t q, int n_t, int n_ct, int* status, cudaStream_t stream) {
+  return launch_tc<true>(p, bsplit, bmax, nullptr, U, q, n_t, n_ct, status, stream);
 }
 
 cudaError_t launch_wait_selftest(int* status, uint64_t limit_ns, cudaStream_t stream) {
   k_wait_selftest<<<1, 32, 0, stream>>>(status, limit_ns);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_near_tc(const TcNear& tc, int64_t n_work, const uint8_t* wsplit, const unsigned long long* wmax,
-                           const int64_t* perm, double* Y, int64_t q, int n_t, int n_ct, int* status,
-                           cudaStream_t stream) {
-  if (n_work == 0) return cudaSuccess;
-  if (n_t <= 0 || n_t > kMaxNt || n_t % 16 != 0) return cudaErrorInvalidValue;
-  const int64_t grid = n_work * n_ct;
-  if (grid > 2147483647LL) return cudaErrorInvalidValue;
-  const int smem = kStages * kStageBytes + 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  NearTcArgs args{tc, wsplit, wmax, perm, Y, q, n_t, n_ct, status};
-  k_near_tc<<<(unsigned)grid, kTcThreads, smem, stream>>>(args);
   return cudaGetLastError();
 }
 

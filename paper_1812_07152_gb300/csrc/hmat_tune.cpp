@@ -180,14 +180,13 @@ extern "C" hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream
     int best = cand[0];
     for (int n_t : cand) {
       const int n_ct = (int)((q + n_t - 1) / n_t);
-      e = launch_w_split(h->tc, h->total_kchunks, W, h->n_points * q, h->perm, q, n_t, n_ct, c->wmax, c->wsplit,
-                         c->w32, s);
+      e = launch_split_f64(h->tc_near, W, h->n_points * q, h->perm, q, n_t, n_ct, c->wmax, c->wsplit, c->w32, s);
       if (e != cudaSuccess) {
         cleanup();
         return cuda_status(e);
       }
       const double t = timer.best([&] {
-        return launch_near_tc(h->tc, h->n_tc_work, c->wsplit, c->wmax, h->perm, Y, q, n_t, n_ct, h->status, s);
+        return launch_tc_near(h->tc_near, c->wsplit, c->wmax, h->perm, Y, q, n_t, n_ct, h->status, s);
       });
       if (t < 0) {
         cleanup();

@@ -306,10 +306,10 @@ def hmat_selftest_timeout(handle: int, limit_ns: int, stream=None) -> None:
 
 
 def hmat_info(handle: int) -> dict:
-    out = (ctypes.c_int64 * 9)()
-    _check(library().hmat_info(handle, out, 9), "hmat_info")
+    out = (ctypes.c_int64 * 10)()
+    _check(library().hmat_info(handle, out, 10), "hmat_info")
     keys = ("n_points", "levels", "near_entries", "far_entries", "near_values", "basis_values",
-            "coupling_values", "sum_rank", "device_bytes")
+            "coupling_values", "sum_rank", "device_bytes", "coupling_engine")
     return dict(zip(keys, [int(v) for v in out]))
 
 

@@ -49,6 +49,7 @@ CASES = [
     ("h2_imq3d_n262144", 5000, 3, (("leaf_size", 40),)),         # leaves of 39/40 points, q = 3
     ("hss_uniform3d_n2048", 1000, 1, ()),                        # q = 1
     ("h2_imq3d_n262144", 2500, 17, (("admissibility", "none"),)),  # all near
+    ("hss_uniform3d_n2048", 1500, 24, (("tol", 0.0), ("max_rank", 10 ** 6))),  # full rank: up to 6 m-tiles per node
     ("hss_uniform3d_n2048", 1200, 9, (("tol", 1.0),)),           # every rank 0
     ("h2_gmm8d_n65536", 60, 5, ()),                              # a single leaf
 ]
@@ -111,5 +112,24 @@ def test_built_handle_mixed_mode():
         Y64 = _eval(h, W, hp.HMAT_MODE_FP64)
         Ymx = _eval(h, W, hp.HMAT_MODE_MIXED)
         assert np.linalg.norm(Ymx - Y64) <= REL_TOL * np.linalg.norm(Y64)
+    finally:
+        hp.hmat_free(h)
+
+
+@pytest.mark.parametrize("base,n,engine", [("h2_gmm8d_n65536", 4096, 1), ("h2_imq3d_n262144", 3000, 2)])
+def test_mixed_coupling_engine_choice(base, n, engine):
+    """Small ranks (d = 8 mixture, ranks <= 31) keep the coupling on the FP32 CUDA cores; ranks near
+    100 fill the 128 x 64 tensor-core tiles and move it there. Both match the oracle."""
+    w, H, _ = oracle_case(base, n, 64)
+    h = hp.hmat_load(**desc_from_oracle(H), flags=hp.HMAT_LOAD_MIXED)
+    try:
+        assert hp.hmat_info(h)["coupling_engine"] == engine
+        W = rhs(w.n, 40, 77)
+        _check(_eval(h, W, hp.HMAT_MODE_MIXED), hm.evaluate(H, W), f"{base} n={n} engine={engine}")
+    finally:
+        hp.hmat_free(h)
+    h = hp.hmat_load(**desc_from_oracle(H))
+    try:
+        assert hp.hmat_info(h)["coupling_engine"] == 0
     finally:
         hp.hmat_free(h)
