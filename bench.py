@@ -51,6 +51,8 @@ def parse_args():
                          "(short: 4 matrices N = 16K..128K, 6 s; full: 8 matrices N = 16K..1M, 2000 req/s, 60 s)")
     ap.add_argument("--precision", choices=["on", "off"], default="on",
                     help="time the precision-mode recipe (N=262144 inverse multiquadric, q=512), FP64 vs mixed")
+    ap.add_argument("--matvec", choices=["on", "off"], default="on",
+                    help="time the matrix-vector recipe (N=262144, kernel 1/r, q=1), FP64 vs mixed")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
     return ap.parse_args()
 
@@ -297,6 +299,8 @@ def run_gpu(args, dist: Dist) -> None:
 
     if args.precision == "on":
         line["precision"] = run_precision(args, dist)
+    if args.matvec == "on":
+        line["matvec"] = run_matvec(args, dist, peak_gflops)
 
     if args.batch == "on":
         line["batch"] = run_batch(args, dist)
@@ -402,6 +406,68 @@ def run_precision(args, dist) -> dict:
     out["mixed"]["error_vs_fp64"] = float(torch.linalg.norm(Ym - Y64) / torch.linalg.norm(Y64))
     out["mixed_over_fp64"] = round(out["mixed"]["value"] / out["fp64"]["value"], 2)
     out["autotune"] = tunes
+    dev.close()
+    return out
+
+
+def run_matvec(args, dist, peak_gflops: float) -> dict:
+    """Matrix-vector form of the comparison with SMASH (Section 4.1): N = 262144 uniform points in [0,1]^3,
+    kernel 1/r (0 for coincident points), geometric admissibility, leaf 256, ID tol 1e-6, q = 1. The FP64 near
+    field is bound by the FP64 pipe even at q = 1 (q/4 flop per stored byte against a ridge of 0.18); the mixed
+    near field reads 4 B per stored value and is bound by HBM."""
+    import torch
+    import paper_1812_07152_gb300 as hp
+    from workloads import WORKLOADS, make_points, normal_rhs
+    w = WORKLOADS["h2_invdist3d_n262144"]
+    t0 = time.perf_counter()
+    dev = hp.DeviceHMatrix.build(make_points(w), flags=hp.HMAT_LOAD_MIXED, **build_params(w))
+    t_build = time.perf_counter() - t0
+    info = dev.info
+    q = w.q
+    W = torch.from_numpy(normal_rhs(w.n, q, w.rhs_seed)).cuda()
+    Ys = {"fp64": torch.empty_like(W), "mixed": torch.empty_like(W)}
+    stream = torch.cuda.current_stream()
+    dev.reserve(q)
+    nv = info["near_values"]
+    peaks = measured_peaks()
+    out = {"workload": w.name, "n": w.n, "q": q, "kernel": "1/r", "leaf_size": w.leaf_size, "tol": w.tol,
+           "near_values": nv, "coupling_values": info["coupling_values"], "sum_rank": info["sum_rank"],
+           "coupling_engine": info["coupling_engine"], "inspector_s": round(t_build, 2), "unit": "cols/s"}
+    steps = max(args.steps, 20)
+    for name, mode in (("fp64", hp.HMAT_MODE_FP64), ("mixed", hp.HMAT_MODE_MIXED)):
+        hp.hmat_autotune(dev.handle, q, mode, stream)
+        for _ in range(args.warmup):
+            hp.hmat_eval(dev.handle, W, Ys[name], q, mode, stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        hp.hmat_profile(dev.handle, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            hp.hmat_eval(dev.handle, W, Ys[name], q, mode, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = dist.max(e0.elapsed_time(e1) / steps)
+        phases = hp.hmat_phase_times(dev.handle)
+        hp.hmat_profile(dev.handle, False)
+        if dev.poll() != hp.HMAT_OK:
+            raise RuntimeError(f"device status error in the matrix-vector {name} steps")
+        near_ms = phases["near"][0] / steps
+        if mode == hp.HMAT_MODE_FP64:
+            achieved = 2.0 * q * nv / (near_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_gflops / 1e3, 4),
+                    "unit": "TFLOP/s", "frac": round(achieved / (peak_gflops / 1e3), 4),
+                    "kernel": "k_grouped_gemm<double> 1-column tiles (near field)"}
+        else:
+            alg = 4.0 * nv + 8.0 * w.n * q * 2
+            achieved = alg / (near_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": round(achieved / peaks["hbm_gbs"], 4), "algorithmic_bytes": alg,
+                    "kernel": "k_tc (tcgen05 near field, 16-column tile)", "peak_source": peaks["source"]}
+        out[name] = {"value": round(dist.world * q / (ms / 1e3), 1), "ms_per_step": round(ms, 4), "steps": steps,
+                     "phases_ms_per_step": {k: round(v[0] / steps, 4) for k, v in phases.items()}, "roofline": roof}
+    out["mixed"]["error_vs_fp64"] = float(torch.linalg.norm(Ys["mixed"] - Ys["fp64"]) / torch.linalg.norm(Ys["fp64"]))
     dev.close()
     return out
 

@@ -88,7 +88,10 @@ typedef struct {
  * interaction computation and low-rank approximation in one native call.
  *
  * Kernel functions (Section 1): HMAT_KERNEL_GAUSSIAN exp(-r^2 / (2 h^2)) with
- * kernel_param = h; HMAT_KERNEL_IMQ 1 / sqrt(r^2 + c^2) with kernel_param = c.
+ * kernel_param = h > 0; HMAT_KERNEL_IMQ 1 / sqrt(r^2 + c^2) with kernel_param =
+ * c > 0; HMAT_KERNEL_INVDIST 1 / r (the kernel of the comparison with SMASH,
+ * Section 4.1), 0 for coincident points including the diagonal (the paper leaves
+ * k(x, x) undefined), kernel_param ignored.
  *
  * Admissibility (Section 2.1, "Compression"; Section 4.1 for HSS):
  * HMAT_ADM_HSS - every pair of distinct siblings is far (weak admissibility);
@@ -99,6 +102,7 @@ typedef struct {
  */
 #define HMAT_KERNEL_GAUSSIAN 0
 #define HMAT_KERNEL_IMQ 1
+#define HMAT_KERNEL_INVDIST 2
 #define HMAT_ADM_HSS 0
 #define HMAT_ADM_GEOMETRIC 1
 #define HMAT_ADM_NONE 2

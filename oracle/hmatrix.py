@@ -8,7 +8,7 @@ generator package ``workloads``, which holds none of the method's arithmetic.
 
 What it builds and computes, with the passage each part follows:
 
-* kernel matrix K(i, j) = k(x_i, x_j)                       (Section 1)
+* kernel matrix K(i, j) = k(x_i, x_j)                       (Section 1; 1/r: Section 4.1)
 * cluster tree by recursive kd median splits                (Section 3.1, "Tree construction")
 * near / far interactions from an admissibility condition   (Section 2.1, "Compression"; Section 4.1 for HSS)
 * nested interpolative decomposition of the far field       (Section 2.1 footnote; Section 3.1, "Low-rank approximation")
@@ -34,7 +34,8 @@ builder only through the fixture itself, never through shared code):
   is approximated (exact when N <= 4096, else a seeded uniform sample of
   min(|C|, max(4 * max_rank, 512)) of them);
 * U = V = P (K is symmetric); a node has a basis iff it or an ancestor has a
-  far interaction; the root never has one.
+  far interaction; the root never has one;
+* the singular kernel 1/r is 0 for coincident points (its diagonal included).
 """
 from __future__ import annotations
 
@@ -64,6 +65,13 @@ def kernel_matrix(kind: str, param: float, X: np.ndarray, Y: np.ndarray) -> np.n
         return np.exp(-r2 / (2.0 * param * param))
     if kind == "imq":
         return 1.0 / np.sqrt(r2 + param * param)
+    if kind == "invdist":
+        # 1 / ||x - y||, the kernel of the comparison with SMASH (Section 4.1); the paper
+        # does not define k(x, x): coincident points interact with 0
+        out = np.zeros_like(r2)
+        nz = r2 > 0.0
+        out[nz] = 1.0 / np.sqrt(r2[nz])
+        return out
     raise ValueError(f"unknown kernel {kind!r}")
 
 

@@ -1,7 +1,7 @@
 // Device evaluation of dense kernel blocks K(I, J) straight into the packed arena:
 // the near blocks D_ij = K(I_i, I_j) and the coupling blocks B_ab = K(S_a, S_b)
 // of the inspector's compression (Section 3.1). One CTA per block, coalesced
-// row-major writes; the kernel functions are those of Section 1.
+// row-major writes; the kernel functions are those of Section 1 (1/r: Section 4.1).
 #include <cuda_runtime.h>
 
 #include "hmat_internal.h"
@@ -30,7 +30,14 @@ k_eval_blocks(const BlockJob* __restrict__ jobs, const double* __restrict__ pts,
       const double diff = x[k] - y[k];
       r2 = __dadd_rn(r2, __dmul_rn(diff, diff));
     }
-    out[r * job.ld + c] = kernel == HMAT_KERNEL_GAUSSIAN ? exp(-r2 / two_h2) : 1.0 / sqrt(r2 + c2);
+    double k;
+    if (kernel == HMAT_KERNEL_GAUSSIAN)
+      k = exp(-r2 / two_h2);
+    else if (kernel == HMAT_KERNEL_IMQ)
+      k = 1.0 / sqrt(r2 + c2);
+    else
+      k = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;  // 1/r, 0 for coincident points
+    out[r * job.ld + c] = k;
   }
 }
 

@@ -32,7 +32,9 @@ double kernel_value(int kernel, double param, const double* x, const double* y, 
     const double diff = x[k] - y[k];
     r2 += diff * diff;
   }
-  return kernel == HMAT_KERNEL_GAUSSIAN ? std::exp(-r2 / (2.0 * param * param)) : 1.0 / std::sqrt(r2 + param * param);
+  if (kernel == HMAT_KERNEL_GAUSSIAN) return std::exp(-r2 / (2.0 * param * param));
+  if (kernel == HMAT_KERNEL_IMQ) return 1.0 / std::sqrt(r2 + param * param);
+  return r2 > 0.0 ? 1.0 / std::sqrt(r2) : 0.0;  // 1/r, 0 for coincident points
 }
 
 template <class F>
@@ -271,8 +273,9 @@ extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t*
   *out = nullptr;
   if (flags & ~HMAT_LOAD_MIXED) return HMAT_EUNSUPPORTED;
   if (!p || p->n_points < 1 || p->dim < 1 || p->dim > 64 || !p->points || p->leaf_size < 2 || p->max_rank < 1 ||
-      !(p->tol >= 0.0) || !(p->kernel_param > 0.0) ||
-      (p->kernel != HMAT_KERNEL_GAUSSIAN && p->kernel != HMAT_KERNEL_IMQ) ||
+      !(p->tol >= 0.0) ||
+      (p->kernel != HMAT_KERNEL_GAUSSIAN && p->kernel != HMAT_KERNEL_IMQ && p->kernel != HMAT_KERNEL_INVDIST) ||
+      (p->kernel != HMAT_KERNEL_INVDIST && !(p->kernel_param > 0.0)) ||
       (p->admissibility != HMAT_ADM_HSS && p->admissibility != HMAT_ADM_GEOMETRIC &&
        p->admissibility != HMAT_ADM_NONE) ||
       (p->admissibility == HMAT_ADM_GEOMETRIC && !(p->eta > 0.0)))

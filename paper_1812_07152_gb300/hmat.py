@@ -58,11 +58,12 @@ class HmatDesc(ctypes.Structure):
 
 HMAT_KERNEL_GAUSSIAN = 0
 HMAT_KERNEL_IMQ = 1
+HMAT_KERNEL_INVDIST = 2
 HMAT_ADM_HSS = 0
 HMAT_ADM_GEOMETRIC = 1
 HMAT_ADM_NONE = 2
 
-_KERNELS = {"gaussian": HMAT_KERNEL_GAUSSIAN, "imq": HMAT_KERNEL_IMQ}
+_KERNELS = {"gaussian": HMAT_KERNEL_GAUSSIAN, "imq": HMAT_KERNEL_IMQ, "invdist": HMAT_KERNEL_INVDIST}
 _ADMISSIBILITY = {"hss": HMAT_ADM_HSS, "geometric": HMAT_ADM_GEOMETRIC, "none": HMAT_ADM_NONE}
 
 

@@ -39,6 +39,7 @@ def _eval(h, W):
     ("h2_imq3d_n262144", 3000, ()),
     ("h2_gmm8d_n65536", 4096, ()),
     ("h2_imq3d_n262144", 4000, (("leaf_size", 40),)),
+    ("h2_invdist3d_n262144", 3000, ()),
 ])
 def test_structure_identical_and_accuracy_comparable(base, n, ov):
     w, H, X = oracle_case(base, n, 8, **dict(ov))
@@ -61,7 +62,8 @@ def test_structure_identical_and_accuracy_comparable(base, n, ov):
         hp.hmat_free(h)
 
 
-@pytest.mark.parametrize("base,n", [("hss_uniform3d_n2048", 2048), ("h2_imq3d_n262144", 4096)])
+@pytest.mark.parametrize("base,n", [("hss_uniform3d_n2048", 2048), ("h2_imq3d_n262144", 4096),
+                                    ("h2_invdist3d_n262144", 4096)])
 def test_error_order_tol_uncapped(base, n):
     w, _, X = oracle_case(base, n, 8)
     W = rhs(w.n, 8, 22)
@@ -96,3 +98,20 @@ def test_build_rejects_bad_parameters():
     Xn[3, 1] = np.nan
     with pytest.raises(hp.HmatError):
         hp.hmat_build(Xn, **base)
+
+
+def test_invdist_blocks_zero_for_coincident_points():
+    """The 1/r kernel's diagonal convention on the device: duplicated points interact with 0,
+    so with nothing far the library reproduces the oracle's dense product exactly."""
+    rng = np.random.default_rng(31)
+    X = rng.random((700, 3))
+    X[350:360] = X[10:20]                                   # ten duplicated points
+    W = rhs(700, 3, 32)
+    h = hp.hmat_build(X, kernel="invdist", kernel_param=0.0, admissibility="none", leaf_size=64, tol=1e-6,
+                      max_rank=64, eta=2.0)
+    try:
+        KW = hm.dense_product(X, "invdist", 0.0, W)
+        assert np.isfinite(KW).all()
+        assert hm.overall_error(_eval(h, W), KW) <= 1e-13
+    finally:
+        hp.hmat_free(h)

@@ -11,6 +11,8 @@ symmetry check fail.
 import json
 import os
 
+import math
+
 import numpy as np
 import pytest
 
@@ -36,6 +38,20 @@ def test_kernel_closed_forms():
     # inverse multiquadric 1/sqrt(r^2 + c^2): at r = 0 -> 1/c; at r = 0.5, c = 0.1 -> 1/sqrt(0.26)
     assert hm.kernel_matrix("imq", 0.1, x, x)[0, 0] == pytest.approx(10.0, rel=1e-15)
     assert hm.kernel_matrix("imq", 0.1, x, y)[0, 0] == pytest.approx(1 / np.sqrt(0.26), rel=1e-15)
+    # 1/r (Section 4.1): 2 at r = 0.5, 0 for coincident points (the paper leaves k(x, x) open)
+    assert hm.kernel_matrix("invdist", 0.0, x, y)[0, 0] == 2.0
+    assert hm.kernel_matrix("invdist", 0.0, x, x)[0, 0] == 0.0
+
+
+def test_invdist_block_matches_pairwise_loop():
+    rng = np.random.default_rng(12)
+    X = rng.random((7, 3))
+    X[4] = X[1]                                              # a duplicated point: its pair is 0 too
+    K = hm.kernel_matrix("invdist", 0.0, X, X)
+    for i in range(7):
+        for j in range(7):
+            r = math.sqrt(sum((X[i, k] - X[j, k]) ** 2 for k in range(3)))
+            assert K[i, j] == (0.0 if r == 0.0 else pytest.approx(1.0 / r, rel=1e-15))
 
 
 # ---------------------------------------------------------------- cluster tree (Section 3.1)
@@ -166,8 +182,9 @@ def _small(w, **kw):
     return H, X
 
 
-def test_all_near_equals_dense_product():
-    w = reduced(WORKLOADS["h2_gmm8d_n65536"], 1200, q=5)
+@pytest.mark.parametrize("base", ["h2_gmm8d_n65536", "h2_invdist3d_n262144"])
+def test_all_near_equals_dense_product(base):
+    w = reduced(WORKLOADS[base], 1200, q=5)
     H, X = _small(w, admissibility="none")
     assert len(H.inter.far) == 0
     W = normal_rhs(w.n, w.q, 3)
@@ -184,7 +201,7 @@ def test_hss_full_rank_reproduces_K():
 
 
 @pytest.mark.parametrize("base,n", [("hss_uniform3d_n2048", 2048), ("h2_imq3d_n262144", 4096),
-                                    ("h2_gmm8d_n65536", 4096)])
+                                    ("h2_gmm8d_n65536", 4096), ("h2_invdist3d_n262144", 4096)])
 def test_error_is_order_tol(base, n):
     w = reduced(WORKLOADS[base], n, q=8)
     X = make_points(w)
@@ -212,7 +229,7 @@ def test_linearity_and_column_independence():
         assert np.linalg.norm(yq[:, 0] - Y1[:, q]) <= 1e-15 * np.linalg.norm(Y1[:, q])
 
 
-@pytest.mark.parametrize("base", ["hss_uniform3d_n2048", "h2_imq3d_n262144"])
+@pytest.mark.parametrize("base", ["hss_uniform3d_n2048", "h2_imq3d_n262144", "h2_invdist3d_n262144"])
 def test_symmetry(base):
     # U = V and B_ba = B_ab^T, D_ji = D_ij^T, so K~ is symmetric: W1^T (K~ W2) = W2^T (K~ W1)
     w = reduced(WORKLOADS[base], 2048, q=3)

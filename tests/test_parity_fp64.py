@@ -51,6 +51,7 @@ CASES = [
     ("hss_uniform3d_n2048", 1000, 1, ()),                       # q = 1
     ("hss_uniform3d_n2048", 777, 3, (("leaf_size", 50),)),      # q = 3, odd sizes
     ("h2_gmm8d_n65536", 4096, 2, ()),                           # q = 2 (2-column tiles)
+    ("h2_invdist3d_n262144", 3000, 1, ()),                      # 1/r kernel, matrix-vector (q = 1)
     ("h2_imq3d_n262144", 3000, 8, ()),                          # q = 8 (8-column tiles)
     ("h2_imq3d_n262144", 2500, 17, (("admissibility", "none"),)),          # all near
     ("hss_uniform3d_n2048", 1500, 20, (("tol", 0.0), ("max_rank", 10 ** 6))),  # rank = |rows|

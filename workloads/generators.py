@@ -45,15 +45,16 @@ class Workload:
     ``admissibility`` is ``"hss"`` (every pair of siblings is far: weak
     admissibility) or ``"geometric"`` (boxes far when the distance of their
     centroids exceeds ``eta`` times the larger of their radii).
-    ``kernel`` is ``"gaussian"`` (exp(-r^2 / (2 h^2)), param = h) or ``"imq"``
-    (1 / sqrt(r^2 + c^2), param = c).
+    ``kernel`` is ``"gaussian"`` (exp(-r^2 / (2 h^2)), param = h), ``"imq"``
+    (1 / sqrt(r^2 + c^2), param = c) or ``"invdist"`` (1 / r, 0 for coincident
+    points; param unused).
     """
     name: str
     n: int
     d: int
     points: str            # "uniform" or "gmm"
     admissibility: str     # "hss" or "geometric"
-    kernel: str            # "gaussian" or "imq"
+    kernel: str            # "gaussian", "imq" or "invdist"
     kernel_param: float
     leaf_size: int
     tol: float
@@ -86,6 +87,10 @@ WORKLOADS = {
     # ID tol 1e-7, rank <= 256, Q=512.
     "h2_imq3d_n262144": Workload("h2_imq3d_n262144", 262144, 3, "uniform", "geometric", "imq", 0.1,
                                  256, 1e-7, 256, 512),
+    # Matrix-vector form of the comparison with SMASH: H2 geometric, N=262144 uniform in
+    # [0,1]^3, kernel 1/r, leaf 256, ID tol 1e-6, rank <= 256, Q=1.
+    "h2_invdist3d_n262144": Workload("h2_invdist3d_n262144", 262144, 3, "uniform", "geometric", "invdist", 0.0,
+                                     256, 1e-6, 256, 1),
 }
 
 
