@@ -297,6 +297,7 @@ def run_gpu(args, dist: Dist) -> None:
         line["mixed"] = mixed
     dev.close()
 
+    line["inspector_reuse"] = run_inspector_reuse(w, X)
     if args.precision == "on":
         line["precision"] = run_precision(args, dist)
     if args.matvec == "on":
@@ -362,6 +363,27 @@ def run_mixed(args, dev, W, Y64, q, info, stream, dist) -> dict:
             "error_vs_fp64": err, "dtype": "f16 hi+lo split, f32 accumulate",
             "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
             "gpu_launches": sum(c for _, c in phases.values()), "roofline": roof, "autotune": tune}
+
+
+def run_inspector_reuse(w, X) -> dict:
+    """Inspector reuse (Section 3.2): the plan (tree + near/far lists) is built once, then the
+    HMatrix is recompressed for the recipe's tolerance and for a ten times looser one without
+    rebuilding it; times in seconds, each recompression including its load to the GPU."""
+    import paper_1812_07152_gb300 as hp
+    t0 = time.perf_counter()
+    plan = hp.hmat_plan_create(X, admissibility=w.admissibility, leaf_size=w.leaf_size, eta=w.eta)
+    t_plan = time.perf_counter() - t0
+    out = {"plan_s": round(t_plan, 3), "recompress_s": {}}
+    try:
+        for tol in (w.tol, 10 * w.tol):
+            t0 = time.perf_counter()
+            h = hp.hmat_plan_build(plan, w.kernel, w.kernel_param, tol, w.max_rank, sample_seed=w.sample_seed)
+            out["recompress_s"][f"{tol:g}"] = round(time.perf_counter() - t0, 3)
+            out.setdefault("sum_rank", {})[f"{tol:g}"] = hp.hmat_info(h)["sum_rank"]
+            hp.hmat_free(h)
+    finally:
+        hp.hmat_plan_free(plan)
+    return out
 
 
 def run_precision(args, dist) -> dict:

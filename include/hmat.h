@@ -98,7 +98,16 @@ typedef struct {
  * HMAT_ADM_GEOMETRIC - nodes a, b are far when the distance of their centroids
  *   exceeds eta * max(r_a, r_b), r the largest distance of a point of the node
  *   to its centroid (the paper's tau * dist > diam_a + diam_b with tau = 2/eta);
- * HMAT_ADM_NONE - nothing is far: every block is kept dense.
+ * HMAT_ADM_NONE - nothing is far: every block is kept dense;
+ * HMAT_ADM_TAU - the paper's tau * dist(a, b) > diam(a) + diam(b) with tau = eta,
+ *   on bounding boxes: dist = the Euclidean gap between the boxes of a and b, diam
+ *   = a box's diagonal.
+ *
+ * Cluster trees (Section 3.1, tree construction): HMAT_TREE_KD splits a node at the
+ * median of its widest bounding-box dimension; HMAT_TREE_TWO_MEANS (the paper's
+ * choice for d > 3) at the median of the projection onto q - p, p the point farthest
+ * from the node's point of smallest input index and q the point farthest from p
+ * (ties by input index). Both give a perfect tree of depth ceil(log2(n / leaf)).
  */
 #define HMAT_KERNEL_GAUSSIAN 0
 #define HMAT_KERNEL_IMQ 1
@@ -106,6 +115,9 @@ typedef struct {
 #define HMAT_ADM_HSS 0
 #define HMAT_ADM_GEOMETRIC 1
 #define HMAT_ADM_NONE 2
+#define HMAT_ADM_TAU 3
+#define HMAT_TREE_KD 0
+#define HMAT_TREE_TWO_MEANS 1
 
 typedef struct {
   int64_t n_points;
@@ -121,15 +133,17 @@ typedef struct {
   int32_t exact_columns;     /* 1: every far point as ID column, 0: a sample, -1: exact iff n_points <= 4096 */
   uint64_t sample_seed;      /* seed of the column sample */
   int32_t threads;           /* host threads of the inspector (0: all cores) */
+  int32_t tree;              /* HMAT_TREE_KD or HMAT_TREE_TWO_MEANS */
 } hmat_build_params;
 
 /*
  * hmat_build - compress the kernel matrix of a point set and load it.
  *
- * The cluster tree is a perfect kd-tree of depth L = ceil(log2(n / leaf_size)):
- * every node above the leaves is split at the median of its widest bounding-box
- * dimension (lowest dimension on ties; points ordered by that coordinate, then
- * by input index; the left child takes floor(n/2)). Near/far pairs come from a
+ * The cluster tree is a perfect binary tree of depth L = ceil(log2(n / leaf_size)):
+ * every node above the leaves is split at a median (HMAT_TREE_KD: of its widest
+ * bounding-box dimension, lowest dimension on ties, points ordered by that
+ * coordinate, then by input index; HMAT_TREE_TWO_MEANS: see above; the left child
+ * takes floor(n/2)). Near/far pairs come from a
  * dual-tree traversal from (root, root). Each node that is, or has an ancestor
  * that is, in a far pair gets a nested row interpolative decomposition (column-
  * pivoted Householder QR of K(R, C)^T; R = the node's points for a leaf and the
@@ -139,6 +153,45 @@ typedef struct {
  * the packed device arena. Synchronous; host threads as requested.
  */
 hmat_status hmat_build(const hmat_build_params* params, int flags, hmat_t* out);
+
+/*
+ * Inspector reuse (Section 3.2, "Reusing inspection"): the tree and the near/far
+ * lists depend only on the points and the admissibility (inspector-p1); the bases
+ * and blocks depend on the kernel and the accuracy too (inspector-p2). A plan holds
+ * the first part, so a new kernel, kernel parameter or tolerance recompresses
+ * without rebuilding it.
+ *
+ * hmat_plan_create - build the cluster tree and the interaction lists of a point
+ * set (the tree, admissibility and threads of hmat_build; copies the points).
+ * hmat_plan_build - nested row IDs for one kernel and accuracy on the host, near
+ * and coupling blocks evaluated on the GPU, then the load; returns a new handle
+ * that owns its memory (the plan may be freed or reused afterwards). hmat_build is
+ * hmat_plan_create + hmat_plan_build + hmat_plan_free, so both give bitwise the
+ * same HMatrix.
+ * hmat_plan_free - release the plan (NULL is a no-op).
+ */
+typedef struct hmat_plan* hmat_plan_t;
+typedef struct {
+  int64_t n_points;
+  int32_t dim;
+  const double* points;      /* host, n_points x dim, row-major, caller order */
+  int32_t admissibility;     /* HMAT_ADM_* */
+  double eta;
+  int32_t leaf_size;         /* >= 2 */
+  int32_t threads;           /* host threads (0: all cores) */
+  int32_t tree;              /* HMAT_TREE_KD or HMAT_TREE_TWO_MEANS */
+} hmat_plan_params;
+typedef struct {
+  int32_t kernel;            /* HMAT_KERNEL_* */
+  double kernel_param;
+  double tol;                /* ID tolerance (bacc) */
+  int32_t max_rank;          /* rank cap (>= 1) */
+  int32_t exact_columns;     /* as in hmat_build_params */
+  uint64_t sample_seed;
+} hmat_compress_params;
+hmat_status hmat_plan_create(const hmat_plan_params* params, hmat_plan_t* out);
+hmat_status hmat_plan_build(hmat_plan_t plan, const hmat_compress_params* params, int flags, hmat_t* out);
+hmat_status hmat_plan_free(hmat_plan_t plan);
 
 /*
  * hmat_structure - copy out the structure of a loaded HMatrix (each pointer may

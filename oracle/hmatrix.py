@@ -9,7 +9,7 @@ generator package ``workloads``, which holds none of the method's arithmetic.
 What it builds and computes, with the passage each part follows:
 
 * kernel matrix K(i, j) = k(x_i, x_j)                       (Section 1; 1/r: Section 4.1)
-* cluster tree by recursive kd median splits                (Section 3.1, "Tree construction")
+* cluster tree by recursive kd or two-means median splits   (Section 3.1, "Tree construction")
 * near / far interactions from an admissibility condition   (Section 2.1, "Compression"; Section 4.1 for HSS)
 * nested interpolative decomposition of the far field       (Section 2.1 footnote; Section 3.1, "Low-rank approximation")
 * full-rank near blocks D and coupling blocks B             (Section 3.1)
@@ -28,6 +28,11 @@ builder only through the fixture itself, never through shared code):
 * geometric admissibility: far iff ||c_a - c_b|| > eta * max(r_a, r_b), c the
   centroid and r the largest distance of a point to it; found by a dual-tree
   traversal from (root, root);
+* two-means (Section 3.1 names it for d > 3 without an algorithm): p farthest
+  from the node's point of smallest input index, q farthest from p, points
+  ordered by their projection onto q - p, split at the median;
+* the paper's tau * dist(a, b) > diam(a) + diam(b) (Section 2.1) on bounding
+  boxes: dist = the gap between the boxes, diam = the box diagonal;
 * HSS: every pair of distinct siblings is far, every leaf is near itself only;
 * ID: column-pivoted QR of K(R, C)^T, rank = #{j : |R_jj| > tol * |R_11|}
   capped at max_rank, columns C = every point whose interaction with the node
@@ -121,8 +126,44 @@ def tree_depth(n: int, leaf_size: int) -> int:
     return L
 
 
-def build_cluster_tree(X: np.ndarray, leaf_size: int) -> ClusterTree:
-    """kd-tree with median splits down to a common depth (Section 3.1)."""
+def _sq_dist_seq(A: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """||a - y||^2 for every row a of A, summed over the coordinates in order."""
+    out = np.zeros(A.shape[0])
+    for k in range(A.shape[1]):
+        diff = A[:, k] - y[k]
+        out = out + diff * diff
+    return out
+
+
+def _first_argmax(values: np.ndarray, idx: np.ndarray) -> int:
+    """Position of the largest value, the smallest input index among equal ones."""
+    best = values.max()
+    cand = np.flatnonzero(values == best)
+    return int(cand[np.argmin(idx[cand])])
+
+
+def two_means_order(pts: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """Balanced two-means split of one node (Section 3.1: two-means partitioning for
+    d > 3; the paper gives no algorithm). Two mutually far centres: p is the point
+    farthest from the point of smallest input index, q the point farthest from p
+    (ties by input index); each point is ordered by its projection onto q - p (ties
+    by input index) and the first floor(n/2) form the left child, so the tree stays
+    balanced."""
+    a0 = int(np.argmin(idx))
+    p = pts[_first_argmax(_sq_dist_seq(pts, pts[a0]), idx)]
+    q = pts[_first_argmax(_sq_dist_seq(pts, p), idx)]
+    proj = np.zeros(pts.shape[0])
+    for k in range(pts.shape[1]):
+        proj = proj + (pts[:, k] - p[k]) * (q[k] - p[k])
+    return np.lexsort((idx, proj))
+
+
+def build_cluster_tree(X: np.ndarray, leaf_size: int, tree: str = "kd") -> ClusterTree:
+    """Perfect binary cluster tree with median splits down to a common depth (Section
+    3.1): ``tree`` is ``"kd"`` (split the widest bounding-box dimension) or
+    ``"two_means"`` (split along the axis of two mutually far points)."""
+    if tree not in ("kd", "two_means"):
+        raise ValueError(f"unknown tree {tree!r}")
     n = X.shape[0]
     if leaf_size < 2:
         raise ValueError("leaf size must be at least 2 (so that no leaf is empty)")
@@ -137,9 +178,14 @@ def build_cluster_tree(X: np.ndarray, leaf_size: int) -> ClusterTree:
             b0, nb = begin[a], size[a]
             idx = perm[b0:b0 + nb]
             pts = X[idx]
-            extent = pts.max(axis=0) - pts.min(axis=0)
-            dim = int(np.argmax(extent))           # first maximum: lowest index on ties
-            order = np.lexsort((idx, pts[:, dim]))  # by coordinate, then by input index
+            if nb == 0:
+                order = np.zeros(0, dtype=np.int64)
+            elif tree == "two_means":
+                order = two_means_order(pts, idx)
+            else:
+                extent = pts.max(axis=0) - pts.min(axis=0)
+                dim = int(np.argmax(extent))           # first maximum: lowest index on ties
+                order = np.lexsort((idx, pts[:, dim]))  # by coordinate, then by input index
             perm[b0:b0 + nb] = idx[order]
             half = nb // 2
             begin[2 * a + 1], size[2 * a + 1] = b0, half
@@ -171,14 +217,36 @@ def node_geometry(tree: ClusterTree, Xt: np.ndarray) -> Tuple[np.ndarray, np.nda
     return cent, rad
 
 
+def node_boxes(tree: ClusterTree, Xt: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """Bounding box (lowest and highest coordinate per dimension) of every node."""
+    d = Xt.shape[1]
+    lo = np.zeros((tree.n_nodes, d))
+    hi = np.zeros((tree.n_nodes, d))
+    for a in range(tree.n_nodes):
+        pts = Xt[tree.begin[a]:tree.begin[a] + tree.size[a]]
+        if len(pts):
+            lo[a], hi[a] = pts.min(axis=0), pts.max(axis=0)
+    return lo, hi
+
+
 def compute_interactions(tree: ClusterTree, Xt: np.ndarray, mode: str, eta: float = 2.0) -> Interactions:
     """Dual-tree traversal from (root, root). A pair of distinct nodes that is
     admissible is far; a pair of leaves that is not is near; otherwise the four
     child pairs are visited. ``mode`` is ``"hss"`` (distinct siblings are always
-    admissible), ``"geometric"`` (centroid distance > eta * max radius) or
-    ``"none"`` (nothing is admissible: every leaf pair is near)."""
+    admissible), ``"geometric"`` (centroid distance > eta * max radius), ``"tau"``
+    (the paper's tau * dist(a, b) > diam(a) + diam(b) of Section 2.1, with tau =
+    ``eta``, read on bounding boxes: dist = the Euclidean gap between the two boxes,
+    diam = a box's diagonal; sums over the coordinates in order) or ``"none"``
+    (nothing is admissible: every leaf pair is near)."""
     if mode == "geometric":
         cent, rad = node_geometry(tree, Xt)
+    if mode == "tau":
+        lo, hi = node_boxes(tree, Xt)
+        diam = np.zeros(tree.n_nodes)
+        for k in range(Xt.shape[1]):
+            ext = hi[:, k] - lo[:, k]
+            diam = diam + ext * ext
+        diam = np.sqrt(diam)
 
     def admissible(a: int, b: int) -> bool:
         if a == b:
@@ -190,6 +258,12 @@ def compute_interactions(tree: ClusterTree, Xt: np.ndarray, mode: str, eta: floa
         if mode == "geometric":
             dist = float(np.sqrt(((cent[a] - cent[b]) ** 2).sum()))
             return dist > eta * max(rad[a], rad[b])
+        if mode == "tau":
+            g2 = 0.0
+            for k in range(Xt.shape[1]):
+                gap = max(0.0, float(lo[b, k] - hi[a, k]), float(lo[a, k] - hi[b, k]))
+                g2 = g2 + gap * gap
+            return eta * math.sqrt(g2) > float(diam[a] + diam[b])
         raise ValueError(f"unknown admissibility {mode!r}")
 
     near, far = [], []
@@ -293,10 +367,10 @@ def far_columns(tree: ClusterTree, far_of: Dict[int, List[int]], a: int) -> np.n
 
 def compress(X: np.ndarray, leaf_size: int, admissibility: str, kernel: str, kernel_param: float,
              tol: float, max_rank: int, sample_seed: int = 2, eta: float = 2.0,
-             exact_columns: Optional[bool] = None) -> HMatrix:
+             exact_columns: Optional[bool] = None, tree: str = "kd") -> HMatrix:
     """Build the HMatrix of K = k(X, X): tree, interactions, nested row IDs bottom-up,
     then the dense near blocks and the coupling blocks on the skeletons."""
-    tree = build_cluster_tree(X, leaf_size)
+    tree = build_cluster_tree(X, leaf_size, tree)
     Xt = X[tree.perm]
     inter = compute_interactions(tree, Xt, admissibility, eta)
     far_of: Dict[int, List[int]] = {}
@@ -346,7 +420,7 @@ def compress_workload(w, **overrides) -> Tuple[HMatrix, np.ndarray]:
     X = make_points(w)
     kw = dict(leaf_size=w.leaf_size, admissibility=w.admissibility, kernel=w.kernel,
               kernel_param=w.kernel_param, tol=w.tol, max_rank=w.max_rank,
-              sample_seed=w.sample_seed, eta=w.eta)
+              sample_seed=w.sample_seed, eta=w.eta, tree=w.tree)
     kw.update(overrides)
     return compress(X, **kw), X
 

@@ -1,7 +1,8 @@
 // Inspector: the compression modules of Section 3.1 on the host, in native code.
 //
-//  * tree construction: a perfect kd-tree by median splits (the widest bounding-box
-//    dimension; lowest dimension on ties; ties of coordinates by input index);
+//  * tree construction: a perfect binary tree by median splits, kd (the widest
+//    bounding-box dimension; lowest dimension on ties; ties of coordinates by input
+//    index) or two-means (along the axis of two mutually far points);
 //  * interaction computation: a dual-tree traversal from (root, root) that marks a
 //    pair far when it is admissible (Section 2.1) and near when two leaves are not;
 //  * low-rank approximation: a nested row interpolative decomposition per node,
@@ -15,6 +16,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <numeric>
 #include <thread>
 #include <vector>
@@ -73,7 +75,52 @@ int tree_depth(int64_t n, int64_t leaf) {
   return L;
 }
 
-void build_tree(const double* X, int64_t n, int d, int leaf, int threads, Tree* t) {
+double sq_dist(const double* x, const double* y, int d) {
+  double s = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const double diff = x[k] - y[k];
+    s += diff * diff;
+  }
+  return s;
+}
+
+// Position (in idx) of the point farthest from y, the smallest input index among ties.
+int64_t farthest(const double* X, int d, const int64_t* idx, int64_t nb, const double* y) {
+  int64_t best = 0;
+  double bd = -1.0;
+  for (int64_t i = 0; i < nb; ++i) {
+    const double v = sq_dist(X + idx[i] * d, y, d);
+    if (v > bd || (v == bd && idx[i] < idx[best])) {
+      bd = v;
+      best = i;
+    }
+  }
+  return best;
+}
+
+// Balanced two-means split order of one node (Section 3.1 names two-means for d > 3
+// without an algorithm): p is the point farthest from the node's point of smallest
+// input index, q the point farthest from p; points are ordered by their projection
+// onto q - p (ties by input index), the first floor(n/2) form the left child.
+void two_means_order(const double* X, int d, int64_t* idx, int64_t nb) {
+  int64_t a0 = 0;
+  for (int64_t i = 1; i < nb; ++i)
+    if (idx[i] < idx[a0]) a0 = i;
+  const int64_t ip = farthest(X, d, idx, nb, X + idx[a0] * d);
+  const double* p = X + idx[ip] * d;
+  const int64_t iq = farthest(X, d, idx, nb, p);
+  const double* q = X + idx[iq] * d;
+  std::vector<std::pair<double, int64_t>> key(nb);
+  for (int64_t i = 0; i < nb; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) s += (X[idx[i] * d + k] - p[k]) * (q[k] - p[k]);
+    key[i] = {s, idx[i]};
+  }
+  std::sort(key.begin(), key.end());
+  for (int64_t i = 0; i < nb; ++i) idx[i] = key[i].second;
+}
+
+void build_tree(const double* X, int64_t n, int d, int leaf, int tree, int threads, Tree* t) {
   t->levels = tree_depth(n, leaf);
   t->n_nodes = ((int64_t)2 << t->levels) - 1;
   t->first_leaf = ((int64_t)1 << t->levels) - 1;
@@ -87,6 +134,16 @@ void build_tree(const double* X, int64_t n, int d, int leaf, int threads, Tree* 
     parallel_for(cnt, threads, [&](int64_t k) {
       const int64_t a = lo + k, b0 = t->begin[a], nb = t->size[a];
       int64_t* idx = t->perm.data() + b0;
+      const int64_t half = nb / 2;
+      t->begin[2 * a + 1] = b0;
+      t->size[2 * a + 1] = half;
+      t->begin[2 * a + 2] = b0 + half;
+      t->size[2 * a + 2] = nb - half;
+      if (nb == 0) return;
+      if (tree == HMAT_TREE_TWO_MEANS) {
+        two_means_order(X, d, idx, nb);
+        return;
+      }
       int dim = 0;
       double best = -1.0;
       for (int j = 0; j < d; ++j) {
@@ -102,11 +159,6 @@ void build_tree(const double* X, int64_t n, int d, int leaf, int threads, Tree* 
         const double vp = X[p * d + dim], vq = X[q * d + dim];
         return vp < vq || (vp == vq && p < q);
       });
-      const int64_t half = nb / 2;
-      t->begin[2 * a + 1] = b0;
-      t->size[2 * a + 1] = half;
-      t->begin[2 * a + 2] = b0 + half;
-      t->size[2 * a + 2] = nb - half;
     });
   }
 }
@@ -137,11 +189,43 @@ void geometry(const Tree& t, const double* Xt, int d, int threads, std::vector<d
 
 void interactions(const Tree& t, const double* Xt, int d, int adm, double eta, int threads,
                   std::vector<std::pair<int64_t, int64_t>>* near, std::vector<std::pair<int64_t, int64_t>>* far) {
-  std::vector<double> cent, rad;
+  std::vector<double> cent, rad, lo, hi, diam;
   if (adm == HMAT_ADM_GEOMETRIC) geometry(t, Xt, d, threads, &cent, &rad);
+  if (adm == HMAT_ADM_TAU) {  // bounding boxes and their diagonals
+    lo.assign(t.n_nodes * d, 0.0);
+    hi.assign(t.n_nodes * d, 0.0);
+    diam.assign(t.n_nodes, 0.0);
+    parallel_for(t.n_nodes, threads, [&](int64_t a) {
+      const int64_t b0 = t.begin[a], nb = t.size[a];
+      if (nb == 0) return;
+      for (int j = 0; j < d; ++j) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (int64_t i = 0; i < nb; ++i) {
+          mn = std::min(mn, Xt[(b0 + i) * d + j]);
+          mx = std::max(mx, Xt[(b0 + i) * d + j]);
+        }
+        lo[a * d + j] = mn;
+        hi[a * d + j] = mx;
+      }
+      double s = 0.0;
+      for (int j = 0; j < d; ++j) {
+        const double ext = hi[a * d + j] - lo[a * d + j];
+        s += ext * ext;
+      }
+      diam[a] = std::sqrt(s);
+    });
+  }
   auto admissible = [&](int64_t a, int64_t b) {
     if (a == b || adm == HMAT_ADM_NONE) return false;
     if (adm == HMAT_ADM_HSS) return true;
+    if (adm == HMAT_ADM_TAU) {  // tau * dist(a, b) > diam(a) + diam(b), dist = the gap between the boxes
+      double g2 = 0.0;
+      for (int j = 0; j < d; ++j) {
+        const double gap = std::max(0.0, std::max(lo[b * d + j] - hi[a * d + j], lo[a * d + j] - hi[b * d + j]));
+        g2 += gap * gap;
+      }
+      return eta * std::sqrt(g2) > diam[a] + diam[b];
+    }
     double s = 0.0;
     for (int j = 0; j < d; ++j) {
       const double diff = cent[a * d + j] - cent[b * d + j];
@@ -268,38 +352,80 @@ void row_id(const std::vector<double>& Xt, int d, int kernel, double param, cons
 
 using namespace hmat;
 
-extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t* out) {
+// Inspector-p1 of Section 3.2 ("Reusing inspection"): everything that depends on the
+// points and the admissibility only, kept so that a change of kernel or accuracy
+// recompresses without rebuilding it.
+struct hmat_plan {
+  int64_t n = 0;
+  int d = 0;
+  int threads = 1;
+  Tree t;
+  std::vector<double> Xt;                           // points in tree order
+  std::vector<std::pair<int64_t, int64_t>> near, far;
+  std::vector<std::vector<int64_t>> far_of;         // far partners per node
+  std::vector<uint8_t> needs;                       // node needs a basis
+};
+
+namespace {
+
+bool valid_compress(const hmat_compress_params* c) {
+  return c && c->max_rank >= 1 && c->tol >= 0.0 &&
+         (c->kernel == HMAT_KERNEL_GAUSSIAN || c->kernel == HMAT_KERNEL_IMQ || c->kernel == HMAT_KERNEL_INVDIST) &&
+         (c->kernel == HMAT_KERNEL_INVDIST || c->kernel_param > 0.0);
+}
+
+}  // namespace
+
+extern "C" hmat_status hmat_plan_create(const hmat_plan_params* p, hmat_plan_t* out) {
   if (!out) return HMAT_EINVAL;
   *out = nullptr;
-  if (flags & ~HMAT_LOAD_MIXED) return HMAT_EUNSUPPORTED;
-  if (!p || p->n_points < 1 || p->dim < 1 || p->dim > 64 || !p->points || p->leaf_size < 2 || p->max_rank < 1 ||
-      !(p->tol >= 0.0) ||
-      (p->kernel != HMAT_KERNEL_GAUSSIAN && p->kernel != HMAT_KERNEL_IMQ && p->kernel != HMAT_KERNEL_INVDIST) ||
-      (p->kernel != HMAT_KERNEL_INVDIST && !(p->kernel_param > 0.0)) ||
+  if (!p || p->n_points < 1 || p->dim < 1 || p->dim > 64 || !p->points || p->leaf_size < 2 ||
       (p->admissibility != HMAT_ADM_HSS && p->admissibility != HMAT_ADM_GEOMETRIC &&
-       p->admissibility != HMAT_ADM_NONE) ||
-      (p->admissibility == HMAT_ADM_GEOMETRIC && !(p->eta > 0.0)))
+       p->admissibility != HMAT_ADM_NONE && p->admissibility != HMAT_ADM_TAU) ||
+      ((p->admissibility == HMAT_ADM_GEOMETRIC || p->admissibility == HMAT_ADM_TAU) && !(p->eta > 0.0)) ||
+      (p->tree != HMAT_TREE_KD && p->tree != HMAT_TREE_TWO_MEANS))
     return HMAT_EINVAL;
   const int64_t n = p->n_points;
   const int d = p->dim;
   for (int64_t i = 0; i < n * d; ++i)
     if (!std::isfinite(p->points[i])) return HMAT_EINVAL;
-  const int threads = p->threads > 0 ? p->threads : (int)std::max(1u, std::thread::hardware_concurrency());
+  hmat_plan* pl = new (std::nothrow) hmat_plan();
+  if (!pl) return HMAT_ENOMEM;
+  pl->n = n;
+  pl->d = d;
+  pl->threads = p->threads > 0 ? p->threads : (int)std::max(1u, std::thread::hardware_concurrency());
+  Tree& t = pl->t;
+  build_tree(p->points, n, d, p->leaf_size, p->tree, pl->threads, &t);
+  pl->Xt.resize((size_t)(n * d));
+  for (int64_t k = 0; k < n; ++k) std::memcpy(&pl->Xt[k * d], &p->points[t.perm[k] * d], d * sizeof(double));
+  interactions(t, pl->Xt.data(), d, p->admissibility, p->eta, pl->threads, &pl->near, &pl->far);
+  pl->far_of.assign(t.n_nodes, {});
+  for (auto [a, b] : pl->far) pl->far_of[a].push_back(b);
+  pl->needs.assign(t.n_nodes, 0);
+  for (int64_t a = 1; a < t.n_nodes; ++a) pl->needs[a] = !pl->far_of[a].empty() || pl->needs[(a - 1) / 2];
+  *out = pl;
+  return HMAT_OK;
+}
 
-  Tree t;
-  build_tree(p->points, n, d, p->leaf_size, threads, &t);
-  std::vector<double> Xt((size_t)(n * d));
-  for (int64_t k = 0; k < n; ++k) std::memcpy(&Xt[k * d], &p->points[t.perm[k] * d], d * sizeof(double));
+extern "C" hmat_status hmat_plan_free(hmat_plan_t plan) {
+  delete plan;
+  return HMAT_OK;
+}
 
-  std::vector<std::pair<int64_t, int64_t>> near, far;
-  interactions(t, Xt.data(), d, p->admissibility, p->eta, threads, &near, &far);
-  std::vector<std::vector<int64_t>> far_of(t.n_nodes);
-  for (auto [a, b] : far) far_of[a].push_back(b);
-  std::vector<uint8_t> needs(t.n_nodes, 0);
-  for (int64_t a = 1; a < t.n_nodes; ++a) needs[a] = !far_of[a].empty() || needs[(a - 1) / 2];
-
-  const bool exact = p->exact_columns > 0 || (p->exact_columns < 0 && n <= kExactColumnsMaxN);
-  const int64_t n_sample = std::max<int64_t>(4 * (int64_t)p->max_rank, 512);
+// Inspector-p2: the nested row IDs for this kernel and accuracy, then the load (near
+// and coupling blocks evaluated on the GPU).
+extern "C" hmat_status hmat_plan_build(hmat_plan_t pl, const hmat_compress_params* c, int flags, hmat_t* out) {
+  if (!out) return HMAT_EINVAL;
+  *out = nullptr;
+  if (flags & ~HMAT_LOAD_MIXED) return HMAT_EUNSUPPORTED;
+  if (!pl || !valid_compress(c)) return HMAT_EINVAL;
+  const Tree& t = pl->t;
+  const int64_t n = pl->n;
+  const int d = pl->d;
+  const int threads = pl->threads;
+  const std::vector<double>& Xt = pl->Xt;
+  const bool exact = c->exact_columns > 0 || (c->exact_columns < 0 && n <= kExactColumnsMaxN);
+  const int64_t n_sample = std::max<int64_t>(4 * (int64_t)c->max_rank, 512);
   std::vector<std::vector<int64_t>> skel(t.n_nodes);
   std::vector<std::vector<double>> basis(t.n_nodes);
   std::vector<int32_t> rank(t.n_nodes, 0);
@@ -307,7 +433,7 @@ extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t*
     const int64_t lo = ((int64_t)1 << level) - 1, cnt = (int64_t)1 << level;
     parallel_for(cnt, threads, [&](int64_t k) {
       const int64_t a = lo + k;
-      if (!needs[a]) return;
+      if (!pl->needs[a]) return;
       std::vector<int64_t> rows;
       if (level == t.levels) {
         rows.resize(t.size[a]);
@@ -318,13 +444,13 @@ extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t*
       }
       std::vector<int64_t> cols;
       for (int64_t g = a;; g = (g - 1) / 2) {
-        for (int64_t b : far_of[g])
+        for (int64_t b : pl->far_of[g])
           for (int64_t i = 0; i < t.size[b]; ++i) cols.push_back(t.begin[b] + i);
         if (g == 0) break;
       }
       std::sort(cols.begin(), cols.end());
       if (!exact && (int64_t)cols.size() > n_sample) {  // seeded uniform sample without replacement
-        uint64_t state = p->sample_seed * 0x100000001B3ull + (uint64_t)a;
+        uint64_t state = c->sample_seed * 0x100000001B3ull + (uint64_t)a;
         for (int64_t i = 0; i < n_sample; ++i) {
           const int64_t j = i + (int64_t)(splitmix64(state) % (uint64_t)(cols.size() - i));
           std::swap(cols[i], cols[j]);
@@ -332,7 +458,7 @@ extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t*
         cols.resize(n_sample);
         std::sort(cols.begin(), cols.end());
       }
-      row_id(Xt, d, p->kernel, p->kernel_param, rows, cols, p->tol, p->max_rank, &skel[a], &basis[a]);
+      row_id(Xt, d, c->kernel, c->kernel_param, rows, cols, c->tol, c->max_rank, &skel[a], &basis[a]);
       rank[a] = (int32_t)skel[a].size();
     });
   }
@@ -340,12 +466,12 @@ extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t*
   // assemble the hmat_desc structure (blocks are evaluated on the device)
   std::vector<int64_t> near_ptr(t.first_leaf + 2, 0), far_ptr(t.n_nodes + 1, 0);
   std::vector<int32_t> near_idx, far_idx;
-  for (auto [i, j] : near) near_ptr[i - t.first_leaf + 1]++;
+  for (auto [i, j] : pl->near) near_ptr[i - t.first_leaf + 1]++;
   for (size_t i = 1; i < near_ptr.size(); ++i) near_ptr[i] += near_ptr[i - 1];
-  for (auto [i, j] : near) near_idx.push_back((int32_t)(j - t.first_leaf));
-  for (auto [a, b] : far) far_ptr[a + 1]++;
+  for (auto [i, j] : pl->near) near_idx.push_back((int32_t)(j - t.first_leaf));
+  for (auto [a, b] : pl->far) far_ptr[a + 1]++;
   for (size_t i = 1; i < far_ptr.size(); ++i) far_ptr[i] += far_ptr[i - 1];
-  for (auto [a, b] : far) far_idx.push_back((int32_t)b);
+  for (auto [a, b] : pl->far) far_idx.push_back((int32_t)b);
   std::vector<const double*> basis_ptr(t.n_nodes, nullptr);
   std::vector<int64_t> skel_points;
   for (int64_t a = 0; a < t.n_nodes; ++a) {
@@ -366,6 +492,23 @@ extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t*
   desc.coupling = nullptr;
   desc.near = nullptr;
   desc.perm = t.perm.data();
-  DeviceBlockSource src{Xt.data(), d, skel_points.data(), p->kernel, p->kernel_param};
+  DeviceBlockSource src{Xt.data(), d, skel_points.data(), c->kernel, c->kernel_param};
   return load_impl(&desc, &src, flags, out);
+}
+
+extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t* out) {
+  if (!out) return HMAT_EINVAL;
+  *out = nullptr;
+  if (flags & ~HMAT_LOAD_MIXED) return HMAT_EUNSUPPORTED;
+  if (!p) return HMAT_EINVAL;
+  const hmat_compress_params c{p->kernel, p->kernel_param, p->tol, p->max_rank, p->exact_columns, p->sample_seed};
+  if (!valid_compress(&c)) return HMAT_EINVAL;
+  const hmat_plan_params pp{p->n_points, p->dim, p->points, p->admissibility, p->eta, p->leaf_size, p->threads,
+                            p->tree};
+  hmat_plan_t plan = nullptr;
+  hmat_status st = hmat_plan_create(&pp, &plan);
+  if (st != HMAT_OK) return st;
+  st = hmat_plan_build(plan, &c, flags, out);
+  hmat_plan_free(plan);
+  return st;
 }

@@ -62,9 +62,13 @@ HMAT_KERNEL_INVDIST = 2
 HMAT_ADM_HSS = 0
 HMAT_ADM_GEOMETRIC = 1
 HMAT_ADM_NONE = 2
+HMAT_ADM_TAU = 3
+HMAT_TREE_KD = 0
+HMAT_TREE_TWO_MEANS = 1
 
 _KERNELS = {"gaussian": HMAT_KERNEL_GAUSSIAN, "imq": HMAT_KERNEL_IMQ, "invdist": HMAT_KERNEL_INVDIST}
-_ADMISSIBILITY = {"hss": HMAT_ADM_HSS, "geometric": HMAT_ADM_GEOMETRIC, "none": HMAT_ADM_NONE}
+_ADMISSIBILITY = {"hss": HMAT_ADM_HSS, "geometric": HMAT_ADM_GEOMETRIC, "none": HMAT_ADM_NONE, "tau": HMAT_ADM_TAU}
+_TREES = {"kd": HMAT_TREE_KD, "two_means": HMAT_TREE_TWO_MEANS}
 
 
 class HmatBuildParams(ctypes.Structure):
@@ -82,7 +86,19 @@ class HmatBuildParams(ctypes.Structure):
         ("exact_columns", ctypes.c_int32),
         ("sample_seed", ctypes.c_uint64),
         ("threads", ctypes.c_int32),
+        ("tree", ctypes.c_int32),
     ]
+
+
+class HmatPlanParams(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("dim", ctypes.c_int32), ("points", ctypes.POINTER(ctypes.c_double)),
+                ("admissibility", ctypes.c_int32), ("eta", ctypes.c_double), ("leaf_size", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("tree", ctypes.c_int32)]
+
+
+class HmatCompressParams(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("kernel_param", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_rank", ctypes.c_int32), ("exact_columns", ctypes.c_int32), ("sample_seed", ctypes.c_uint64)]
 
 
 class HmatServerParams(ctypes.Structure):
@@ -140,13 +156,18 @@ def library() -> ctypes.CDLL:
         lib.hmat_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.POINTER(HmatTuneReport)]
         lib.hmat_selftest_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        lib.hmat_plan_create.argtypes = [ctypes.POINTER(HmatPlanParams), ctypes.POINTER(ctypes.c_void_p)]
+        lib.hmat_plan_build.argtypes = [ctypes.c_void_p, ctypes.POINTER(HmatCompressParams), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_void_p)]
+        lib.hmat_plan_free.argtypes = [ctypes.c_void_p]
         lib.hmat_strerror.argtypes = [ctypes.c_int]
         lib.hmat_strerror.restype = ctypes.c_char_p
         for name in ("hmat_load", "hmat_build", "hmat_structure", "hmat_eval", "hmat_reserve", "hmat_status_poll",
                      "hmat_info", "hmat_free", "hmat_eval_host", "hmat_profile", "hmat_phase_times",
                      "hmat_measure_fp64_peak", "hmat_batch_create", "hmat_batch_eval", "hmat_batch_free",
                      "hmat_server_create", "hmat_server_submit", "hmat_server_wait", "hmat_server_stats",
-                     "hmat_server_free", "hmat_autotune", "hmat_selftest_timeout"):
+                     "hmat_server_free", "hmat_autotune", "hmat_selftest_timeout", "hmat_plan_create", "hmat_plan_build",
+                     "hmat_plan_free"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -220,15 +241,41 @@ def hmat_load(n_points: int, levels: int, node_begin, node_size, rank, near_ptr,
 
 def hmat_build(points: np.ndarray, kernel: str, kernel_param: float, admissibility: str, leaf_size: int,
                tol: float, max_rank: int, eta: float = 2.0, exact_columns: int = -1, sample_seed: int = 2,
-               threads: int = 0, flags: int = 0) -> int:
+               threads: int = 0, flags: int = 0, tree: str = "kd") -> int:
     """Compress the kernel matrix of `points` (n x d, caller order) and load it; returns the handle."""
     X = np.ascontiguousarray(points, dtype=np.float64)
     p = HmatBuildParams(X.shape[0], X.shape[1], X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                         _KERNELS[kernel], float(kernel_param), _ADMISSIBILITY[admissibility], float(eta),
-                        int(leaf_size), float(tol), int(max_rank), int(exact_columns), int(sample_seed), int(threads))
+                        int(leaf_size), float(tol), int(max_rank), int(exact_columns), int(sample_seed), int(threads),
+                        _TREES[tree])
     h = ctypes.c_void_p()
     _check(library().hmat_build(ctypes.byref(p), int(flags), ctypes.byref(h)), "hmat_build")
     return int(h.value)
+
+
+def hmat_plan_create(points: np.ndarray, admissibility: str, leaf_size: int, eta: float = 2.0,
+                     threads: int = 0, tree: str = "kd") -> int:
+    """Inspector-p1: cluster tree and near/far lists of `points` (n x d, caller order); returns a plan."""
+    X = np.ascontiguousarray(points, dtype=np.float64)
+    p = HmatPlanParams(X.shape[0], X.shape[1], X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       _ADMISSIBILITY[admissibility], float(eta), int(leaf_size), int(threads), _TREES[tree])
+    plan = ctypes.c_void_p()
+    _check(library().hmat_plan_create(ctypes.byref(p), ctypes.byref(plan)), "hmat_plan_create")
+    return int(plan.value)
+
+
+def hmat_plan_build(plan: int, kernel: str, kernel_param: float, tol: float, max_rank: int,
+                    exact_columns: int = -1, sample_seed: int = 2, flags: int = 0) -> int:
+    """Inspector-p2 and load for one kernel and accuracy, reusing the plan; returns the handle."""
+    c = HmatCompressParams(_KERNELS[kernel], float(kernel_param), float(tol), int(max_rank), int(exact_columns),
+                           int(sample_seed))
+    h = ctypes.c_void_p()
+    _check(library().hmat_plan_build(plan, ctypes.byref(c), int(flags), ctypes.byref(h)), "hmat_plan_build")
+    return int(h.value)
+
+
+def hmat_plan_free(plan: int) -> None:
+    _check(library().hmat_plan_free(plan), "hmat_plan_free")
 
 
 def hmat_structure(handle: int) -> dict:

@@ -40,6 +40,9 @@ def _eval(h, W):
     ("h2_gmm8d_n65536", 4096, ()),
     ("h2_imq3d_n262144", 4000, (("leaf_size", 40),)),
     ("h2_invdist3d_n262144", 3000, ()),
+    ("h2_gmm8d_n65536", 4096, (("tree", "two_means"),)),                      # the paper's tree for d > 3
+    ("h2_imq3d_n262144", 3000, (("admissibility", "tau"), ("eta", 3.0))),     # the paper's tau condition
+    ("h2_gmm8d_n65536", 3000, (("tree", "two_means"), ("admissibility", "tau"), ("eta", 5.0))),
 ])
 def test_structure_identical_and_accuracy_comparable(base, n, ov):
     w, H, X = oracle_case(base, n, 8, **dict(ov))
@@ -115,3 +118,41 @@ def test_invdist_blocks_zero_for_coincident_points():
         assert hm.overall_error(_eval(h, W), KW) <= 1e-13
     finally:
         hp.hmat_free(h)
+
+
+def test_plan_reuse_equals_fresh_builds():
+    """Inspector reuse (Section 3.2): one plan (tree + lists) recompressed for other kernels and
+    tolerances gives bitwise the HMatrix of a fresh hmat_build with the same parameters."""
+    w, _, X = oracle_case("h2_imq3d_n262144", 3000, 8)
+    plan = hp.hmat_plan_create(X, admissibility=w.admissibility, leaf_size=w.leaf_size, eta=w.eta)
+    try:
+        W = rhs(w.n, 5, 41)
+        for kernel, param, tol in (("imq", 0.1, 1e-7), ("gaussian", 0.3, 1e-5), ("invdist", 0.0, 1e-6)):
+            h1 = hp.hmat_plan_build(plan, kernel, param, tol, 256, sample_seed=w.sample_seed)
+            h2 = hp.hmat_build(X, **_params(w, kernel=kernel, kernel_param=param, tol=tol, max_rank=256))
+            try:
+                s1, s2 = hp.hmat_structure(h1), hp.hmat_structure(h2)
+                for k in s1:
+                    assert np.array_equal(s1[k], s2[k]), (kernel, k)
+                assert np.array_equal(_eval(h1, W), _eval(h2, W)), kernel
+                KW = hm.dense_product(X, kernel, param, W)
+                assert hm.overall_error(_eval(h1, W), KW) <= max(100 * tol, 1e-12)
+            finally:
+                hp.hmat_free(h1)
+                hp.hmat_free(h2)
+    finally:
+        hp.hmat_plan_free(plan)
+
+
+def test_plan_rejects_bad_parameters():
+    w, _, X = oracle_case("hss_uniform3d_n2048", 1000, 1)
+    with pytest.raises(hp.HmatError):
+        hp.hmat_plan_create(X, admissibility=w.admissibility, leaf_size=1)
+    plan = hp.hmat_plan_create(X, admissibility=w.admissibility, leaf_size=w.leaf_size)
+    try:
+        for kernel, param, tol, rank in (("gaussian", 0.0, 1e-6, 64), ("imq", 0.1, -1.0, 64), ("imq", 0.1, 1e-6, 0)):
+            with pytest.raises(hp.HmatError) as ei:
+                hp.hmat_plan_build(plan, kernel, param, tol, rank)
+            assert ei.value.status == hp.HMAT_EINVAL
+    finally:
+        hp.hmat_plan_free(plan)

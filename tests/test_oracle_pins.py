@@ -101,6 +101,57 @@ def test_admissibility_golden_line():
     assert sorted(map(tuple, g["hss_far"])) == hss.far
 
 
+def test_tau_admissibility_golden_line():
+    g = _golden("admissibility_tau_line_16pts.json")
+    X = np.array(g["points"], dtype=float)
+    t = hm.build_cluster_tree(X, g["leaf_size"])
+    inter = hm.compute_interactions(t, X[t.perm], "tau", g["tau"])
+    assert sorted(map(tuple, g["near"])) == inter.near
+    assert sorted(map(tuple, g["far"])) == inter.far
+
+
+def test_two_means_golden_splits():
+    for case in _golden("two_means_splits.json")["cases"]:
+        X = np.array(case["points"], dtype=float)
+        t = hm.build_cluster_tree(X, case["leaf_size"], tree="two_means")
+        assert t.perm.tolist() == case["perm"], case["derivation"]
+        if "sizes" in case:
+            assert t.size.tolist() == case["sizes"]
+        if "kd_perm" in case:
+            assert hm.build_cluster_tree(X, case["leaf_size"]).perm.tolist() == case["kd_perm"]
+
+
+def _box_gap_and_diams(t, Xt, a, b):
+    """Bounding-box gap and diagonals of two nodes, by plain loops over points and coordinates."""
+    def box(x):
+        pts = [Xt[i] for i in range(t.begin[x], t.begin[x] + t.size[x])]
+        return ([min(p[k] for p in pts) for k in range(Xt.shape[1])], [max(p[k] for p in pts) for k in range(Xt.shape[1])])
+    (la, ha), (lb, hb) = box(a), box(b)
+    gap = math.sqrt(sum(max(0.0, lb[k] - ha[k], la[k] - hb[k]) ** 2 for k in range(Xt.shape[1])))
+    da = math.sqrt(sum((ha[k] - la[k]) ** 2 for k in range(Xt.shape[1])))
+    db = math.sqrt(sum((hb[k] - lb[k]) ** 2 for k in range(Xt.shape[1])))
+    return gap, da, db
+
+
+@pytest.mark.parametrize("tau", [3.0, 5.0, 10.0])
+def test_tau_far_pairs_admissible_and_minimal(tau):
+    """Every far pair meets tau * gap > diam_a + diam_b and its parent pair does not (the traversal
+    stops at the first admissible level), checked with plain loops."""
+    w = reduced(WORKLOADS["h2_invdist3d_n262144"], 700, q=1)
+    X = make_points(w)
+    t = hm.build_cluster_tree(X, 40)
+    Xt = X[t.perm]
+    inter = hm.compute_interactions(t, Xt, "tau", tau)
+    assert inter.far
+    for a, b in inter.far:
+        gap, da, db = _box_gap_and_diams(t, Xt, a, b)
+        assert tau * gap > da + db
+        pa, pb = (a - 1) // 2, (b - 1) // 2
+        if a > 0 and pa != pb:
+            gap, da, db = _box_gap_and_diams(t, Xt, pa, pb)
+            assert not tau * gap > da + db
+
+
 def _covering_counts(t, inter):
     """How many times each leaf pair is covered by a near pair or a far pair of ancestors."""
     fl, nl = t.first_leaf, t.n_leaves
@@ -122,15 +173,22 @@ def _is_desc(x, a, t):
     return x == a
 
 
-@pytest.mark.parametrize("mode,X", [
-    ("hss", uniform_points(1000, 3, 3)),
-    ("geometric", uniform_points(2048, 3, 4)),
-    ("geometric", uniform_points(1500, 2, 5)),
-    ("geometric", gmm_points(2048, 8, 10, 6)),
+@pytest.mark.parametrize("mode,X,tree,eta", [
+    ("hss", uniform_points(1000, 3, 3), "kd", 2.0),
+    ("geometric", uniform_points(2048, 3, 4), "kd", 2.0),
+    ("geometric", uniform_points(1500, 2, 5), "kd", 2.0),
+    ("geometric", gmm_points(2048, 8, 10, 6), "kd", 2.0),
+    ("geometric", gmm_points(2048, 8, 10, 6), "two_means", 2.0),
+    ("tau", uniform_points(2048, 3, 4), "kd", 3.0),
+    ("tau", gmm_points(1500, 8, 10, 7), "two_means", 5.0),
 ])
-def test_interactions_symmetric_and_covering(mode, X):
-    t = hm.build_cluster_tree(X, 32)
-    inter = hm.compute_interactions(t, X[t.perm], mode)
+def test_interactions_symmetric_and_covering(mode, X, tree, eta):
+    t = hm.build_cluster_tree(X, 32, tree=tree)
+    if tree == "two_means":                                   # a perfect, balanced tree of every point
+        assert sorted(t.perm.tolist()) == list(range(X.shape[0]))
+        for a in range(t.first_leaf):
+            assert t.size[2 * a + 1] == t.size[a] // 2 and t.begin[2 * a + 2] == t.begin[a] + t.size[a] // 2
+    inter = hm.compute_interactions(t, X[t.perm], mode, eta)
     assert set(inter.near) == {(j, i) for i, j in inter.near}
     assert set(inter.far) == {(b, a) for a, b in inter.far}
     for a, b in inter.far:
@@ -200,16 +258,19 @@ def test_hss_full_rank_reproduces_K():
     assert hm.overall_error(hm.evaluate(H, W), KW) <= 1e-13
 
 
-@pytest.mark.parametrize("base,n", [("hss_uniform3d_n2048", 2048), ("h2_imq3d_n262144", 4096),
-                                    ("h2_gmm8d_n65536", 4096), ("h2_invdist3d_n262144", 4096)])
-def test_error_is_order_tol(base, n):
-    w = reduced(WORKLOADS[base], n, q=8)
+@pytest.mark.parametrize("base,n,ov", [("hss_uniform3d_n2048", 2048, {}), ("h2_imq3d_n262144", 4096, {}),
+                                       ("h2_gmm8d_n65536", 4096, {}), ("h2_invdist3d_n262144", 4096, {}),
+                                       ("h2_gmm8d_n65536", 4096, {"tree": "two_means"}),
+                                       ("h2_imq3d_n262144", 4096, {"admissibility": "tau", "eta": 3.0})])
+def test_error_is_order_tol(base, n, ov):
+    w = reduced(WORKLOADS[base], n, q=8, **ov)
     X = make_points(w)
     W = normal_rhs(w.n, w.q, 5)
     KW = hm.dense_product(X, w.kernel, w.kernel_param, W)
     errs = []
     for tol in (1e-3, 1e-5, 1e-7):
-        H = hm.compress(X, w.leaf_size, w.admissibility, w.kernel, w.kernel_param, tol, 10 ** 6, eta=w.eta)
+        H = hm.compress(X, w.leaf_size, w.admissibility, w.kernel, w.kernel_param, tol, 10 ** 6, eta=w.eta,
+                        tree=w.tree)
         e = hm.overall_error(hm.evaluate(H, W), KW)
         assert e <= 100 * tol, (tol, e)
         errs.append(e)

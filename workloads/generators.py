@@ -43,8 +43,9 @@ class Workload:
     """Parameters of one HMatrix evaluation workload.
 
     ``admissibility`` is ``"hss"`` (every pair of siblings is far: weak
-    admissibility) or ``"geometric"`` (boxes far when the distance of their
-    centroids exceeds ``eta`` times the larger of their radii).
+    admissibility), ``"geometric"`` (boxes far when the distance of their
+    centroids exceeds ``eta`` times the larger of their radii) or ``"tau"``
+    (``eta`` * gap between bounding boxes > sum of their diagonals).
     ``kernel`` is ``"gaussian"`` (exp(-r^2 / (2 h^2)), param = h), ``"imq"``
     (1 / sqrt(r^2 + c^2), param = c) or ``"invdist"`` (1 / r, 0 for coincident
     points; param unused).
@@ -65,6 +66,7 @@ class Workload:
     sample_seed: int = 2
     eta: float = 2.0
     gmm_components: int = 10
+    tree: str = "kd"       # "kd" or "two_means"
 
 
 def make_points(w: Workload) -> np.ndarray:
