@@ -278,7 +278,7 @@ def run_gpu(args, dist: Dist) -> None:
         "gflops": round(total_flops / (ms / 1e3) / 1e9, 2),
         "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
         "roofline": {
-            "bound": "alu", "kernel": "k_fp64_grouped_gemm (near field)",
+            "bound": "alu", "kernel": "k_grouped_gemm<double> (near field, tuned column tile)",
             "launches_per_eval": near_launches // args.steps,
             "achieved": round(achieved_tflops, 4), "peak": round(peak_gflops / 1e3, 4), "unit": "TFLOP/s",
             "frac": round(achieved_tflops / (peak_gflops / 1e3), 4),
@@ -357,7 +357,7 @@ def run_mixed(args, dev, W, Y64, q, info, stream, dist) -> dict:
                 "unit": "GB/s"}
     roof.update({"frac": round(roof["achieved"] / roof["peak"], 4),
                  "traffic": measured_traffic("mixed_near", nv), "algorithmic_bytes": alg_bytes,
-                 "kernel": "k_near_tc (tcgen05 near field)", "peak_source": peaks["source"],
+                 "kernel": "k_tc<0> (tcgen05 near field)", "peak_source": peaks["source"],
                  "t_tensor_ms": round(t_tensor, 4), "t_hbm_ms": round(t_hbm, 4)})
     return {"value": round(dist.world * q / (ms / 1e3), 3), "unit": "cols/s", "ms_per_step": round(ms, 4),
             "error_vs_fp64": err, "dtype": "f16 hi+lo split, f32 accumulate",
