@@ -373,14 +373,16 @@ def run_inspector_reuse(w, X) -> dict:
     t0 = time.perf_counter()
     plan = hp.hmat_plan_create(X, admissibility=w.admissibility, leaf_size=w.leaf_size, eta=w.eta)
     t_plan = time.perf_counter() - t0
-    out = {"plan_s": round(t_plan, 3), "recompress_s": {}}
+    out = {"plan_s": round(t_plan, 3), "recompress_s": {}, "recompress_gpu_id_s": {}}
     try:
         for tol in (w.tol, 10 * w.tol):
-            t0 = time.perf_counter()
-            h = hp.hmat_plan_build(plan, w.kernel, w.kernel_param, tol, w.max_rank, sample_seed=w.sample_seed)
-            out["recompress_s"][f"{tol:g}"] = round(time.perf_counter() - t0, 3)
-            out.setdefault("sum_rank", {})[f"{tol:g}"] = hp.hmat_info(h)["sum_rank"]
-            hp.hmat_free(h)
+            for key, flags in (("recompress_s", 0), ("recompress_gpu_id_s", hp.HMAT_BUILD_ID_GPU)):
+                t0 = time.perf_counter()
+                h = hp.hmat_plan_build(plan, w.kernel, w.kernel_param, tol, w.max_rank, sample_seed=w.sample_seed,
+                                       flags=flags)
+                out[key][f"{tol:g}"] = round(time.perf_counter() - t0, 3)
+                out.setdefault("sum_rank", {})[f"{tol:g} {key}"] = hp.hmat_info(h)["sum_rank"]
+                hp.hmat_free(h)
     finally:
         hp.hmat_plan_free(plan)
     return out
@@ -429,6 +431,12 @@ def run_precision(args, dist) -> dict:
     out["mixed_over_fp64"] = round(out["mixed"]["value"] / out["fp64"]["value"], 2)
     out["autotune"] = tunes
     dev.close()
+    # the same compression with the row IDs on the GPU (one CTA per node of a level)
+    t0 = time.perf_counter()
+    h = hp.hmat_build(make_points(w), flags=hp.HMAT_BUILD_ID_GPU, **build_params(w))
+    out["inspector_gpu_id_s"] = round(time.perf_counter() - t0, 2)
+    out["sum_rank_gpu_id"] = hp.hmat_info(h)["sum_rank"]
+    hp.hmat_free(h)
     return out
 
 

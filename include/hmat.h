@@ -208,6 +208,11 @@ hmat_status hmat_structure(hmat_t h, int64_t* perm, int32_t* rank, int64_t* near
                                        FP32 accumulation drained per block into compensated sums),
                                        far field in FP32; needs a handle loaded with HMAT_LOAD_MIXED */
 
+/* Build flag (hmat_build, hmat_plan_build): the nested row IDs run on the GPU, one CTA
+   per node of a tree level (same algorithm as on the host; sums in another order, so a
+   pivot may differ where two candidates are within rounding of each other). */
+#define HMAT_BUILD_ID_GPU 2
+
 /* Load flags (hmat_load, hmat_build). */
 #define HMAT_LOAD_MIXED 1           /* also keep the tensor-core copy of the near blocks (FP16 hi/lo,
                                        4 bytes per value) and an FP32 copy of the bases and coupling

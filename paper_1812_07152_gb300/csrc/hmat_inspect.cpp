@@ -414,10 +414,92 @@ extern "C" hmat_status hmat_plan_free(hmat_plan_t plan) {
 
 // Inspector-p2: the nested row IDs for this kernel and accuracy, then the load (near
 // and coupling blocks evaluated on the GPU).
+namespace {
+
+// The row IDs of every node of one level on the GPU; fills skel, basis and rank of
+// those nodes from the device's pivots and T = R_11^{-1} R_12.
+hmat_status row_ids_gpu(const hmat_plan& pl, const hmat_compress_params& c, const double* d_pts,
+                        const std::vector<int64_t>& nodes, const std::vector<std::vector<int64_t>>& rows_of,
+                        const std::vector<std::vector<int64_t>>& cols_of, std::vector<std::vector<int64_t>>* skel,
+                        std::vector<std::vector<double>>* basis, std::vector<int32_t>* rank) {
+  const int64_t nj = (int64_t)nodes.size();
+  if (nj == 0) return HMAT_OK;
+  std::vector<IdJob> jobs(nj);
+  std::vector<int64_t> ids;
+  int64_t a_total = 0, piv_total = 0, max_rows = 1;
+  for (int64_t t = 0; t < nj; ++t) {
+    const auto& r = rows_of[t];
+    const auto& cc = cols_of[t];
+    jobs[t] = IdJob{a_total, (int64_t)ids.size(), (int64_t)(ids.size() + r.size()), piv_total, (int32_t)r.size(),
+                    (int32_t)cc.size()};
+    ids.insert(ids.end(), r.begin(), r.end());
+    ids.insert(ids.end(), cc.begin(), cc.end());
+    a_total += (int64_t)r.size() * (int64_t)cc.size();
+    piv_total += (int64_t)r.size();
+    max_rows = std::max<int64_t>(max_rows, (int64_t)r.size());
+  }
+  IdJob* d_jobs = nullptr;
+  int64_t* d_ids = nullptr;
+  double* d_work = nullptr;
+  int32_t* d_piv = nullptr;
+  int32_t* d_rank = nullptr;
+  auto release = [&]() {
+    cudaFree(d_jobs);
+    cudaFree(d_ids);
+    cudaFree(d_work);
+    cudaFree(d_piv);
+    cudaFree(d_rank);
+  };
+  cudaError_t e = cudaMalloc((void**)&d_jobs, sizeof(IdJob) * nj);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d_ids, sizeof(int64_t) * std::max<size_t>(ids.size(), 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d_work, sizeof(double) * std::max<int64_t>(a_total, 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d_piv, sizeof(int32_t) * std::max<int64_t>(piv_total, 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d_rank, sizeof(int32_t) * nj);
+  if (e == cudaSuccess) e = cudaMemcpy(d_jobs, jobs.data(), sizeof(IdJob) * nj, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !ids.empty())
+    e = cudaMemcpy(d_ids, ids.data(), sizeof(int64_t) * ids.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = launch_row_id(d_jobs, nj, max_rows, d_pts, pl.d, d_ids, c.kernel, c.kernel_param, c.tol, c.max_rank, d_work,
+                      d_piv, d_rank, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  std::vector<int32_t> rk(nj), piv(std::max<int64_t>(piv_total, 1));
+  if (e == cudaSuccess) e = cudaMemcpy(rk.data(), d_rank, sizeof(int32_t) * nj, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(piv.data(), d_piv, sizeof(int32_t) * piv.size(), cudaMemcpyDeviceToHost);
+  std::vector<double> T;
+  for (int64_t t = 0; t < nj && e == cudaSuccess; ++t) {
+    const int64_t a = nodes[t], n = jobs[t].n_rows, m = jobs[t].n_cols, k = rk[t];
+    const int32_t* pv = piv.data() + jobs[t].piv_off;
+    // T (k x (n - k)): rows 0..k-1 of the columns k..n-1 of this node's A
+    T.assign((size_t)(k * (n - k)), 0.0);
+    if (k > 0 && n > k)
+      e = cudaMemcpy2D(T.data(), (size_t)k * sizeof(double), d_work + jobs[t].a_off + k * m, (size_t)m * sizeof(double),
+                       (size_t)k * sizeof(double), (size_t)(n - k), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) break;
+    auto& P = (*basis)[a];
+    P.assign((size_t)(n * k), 0.0);
+    (*skel)[a].resize(k);
+    for (int64_t j = 0; j < k; ++j) {
+      P[pv[j] * k + j] = 1.0;
+      (*skel)[a][j] = rows_of[t][pv[j]];
+    }
+    for (int64_t cix = 0; cix < n - k; ++cix)
+      for (int64_t j = 0; j < k; ++j) P[pv[k + cix] * k + j] = T[cix * k + j];
+    (*rank)[a] = (int32_t)k;
+  }
+  release();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  return HMAT_OK;
+}
+
+}  // namespace
+
 extern "C" hmat_status hmat_plan_build(hmat_plan_t pl, const hmat_compress_params* c, int flags, hmat_t* out) {
   if (!out) return HMAT_EINVAL;
   *out = nullptr;
-  if (flags & ~HMAT_LOAD_MIXED) return HMAT_EUNSUPPORTED;
+  if (flags & ~(HMAT_LOAD_MIXED | HMAT_BUILD_ID_GPU)) return HMAT_EUNSUPPORTED;
   if (!pl || !valid_compress(c)) return HMAT_EINVAL;
   const Tree& t = pl->t;
   const int64_t n = pl->n;
@@ -429,8 +511,20 @@ extern "C" hmat_status hmat_plan_build(hmat_plan_t pl, const hmat_compress_param
   std::vector<std::vector<int64_t>> skel(t.n_nodes);
   std::vector<std::vector<double>> basis(t.n_nodes);
   std::vector<int32_t> rank(t.n_nodes, 0);
+  const bool on_gpu = (flags & HMAT_BUILD_ID_GPU) != 0;
+  double* d_pts = nullptr;
+  if (on_gpu) {
+    cudaError_t e = cudaMalloc((void**)&d_pts, sizeof(double) * std::max<size_t>(Xt.size(), 1));
+    if (e == cudaSuccess) e = cudaMemcpy(d_pts, Xt.data(), sizeof(double) * Xt.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d_pts);
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+  }
   for (int level = t.levels; level >= 1; --level) {
     const int64_t lo = ((int64_t)1 << level) - 1, cnt = (int64_t)1 << level;
+    std::vector<std::vector<int64_t>> rows_of(on_gpu ? cnt : 0), cols_of(on_gpu ? cnt : 0);
     parallel_for(cnt, threads, [&](int64_t k) {
       const int64_t a = lo + k;
       if (!pl->needs[a]) return;
@@ -458,10 +552,31 @@ extern "C" hmat_status hmat_plan_build(hmat_plan_t pl, const hmat_compress_param
         cols.resize(n_sample);
         std::sort(cols.begin(), cols.end());
       }
+      if (on_gpu) {
+        rows_of[k] = std::move(rows);
+        cols_of[k] = std::move(cols);
+        return;
+      }
       row_id(Xt, d, c->kernel, c->kernel_param, rows, cols, c->tol, c->max_rank, &skel[a], &basis[a]);
       rank[a] = (int32_t)skel[a].size();
     });
+    if (on_gpu) {
+      std::vector<int64_t> nodes;
+      std::vector<std::vector<int64_t>> r2, c2;
+      for (int64_t k = 0; k < cnt; ++k)
+        if (pl->needs[lo + k]) {
+          nodes.push_back(lo + k);
+          r2.push_back(std::move(rows_of[k]));
+          c2.push_back(std::move(cols_of[k]));
+        }
+      const hmat_status st = row_ids_gpu(*pl, *c, d_pts, nodes, r2, c2, &skel, &basis, &rank);
+      if (st != HMAT_OK) {
+        cudaFree(d_pts);
+        return st;
+      }
+    }
   }
+  cudaFree(d_pts);
 
   // assemble the hmat_desc structure (blocks are evaluated on the device)
   std::vector<int64_t> near_ptr(t.first_leaf + 2, 0), far_ptr(t.n_nodes + 1, 0);
@@ -493,13 +608,13 @@ extern "C" hmat_status hmat_plan_build(hmat_plan_t pl, const hmat_compress_param
   desc.near = nullptr;
   desc.perm = t.perm.data();
   DeviceBlockSource src{Xt.data(), d, skel_points.data(), c->kernel, c->kernel_param};
-  return load_impl(&desc, &src, flags, out);
+  return load_impl(&desc, &src, flags & HMAT_LOAD_MIXED, out);
 }
 
 extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t* out) {
   if (!out) return HMAT_EINVAL;
   *out = nullptr;
-  if (flags & ~HMAT_LOAD_MIXED) return HMAT_EUNSUPPORTED;
+  if (flags & ~(HMAT_LOAD_MIXED | HMAT_BUILD_ID_GPU)) return HMAT_EUNSUPPORTED;
   if (!p) return HMAT_EINVAL;
   const hmat_compress_params c{p->kernel, p->kernel_param, p->tol, p->max_rank, p->exact_columns, p->sample_seed};
   if (!valid_compress(&c)) return HMAT_EINVAL;

@@ -227,6 +227,21 @@ struct BlockJob {
   int32_t col_skel;
 };
 
+// One node's row ID on the device (hmat_id.cu): rows and columns are point indices
+// (tree order) at ids[rows_off ..] and ids[cols_off ..]; A (n_cols x n_rows,
+// column-major) at work[a_off ..]; pivots at piv[piv_off ..].
+struct IdJob {
+  int64_t a_off;
+  int64_t rows_off;
+  int64_t cols_off;
+  int64_t piv_off;
+  int32_t n_rows;
+  int32_t n_cols;
+};
+cudaError_t launch_row_id(const IdJob* jobs, int64_t n_jobs, int64_t max_rows, const double* pts, int d,
+                          const int64_t* ids, int kernel, double param, double tol, int max_rank, double* work,
+                          int32_t* piv, int32_t* rank, cudaStream_t stream);
+
 // Source of the near and coupling blocks when they are evaluated on the device.
 struct DeviceBlockSource {
   const double* points_tree;   // host, n_points x dim, tree order

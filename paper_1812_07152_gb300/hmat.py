@@ -63,6 +63,7 @@ HMAT_ADM_HSS = 0
 HMAT_ADM_GEOMETRIC = 1
 HMAT_ADM_NONE = 2
 HMAT_ADM_TAU = 3
+HMAT_BUILD_ID_GPU = 2
 HMAT_TREE_KD = 0
 HMAT_TREE_TWO_MEANS = 1
 

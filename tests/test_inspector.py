@@ -156,3 +156,50 @@ def test_plan_rejects_bad_parameters():
             assert ei.value.status == hp.HMAT_EINVAL
     finally:
         hp.hmat_plan_free(plan)
+
+
+@pytest.mark.parametrize("base,n,ov", [
+    ("hss_uniform3d_n2048", 2048, ()),
+    ("h2_imq3d_n262144", 3000, ()),
+    ("h2_gmm8d_n65536", 4096, ()),
+    ("h2_invdist3d_n262144", 3000, ()),
+    ("h2_imq3d_n262144", 5000, (("leaf_size", 256),)),
+])
+def test_gpu_row_ids_match_host_row_ids(base, n, ov):
+    """HMAT_BUILD_ID_GPU runs the same pivoted QR per node on the GPU (sums in another order):
+    the same ranks and skeletons except where two pivot candidates tie within rounding, and
+    the same accuracy against the dense product."""
+    w, H, X = oracle_case(base, n, 8, **dict(ov))
+    plan = hp.hmat_plan_create(X, admissibility=w.admissibility, leaf_size=w.leaf_size, eta=w.eta)
+    try:
+        args = (w.kernel, w.kernel_param, w.tol, w.max_rank)
+        h_host = hp.hmat_plan_build(plan, *args, sample_seed=w.sample_seed)
+        h_gpu = hp.hmat_plan_build(plan, *args, sample_seed=w.sample_seed, flags=hp.HMAT_BUILD_ID_GPU)
+        try:
+            r_host = hp.hmat_structure(h_host)["rank"].astype(int)
+            r_gpu = hp.hmat_structure(h_gpu)["rank"].astype(int)
+            assert np.abs(r_host - r_gpu).max() <= 1
+            assert np.mean(r_host == r_gpu) >= 0.95
+            W = rhs(w.n, 8, 51)
+            KW = hm.dense_product(X, w.kernel, w.kernel_param, W)
+            e_host = hm.overall_error(_eval(h_host, W), KW)
+            e_gpu = hm.overall_error(_eval(h_gpu, W), KW)
+            assert e_gpu <= 1.5 * e_host + 1e-13, (e_gpu, e_host)
+            e_orc = hm.overall_error(hm.evaluate(H, W), KW)
+            assert e_gpu <= 3 * e_orc + 1e-12, (e_gpu, e_orc)
+        finally:
+            hp.hmat_free(h_host)
+            hp.hmat_free(h_gpu)
+    finally:
+        hp.hmat_plan_free(plan)
+
+
+def test_gpu_row_ids_full_rank_is_exact():
+    w, _, X = oracle_case("hss_uniform3d_n2048", 1024, 4)
+    h = hp.hmat_build(X, **_params(w, tol=0.0, max_rank=10 ** 6), flags=hp.HMAT_BUILD_ID_GPU)
+    try:
+        W = rhs(w.n, 4, 52)
+        KW = hm.dense_product(X, w.kernel, w.kernel_param, W)
+        assert hm.overall_error(_eval(h, W), KW) <= 1e-13
+    finally:
+        hp.hmat_free(h)
