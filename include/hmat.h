@@ -101,7 +101,12 @@ typedef struct {
  * HMAT_ADM_NONE - nothing is far: every block is kept dense;
  * HMAT_ADM_TAU - the paper's tau * dist(a, b) > diam(a) + diam(b) with tau = eta,
  *   on bounding boxes: dist = the Euclidean gap between the boxes of a and b, diam
- *   = a box's diagonal.
+ *   = a box's diagonal;
+ * HMAT_ADM_BUDGET - GOFMM's budget (the paper's H2-b, Section 4.1), budget = eta in
+ *   [0, 1]: the 32 nearest neighbours of every point vote for their leaves, a leaf
+ *   is near itself and the floor(budget * leaves) most-voted leaves (ties by leaf
+ *   index), symmetrised, and a node pair is far when no near leaf pair lies below it
+ *   (budget 0 gives HSS). The neighbours are found by brute force (n^2 distances).
  *
  * Cluster trees (Section 3.1, tree construction): HMAT_TREE_KD splits a node at the
  * median of its widest bounding-box dimension; HMAT_TREE_TWO_MEANS (the paper's
@@ -116,6 +121,7 @@ typedef struct {
 #define HMAT_ADM_GEOMETRIC 1
 #define HMAT_ADM_NONE 2
 #define HMAT_ADM_TAU 3
+#define HMAT_ADM_BUDGET 4
 #define HMAT_TREE_KD 0
 #define HMAT_TREE_TWO_MEANS 1
 

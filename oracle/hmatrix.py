@@ -33,6 +33,9 @@ builder only through the fixture itself, never through shared code):
   ordered by their projection onto q - p, split at the median;
 * the paper's tau * dist(a, b) > diam(a) + diam(b) (Section 2.1) on bounding
   boxes: dist = the gap between the boxes, diam = the box diagonal;
+* GOFMM's budget (the paper's H2-b, Section 4.1): 32 nearest neighbours per point
+  vote for leaves; a leaf keeps floor(budget * leaves) most-voted leaves as near;
+  a pair is far when no near leaf pair lies below it;
 * HSS: every pair of distinct siblings is far, every leaf is near itself only;
 * ID: column-pivoted QR of K(R, C)^T, rank = #{j : |R_jj| > tol * |R_11|}
   capped at max_rank, columns C = every point whose interaction with the node
@@ -229,6 +232,53 @@ def node_boxes(tree: ClusterTree, Xt: np.ndarray) -> Tuple[np.ndarray, np.ndarra
     return lo, hi
 
 
+BUDGET_NEIGHBOURS = 32
+
+
+def knn_tree_order(Xt: np.ndarray, k: int) -> np.ndarray:
+    """Indices (tree order) of the k nearest other points of every point, by brute force:
+    squared distances summed over the coordinates in order, ties by index."""
+    n = Xt.shape[0]
+    k = min(k, n - 1)
+    out = np.zeros((n, max(k, 0)), dtype=np.int64)
+    if k <= 0:
+        return out
+    for i in range(n):
+        d2 = _sq_dist_seq(Xt, Xt[i])
+        d2[i] = np.inf
+        order = np.lexsort((np.arange(n), d2))
+        out[i] = order[:k]
+    return out
+
+
+def budget_near_leaves(tree: ClusterTree, Xt: np.ndarray, budget: float) -> set:
+    """Near leaf pairs of GOFMM's budget admissibility (used by the paper for its H2-b
+    structure, Section 4.1; the paper gives no algorithm): every point votes for the leaves
+    of its BUDGET_NEIGHBOURS nearest neighbours; a leaf is near itself and the
+    floor(budget * leaves) leaves with the most votes from its points (ties by leaf index);
+    the relation is made symmetric."""
+    nl, fl = tree.n_leaves, tree.first_leaf
+    leaf_of = np.zeros(Xt.shape[0], dtype=np.int64)
+    for i in range(nl):
+        leaf_of[tree.begin[fl + i]:tree.begin[fl + i] + tree.size[fl + i]] = i
+    nbr = knn_tree_order(Xt, BUDGET_NEIGHBOURS)
+    keep = int(math.floor(budget * nl))
+    near = set()
+    for i in range(nl):
+        near.add((i, i))
+        pts = range(tree.begin[fl + i], tree.begin[fl + i] + tree.size[fl + i])
+        votes = np.zeros(nl, dtype=np.int64)
+        for p_ in pts:
+            for q_ in nbr[p_]:
+                votes[leaf_of[q_]] += 1
+        votes[i] = 0
+        cand = [j for j in np.lexsort((np.arange(nl), -votes)) if votes[j] > 0][:keep]
+        for j in cand:
+            near.add((i, int(j)))
+            near.add((int(j), i))
+    return near
+
+
 def compute_interactions(tree: ClusterTree, Xt: np.ndarray, mode: str, eta: float = 2.0) -> Interactions:
     """Dual-tree traversal from (root, root). A pair of distinct nodes that is
     admissible is far; a pair of leaves that is not is near; otherwise the four
@@ -236,10 +286,22 @@ def compute_interactions(tree: ClusterTree, Xt: np.ndarray, mode: str, eta: floa
     admissible), ``"geometric"`` (centroid distance > eta * max radius), ``"tau"``
     (the paper's tau * dist(a, b) > diam(a) + diam(b) of Section 2.1, with tau =
     ``eta``, read on bounding boxes: dist = the Euclidean gap between the two boxes,
-    diam = a box's diagonal; sums over the coordinates in order) or ``"none"``
-    (nothing is admissible: every leaf pair is near)."""
+    diam = a box's diagonal; sums over the coordinates in order), ``"budget"``
+    (GOFMM's budget, ``eta`` = the budget: a pair is far when no leaf pair below it is
+    in ``budget_near_leaves``) or ``"none"`` (nothing is admissible: every leaf pair
+    is near)."""
     if mode == "geometric":
         cent, rad = node_geometry(tree, Xt)
+    if mode == "budget":
+        fl = tree.first_leaf
+        near_below = set()          # (a, b) with a near leaf pair below, on every level
+        for i, j in budget_near_leaves(tree, Xt, eta):
+            a, b = fl + i, fl + j
+            while True:
+                near_below.add((a, b))
+                if a == 0:
+                    break
+                a, b = (a - 1) // 2, (b - 1) // 2
     if mode == "tau":
         lo, hi = node_boxes(tree, Xt)
         diam = np.zeros(tree.n_nodes)
@@ -258,6 +320,8 @@ def compute_interactions(tree: ClusterTree, Xt: np.ndarray, mode: str, eta: floa
         if mode == "geometric":
             dist = float(np.sqrt(((cent[a] - cent[b]) ** 2).sum()))
             return dist > eta * max(rad[a], rad[b])
+        if mode == "budget":
+            return (a, b) not in near_below
         if mode == "tau":
             g2 = 0.0
             for k in range(Xt.shape[1]):

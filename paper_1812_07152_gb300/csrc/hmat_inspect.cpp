@@ -187,8 +187,73 @@ void geometry(const Tree& t, const double* Xt, int d, int threads, std::vector<d
   });
 }
 
+constexpr int kBudgetNeighbours = 32;
+
+// GOFMM's budget admissibility (the paper's H2-b, Section 4.1; no algorithm given): every
+// point votes for the leaves of its kBudgetNeighbours nearest other points (squared
+// distances summed over the coordinates in order, ties by index); a leaf is near itself
+// and the floor(budget * leaves) leaves with the most votes from its points (ties by
+// leaf index), symmetrised. Returns, per level, which node pairs have a near leaf pair
+// below them (row-major over the level's nodes).
+std::vector<std::vector<uint8_t>> budget_near_below(const Tree& t, const double* Xt, int d, double budget,
+                                                    int threads) {
+  const int64_t n = t.size[0], nl = (int64_t)1 << t.levels, fl = t.first_leaf;
+  const int64_t kk = std::min<int64_t>(kBudgetNeighbours, n - 1);
+  std::vector<int64_t> nbr((size_t)std::max<int64_t>(n * kk, 1));
+  parallel_for(n, threads, [&](int64_t i) {
+    std::vector<std::pair<double, int64_t>> best;  // max-heap of the kk best (distance, index)
+    best.reserve((size_t)kk + 1);
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      const std::pair<double, int64_t> c{sq_dist(Xt + i * d, Xt + j * d, d), j};
+      if ((int64_t)best.size() < kk) {
+        best.push_back(c);
+        std::push_heap(best.begin(), best.end());
+      } else if (kk > 0 && c < best.front()) {
+        std::pop_heap(best.begin(), best.end());
+        best.back() = c;
+        std::push_heap(best.begin(), best.end());
+      }
+    }
+    std::sort_heap(best.begin(), best.end());
+    for (int64_t r = 0; r < kk; ++r) nbr[i * kk + r] = best[r].second;
+  });
+  std::vector<int64_t> leaf_of(n);
+  for (int64_t i = 0; i < nl; ++i)
+    for (int64_t p = t.begin[fl + i]; p < t.begin[fl + i] + t.size[fl + i]; ++p) leaf_of[p] = i;
+  const int64_t keep = (int64_t)std::floor(budget * (double)nl);
+  std::vector<uint8_t> near((size_t)(nl * nl), 0);
+  for (int64_t i = 0; i < nl; ++i) {
+    near[i * nl + i] = 1;
+    std::vector<int64_t> votes(nl, 0);
+    for (int64_t p = t.begin[fl + i]; p < t.begin[fl + i] + t.size[fl + i]; ++p)
+      for (int64_t r = 0; r < kk; ++r) votes[leaf_of[nbr[p * kk + r]]]++;
+    votes[i] = 0;
+    std::vector<int64_t> cand;
+    for (int64_t j = 0; j < nl; ++j)
+      if (votes[j] > 0) cand.push_back(j);
+    std::stable_sort(cand.begin(), cand.end(), [&](int64_t x, int64_t y) { return votes[x] > votes[y]; });
+    for (int64_t c = 0; c < (int64_t)cand.size() && c < keep; ++c) {
+      near[i * nl + cand[c]] = 1;
+      near[cand[c] * nl + i] = 1;
+    }
+  }
+  std::vector<std::vector<uint8_t>> below(t.levels + 1);
+  below[t.levels] = near;
+  for (int level = t.levels - 1; level >= 0; --level) {
+    const int64_t w = (int64_t)1 << level, wc = 2 * w;
+    below[level].assign((size_t)(w * w), 0);
+    for (int64_t a = 0; a < wc; ++a)
+      for (int64_t b = 0; b < wc; ++b)
+        if (below[level + 1][a * wc + b]) below[level][(a / 2) * w + b / 2] = 1;
+  }
+  return below;
+}
+
 void interactions(const Tree& t, const double* Xt, int d, int adm, double eta, int threads,
                   std::vector<std::pair<int64_t, int64_t>>* near, std::vector<std::pair<int64_t, int64_t>>* far) {
+  std::vector<std::vector<uint8_t>> below;
+  if (adm == HMAT_ADM_BUDGET) below = budget_near_below(t, Xt, d, eta, threads);
   std::vector<double> cent, rad, lo, hi, diam;
   if (adm == HMAT_ADM_GEOMETRIC) geometry(t, Xt, d, threads, &cent, &rad);
   if (adm == HMAT_ADM_TAU) {  // bounding boxes and their diagonals
@@ -218,6 +283,12 @@ void interactions(const Tree& t, const double* Xt, int d, int adm, double eta, i
   auto admissible = [&](int64_t a, int64_t b) {
     if (a == b || adm == HMAT_ADM_NONE) return false;
     if (adm == HMAT_ADM_HSS) return true;
+    if (adm == HMAT_ADM_BUDGET) {  // far when no near leaf pair lies below the pair
+      int l = 0;
+      while (((int64_t)2 << l) - 1 <= a) ++l;
+      const int64_t base = ((int64_t)1 << l) - 1, w = (int64_t)1 << l;
+      return below[l][(a - base) * w + (b - base)] == 0;
+    }
     if (adm == HMAT_ADM_TAU) {  // tau * dist(a, b) > diam(a) + diam(b), dist = the gap between the boxes
       double g2 = 0.0;
       for (int j = 0; j < d; ++j) {
@@ -381,8 +452,9 @@ extern "C" hmat_status hmat_plan_create(const hmat_plan_params* p, hmat_plan_t* 
   *out = nullptr;
   if (!p || p->n_points < 1 || p->dim < 1 || p->dim > 64 || !p->points || p->leaf_size < 2 ||
       (p->admissibility != HMAT_ADM_HSS && p->admissibility != HMAT_ADM_GEOMETRIC &&
-       p->admissibility != HMAT_ADM_NONE && p->admissibility != HMAT_ADM_TAU) ||
+       p->admissibility != HMAT_ADM_NONE && p->admissibility != HMAT_ADM_TAU && p->admissibility != HMAT_ADM_BUDGET) ||
       ((p->admissibility == HMAT_ADM_GEOMETRIC || p->admissibility == HMAT_ADM_TAU) && !(p->eta > 0.0)) ||
+      (p->admissibility == HMAT_ADM_BUDGET && !(p->eta >= 0.0 && p->eta <= 1.0)) ||
       (p->tree != HMAT_TREE_KD && p->tree != HMAT_TREE_TWO_MEANS))
     return HMAT_EINVAL;
   const int64_t n = p->n_points;

@@ -63,12 +63,14 @@ HMAT_ADM_HSS = 0
 HMAT_ADM_GEOMETRIC = 1
 HMAT_ADM_NONE = 2
 HMAT_ADM_TAU = 3
+HMAT_ADM_BUDGET = 4
 HMAT_BUILD_ID_GPU = 2
 HMAT_TREE_KD = 0
 HMAT_TREE_TWO_MEANS = 1
 
 _KERNELS = {"gaussian": HMAT_KERNEL_GAUSSIAN, "imq": HMAT_KERNEL_IMQ, "invdist": HMAT_KERNEL_INVDIST}
-_ADMISSIBILITY = {"hss": HMAT_ADM_HSS, "geometric": HMAT_ADM_GEOMETRIC, "none": HMAT_ADM_NONE, "tau": HMAT_ADM_TAU}
+_ADMISSIBILITY = {"hss": HMAT_ADM_HSS, "geometric": HMAT_ADM_GEOMETRIC, "none": HMAT_ADM_NONE, "tau": HMAT_ADM_TAU,
+                  "budget": HMAT_ADM_BUDGET}
 _TREES = {"kd": HMAT_TREE_KD, "two_means": HMAT_TREE_TWO_MEANS}
 
 

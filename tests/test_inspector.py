@@ -43,6 +43,8 @@ def _eval(h, W):
     ("h2_gmm8d_n65536", 4096, (("tree", "two_means"),)),                      # the paper's tree for d > 3
     ("h2_imq3d_n262144", 3000, (("admissibility", "tau"), ("eta", 3.0))),     # the paper's tau condition
     ("h2_gmm8d_n65536", 3000, (("tree", "two_means"), ("admissibility", "tau"), ("eta", 5.0))),
+    ("h2_gmm8d_n65536", 2048, (("admissibility", "budget"), ("eta", 0.03))),     # the paper's H2-b
+    ("h2_imq3d_n262144", 3000, (("admissibility", "budget"), ("eta", 0.1))),
 ])
 def test_structure_identical_and_accuracy_comparable(base, n, ov):
     w, H, X = oracle_case(base, n, 8, **dict(ov))

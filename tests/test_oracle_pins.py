@@ -110,6 +110,30 @@ def test_tau_admissibility_golden_line():
     assert sorted(map(tuple, g["far"])) == inter.far
 
 
+def test_budget_admissibility_golden_line():
+    g = _golden("admissibility_budget_line_16pts.json")
+    X = np.array(g["points"], dtype=float)
+    t = hm.build_cluster_tree(X, g["leaf_size"])
+    inter = hm.compute_interactions(t, X[t.perm], "budget", g["budget"])
+    assert sorted(map(tuple, g["near"])) == inter.near
+    assert sorted(map(tuple, g["far"])) == inter.far
+
+
+def test_budget_zero_is_hss():
+    """Section 4.1: budget 0 gives the HSS structure."""
+    X = uniform_points(1000, 3, 13)
+    t = hm.build_cluster_tree(X, 32)
+    b = hm.compute_interactions(t, X[t.perm], "budget", 0.0)
+    h = hm.compute_interactions(t, X[t.perm], "hss")
+    assert b.near == h.near and b.far == h.far
+
+
+def test_knn_brute_force_small():
+    X = np.array([[0.0], [1.0], [3.0], [3.5], [10.0]])
+    nbr = hm.knn_tree_order(X, 2)
+    assert nbr.tolist() == [[1, 2], [0, 2], [3, 1], [2, 1], [3, 2]]
+
+
 def test_two_means_golden_splits():
     for case in _golden("two_means_splits.json")["cases"]:
         X = np.array(case["points"], dtype=float)
@@ -181,6 +205,8 @@ def _is_desc(x, a, t):
     ("geometric", gmm_points(2048, 8, 10, 6), "two_means", 2.0),
     ("tau", uniform_points(2048, 3, 4), "kd", 3.0),
     ("tau", gmm_points(1500, 8, 10, 7), "two_means", 5.0),
+    ("budget", uniform_points(1024, 3, 8), "kd", 0.1),
+    ("budget", gmm_points(1024, 8, 10, 9), "two_means", 0.05),
 ])
 def test_interactions_symmetric_and_covering(mode, X, tree, eta):
     t = hm.build_cluster_tree(X, 32, tree=tree)
@@ -261,7 +287,8 @@ def test_hss_full_rank_reproduces_K():
 @pytest.mark.parametrize("base,n,ov", [("hss_uniform3d_n2048", 2048, {}), ("h2_imq3d_n262144", 4096, {}),
                                        ("h2_gmm8d_n65536", 4096, {}), ("h2_invdist3d_n262144", 4096, {}),
                                        ("h2_gmm8d_n65536", 4096, {"tree": "two_means"}),
-                                       ("h2_imq3d_n262144", 4096, {"admissibility": "tau", "eta": 3.0})])
+                                       ("h2_imq3d_n262144", 4096, {"admissibility": "tau", "eta": 3.0}),
+                                       ("h2_gmm8d_n65536", 2048, {"admissibility": "budget", "eta": 0.03})])
 def test_error_is_order_tol(base, n, ov):
     w = reduced(WORKLOADS[base], n, q=8, **ov)
     X = make_points(w)
