@@ -232,13 +232,20 @@ def run_gpu(args, dist: Dist) -> None:
 
     # end to end: host W -> device, evaluate, device Y -> host, every step (pinned host buffers)
     Y_host = torch.empty_like(W_host).pin_memory()
-    hp.hmat_eval_host(dev.handle, W_host, Y_host, hp.HMAT_MODE_FP64, stream)
-    dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        hp.hmat_eval_host(dev.handle, W_host, Y_host, hp.HMAT_MODE_FP64, stream)
-    e2e_s = dist.max((time.perf_counter() - t0) / args.steps)
-    e2e_value = dist.world * q / e2e_s
+    e2e = {}
+    modes = [("fp64", hp.HMAT_MODE_FP64)] + ([("mixed", hp.HMAT_MODE_MIXED)] if mixed is not None else [])
+    for name, mode in modes:
+        hp.hmat_eval_host(dev.handle, W_host, Y_host, mode, stream)
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hp.hmat_eval_host(dev.handle, W_host, Y_host, mode, stream)
+        e2e[name] = dist.world * q / dist.max((time.perf_counter() - t0) / args.steps)
+    if mixed is not None:
+        mixed["e2e"] = {"value": round(e2e["mixed"], 3), "unit": "cols/s", "h2d_bytes_per_step": int(W_host.numel() * 8),
+                        "d2h_bytes_per_step": int(Y_host.numel() * 8)}
+
+    e2e_value = e2e["fp64"]
 
     # roofline of the dominant kernel: the FP64 near-field grouped GEMM (bound by the DFMA pipe)
     # (a phase may be split into one launch per row-tile size: the unit is one evaluation's near field)
