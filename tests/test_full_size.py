@@ -1,0 +1,80 @@
+"""GPU parity at the full sizes of the benchmark recipes, in the launch configuration
+bench.py times.
+
+* N = 65536 mixture recipe (d = 8, Gaussian h = 1, leaf 128, tol 1e-5, q = 256): the
+  oracle's own full-size HMatrix is loaded through hmat_load; the rows of eight sampled
+  leaves (the longest and shortest near lists among them) are formed by the oracle's
+  leaf-subset evaluator and compared with the GPU's FP64 result (relative error <=
+  1e-12 on those rows) and its mixed result (<= 1e-6), after autotuning as the bench does.
+* N = 262144 inverse-multiquadric recipe (q = 512): too large for the oracle, so the
+  GPU's own HMatrix (hmat_build) is held to properties that hold at any size: K~ is
+  symmetric (W1^T K~ W2 = W2^T K~ W1) and the product is linear, in FP64 to 1e-12.
+"""
+import numpy as np
+import pytest
+
+import paper_1812_07152_gb300 as hp
+from oracle import hmatrix as hm
+from tests.fixtures import desc_from_oracle
+from workloads import WORKLOADS, make_points, normal_rhs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _rows(H, leaves):
+    t = H.tree
+    return np.concatenate([t.perm[t.index_set(a)] for a in leaves])
+
+
+def test_mixture_recipe_full_size_sampled_rows():
+    w = WORKLOADS["h2_gmm8d_n65536"]
+    H, _ = hm.compress_workload(w)
+    t = H.tree
+    lengths = {}
+    for i, _ in H.inter.near:
+        lengths[i] = lengths.get(i, 0) + 1
+    by_len = sorted(lengths, key=lambda a: (lengths[a], a))
+    rng = np.random.default_rng(3)
+    leaves = sorted(set(by_len[:2] + by_len[-2:] + list(rng.choice(range(t.first_leaf, t.n_nodes), 4, replace=False))))
+    W = normal_rhs(w.n, w.q, w.rhs_seed)
+    Yref = hm.evaluate(H, W, leaves=leaves)
+    rows = _rows(H, leaves)
+    h = hp.hmat_load(**desc_from_oracle(H), flags=hp.HMAT_LOAD_MIXED)
+    try:
+        Wd = torch.from_numpy(W).cuda()
+        Yd = torch.empty_like(Wd)
+        for mode, tol in ((hp.HMAT_MODE_FP64, 1e-12), (hp.HMAT_MODE_MIXED, 1e-6)):
+            hp.hmat_autotune(h, w.q, mode)
+            hp.hmat_eval(h, Wd, Yd, w.q, mode)
+            assert hp.hmat_status_poll(h) == hp.HMAT_OK
+            Y = Yd.cpu().numpy()[rows]
+            err = np.linalg.norm(Y - Yref[rows]) / np.linalg.norm(Yref[rows])
+            print(f"full-size mixture recipe, mode {mode}: relative error on {len(rows)} sampled rows {err:.3e}")
+            assert err <= tol, (mode, err)
+    finally:
+        hp.hmat_free(h)
+
+
+def test_imq_recipe_full_size_symmetry_and_linearity():
+    w = WORKLOADS["h2_imq3d_n262144"]
+    X = make_points(w)
+    h = hp.hmat_build(X, kernel=w.kernel, kernel_param=w.kernel_param, admissibility=w.admissibility,
+                      leaf_size=w.leaf_size, tol=w.tol, max_rank=w.max_rank, eta=w.eta, sample_seed=w.sample_seed)
+    try:
+        q = w.q
+        W1 = torch.from_numpy(normal_rhs(w.n, q, 61)).cuda()
+        W2 = torch.from_numpy(normal_rhs(w.n, q, 62)).cuda()
+        Y1, Y2, Y3 = torch.empty_like(W1), torch.empty_like(W1), torch.empty_like(W1)
+        hp.hmat_eval(h, W1, Y1, q)
+        hp.hmat_eval(h, W2, Y2, q)
+        hp.hmat_eval(h, 2.5 * W1 - 0.75 * W2, Y3, q)
+        assert hp.hmat_status_poll(h) == hp.HMAT_OK
+        G12 = W1.T @ Y2
+        G21 = W2.T @ Y1
+        sym = float(torch.linalg.norm(G12 - G21.T) / torch.linalg.norm(G12))
+        lin = float(torch.linalg.norm(Y3 - (2.5 * Y1 - 0.75 * Y2)) / torch.linalg.norm(Y3))
+        print(f"full-size IMQ recipe: symmetry {sym:.3e}, linearity {lin:.3e}")
+        assert sym <= 1e-12 and lin <= 1e-12
+    finally:
+        hp.hmat_free(h)
