@@ -1,5 +1,5 @@
 // libhmat C ABI: validation and level-packed upload of an HMatrix (hmat_load),
-// the evaluation driver (hmat_eval) and the handle's lifetime.
+// the evaluation runtime (hmat_eval) and the handle's lifetime.
 //
 // The phases follow the evaluation of Section 2.1: the near-field reduction over
 // D, the bottom-up tree loop over the bases, the far-field reduction over B and

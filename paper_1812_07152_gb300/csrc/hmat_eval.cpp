@@ -1,4 +1,4 @@
-// Evaluation driver: Y = K~ W for one loaded HMatrix (Section 2.1, "Evaluation").
+// Evaluation runtime: Y = K~ W for one loaded HMatrix (Section 2.1, "Evaluation").
 //
 // FP64 mode: the phases in order (near field, upward leaves, upward transfers level by
 // level, coupling, downward transfers level by level, downward leaves), each one
