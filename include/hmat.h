@@ -261,7 +261,11 @@ hmat_status hmat_reserve(hmat_t h, int64_t q_max);
  * caller order): copies W to a device buffer owned by the handle, evaluates as
  * hmat_eval does, copies Y back, all on `stream`, and synchronises the stream
  * before returning. Pinned host buffers give full copy bandwidth. The device
- * buffers grow on demand (cudaMalloc, which synchronises the device).
+ * buffers grow on demand (cudaMalloc, which synchronises the device). In the mixed
+ * mode with q >= 128 the columns are evaluated in two groups whose copies overlap the
+ * other group's evaluation (on a copy stream of the handle); the groups' W scales
+ * differ from one whole-q evaluation, so results can differ from hmat_eval's by
+ * rounding (within the mixed mode's accuracy).
  */
 hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream);
 

@@ -21,6 +21,8 @@ namespace hmat {
 namespace {
 
 constexpr int64_t kAlignBytes = 256;
+// hmat_eval_host pipelines the mixed mode in two column groups from this many columns each.
+constexpr int64_t kHostSplitMinQ = 64;
 
 int64_t align_up(int64_t x) { return (x + kAlignBytes - 1) / kAlignBytes * kAlignBytes; }
 
@@ -125,6 +127,12 @@ void ctx_destroy(EvalContext* c) {
   cudaFree(c->host_w);
   cudaFree(c->host_y);
   if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->copy) {
+    cudaStreamSynchronize(c->copy);
+    cudaStreamDestroy(c->copy);
+  }
+  for (cudaEvent_t ev : c->ev_copy)
+    if (ev) cudaEventDestroy(ev);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
@@ -301,6 +309,51 @@ extern "C" hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int6
     c->host_cap = values;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (mode == HMAT_MODE_MIXED && q >= 2 * kHostSplitMinQ) {
+    // Two column groups, the copies on a stream of their own: the second group's upload
+    // runs under the first group's evaluation and the first group's download under the
+    // second's (the mixed evaluation takes milliseconds, like the copies).
+    if (!c->copy) {
+      cudaError_t e = cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking);
+      for (cudaEvent_t& ev : c->ev_copy)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    const int64_t n = h->n_points;
+    const int64_t qa = std::min<int64_t>(q - 16, (q / 2 + 15) / 16 * 16), qb = q - qa;
+    double* wa = c->host_w;
+    double* wb = c->host_w + n * qa;
+    double* ya = c->host_y;
+    double* yb = c->host_y + n * qa;
+    cudaEvent_t* ev = c->ev_copy;
+    const size_t pitch = (size_t)q * sizeof(double);
+    cudaError_t e = cudaEventRecord(ev[0], s);  // earlier work on s that used these buffers
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy, ev[0], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(wa, qa * sizeof(double), W, pitch, qa * sizeof(double), n, cudaMemcpyHostToDevice, c->copy);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->copy);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(wb, qb * sizeof(double), W + qa, pitch, qb * sizeof(double), n, cudaMemcpyHostToDevice,
+                            c->copy);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
+    if (e != cudaSuccess) return cuda_status(e);
+    hmat_status st = hmat_eval(h, wa, ya, qa, mode, stream);
+    if (st != HMAT_OK) return st;
+    if ((e = cudaEventRecord(ev[3], s)) != cudaSuccess || (e = cudaStreamWaitEvent(s, ev[2], 0)) != cudaSuccess)
+      return cuda_status(e);
+    if ((st = hmat_eval(h, wb, yb, qb, mode, stream)) != HMAT_OK) return st;
+    e = cudaEventRecord(ev[4], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy, ev[3], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(Y, pitch, ya, qa * sizeof(double), qa * sizeof(double), n, cudaMemcpyDeviceToHost, c->copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy, ev[4], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(Y + qa, pitch, yb, qb * sizeof(double), qb * sizeof(double), n, cudaMemcpyDeviceToHost,
+                            c->copy);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy);
+    return cuda_status(e);
+  }
   const size_t bytes = (size_t)values * sizeof(double);
   cudaError_t e = cudaMemcpyAsync(c->host_w, W, bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);

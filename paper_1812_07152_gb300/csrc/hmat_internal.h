@@ -149,6 +149,8 @@ struct EvalContext {
   double* host_w = nullptr;      // device copies of W / Y for hmat_eval_host
   double* host_y = nullptr;
   int64_t host_cap = 0;          // values
+  cudaStream_t copy = nullptr;   // hmat_eval_host: host <-> device copies beside the evaluation
+  cudaEvent_t ev_copy[5] = {};
   cudaStream_t aux = nullptr;    // mixed: the far chain runs here, beside the near field
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };

@@ -134,3 +134,22 @@ def test_mixed_coupling_engine_choice(base, n, engine):
         assert hp.hmat_info(h)["coupling_engine"] == 0
     finally:
         hp.hmat_free(h)
+
+
+def test_eval_host_pipelined_mixed_and_fp64():
+    """hmat_eval_host: FP64 gives hmat_eval's result bit for bit; the mixed mode at q >= 128
+    evaluates two column groups with overlapped copies and stays within the mixed tolerance."""
+    w, H, _ = oracle_case("h2_imq3d_n262144", 3000, 64)
+    h = hp.hmat_load(**desc_from_oracle(H), flags=hp.HMAT_LOAD_MIXED)
+    try:
+        for q in (200, 130):
+            W = rhs(w.n, q, 90 + q)
+            Yref = hm.evaluate(H, W)
+            Wh = torch.from_numpy(W).pin_memory()
+            Yh = torch.empty_like(Wh).pin_memory()
+            hp.hmat_eval_host(h, Wh, Yh, hp.HMAT_MODE_MIXED)
+            _check(Yh.numpy(), Yref, f"eval_host mixed q={q}")
+            hp.hmat_eval_host(h, Wh, Yh, hp.HMAT_MODE_FP64)
+            assert np.array_equal(Yh.numpy(), _eval(h, W, hp.HMAT_MODE_FP64))
+    finally:
+        hp.hmat_free(h)
