@@ -41,6 +41,7 @@ constexpr uint32_t kTmemCols = 512;          // main[0], main[1], cross, compens
 constexpr uint64_t kWaitNs = 2000000000ull;  // give up a wait after 2 s
 constexpr int kScaleTop = 13;                // scaled maxima land in [2^13, 2^14)
 constexpr int kDrainBlocks = 2;              // near blocks accumulated in TMEM between two drains
+constexpr int kStagedEntries = 1024;         // list entries whose metadata a CTA keeps in shared memory
 
 // ------------------------------------------------------------------ PTX helpers
 
@@ -341,6 +342,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ volatile int issued_a, issued_b, consumed;
+  // per list entry: k-chunks of its source, byte offset of its A tiles, its first X chunk
+  __shared__ int32_t s_kc[kStagedEntries];
+  __shared__ int64_t s_aoff[kStagedEntries], s_g0[kStagedEntries];
+  __shared__ int s_nb;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TcTile work = a.tc.work[blockIdx.x / a.n_ct];
@@ -350,6 +355,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   const uint32_t b_bytes = 2u * (uint32_t)a.n_t * 128u;
   const uint32_t a_bytes = 2u * kTcTileBytes;
 
+  // The roles walk the target's list one entry at a time; its metadata (two dependent
+  // global loads per entry) is loaded once, by every thread together, before they start.
+  if (threadIdx.x == 0) s_nb = 0;
+  __syncthreads();
+  {
+    int cnt = 0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int j = a.tc.idx[e];
+      const int kc = a.tc.kc[j];
+      cnt += kc > 0;
+      const int64_t i = e - e0;
+      if (i < kStagedEntries) {
+        s_kc[i] = kc;
+        s_aoff[i] = a.tc.a_off[e];
+        s_g0[i] = a.tc.kcum[j];
+      }
+    }
+    if (cnt) atomicAdd(&s_nb, cnt);
+  }
+  auto ent_kc = [&](int64_t e) -> int {
+    const int64_t i = e - e0;
+    return i < kStagedEntries ? s_kc[i] : a.tc.kc[a.tc.idx[e]];
+  };
+  auto ent_aoff = [&](int64_t e) -> int64_t {
+    const int64_t i = e - e0;
+    return i < kStagedEntries ? s_aoff[i] : a.tc.a_off[e];
+  };
+  auto ent_g0 = [&](int64_t e) -> int64_t {
+    const int64_t i = e - e0;
+    return i < kStagedEntries ? s_g0[i] : a.tc.kcum[a.tc.idx[e]];
+  };
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 2);  // the D and the W producer each arrive once per stage
@@ -388,11 +424,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
       int it = 0;
       bool ok = true;
       for (int64_t e = e0; e < e1 && ok; ++e) {
-        const int j = a.tc.idx[e];
-        const int kc = a.tc.kc[j];
+        const int kc = ent_kc(e);
         if (kc == 0) continue;
-        const uint8_t* abase = a.tc.tiles + a.tc.a_off[e] + (int64_t)mt * kc * a_bytes;
-        const int64_t g0 = a.tc.kcum[j];
+        const uint8_t* abase = a.tc.tiles + ent_aoff(e) + (int64_t)mt * kc * a_bytes;
+        const int64_t g0 = ent_g0(e);
         for (int c = 0; c < kc; ++c, ++it) {
           const int s = it % kStages, r = it / kStages;
           if (r > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (r - 1) & 1, &abort_flag)) {
@@ -419,12 +454,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
     if (lane == 0) {
       const uint32_t idesc = idesc_f16(kTcRows, a.n_t);
       const uint32_t cross = tmem + 256;
-      int nb = 0;  // blocks with data
-      for (int64_t e = e0; e < e1; ++e) nb += a.tc.kc[a.tc.idx[e]] > 0;
+      const int nb = s_nb;  // blocks with data
       int it = 0, blk = 0;
       bool ok = true;
       for (int64_t e = e0; e < e1 && ok; ++e) {
-        const int kc = a.tc.kc[a.tc.idx[e]];
+        const int kc = ent_kc(e);
         if (kc == 0) continue;
         const int grp = blk / kDrainBlocks, b = grp & 1, rb = grp >> 1;
         const bool first_of_group = blk % kDrainBlocks == 0;
@@ -482,8 +516,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) tmem_st16(comp + cc * 16, z);
     }
-    int nb = 0;  // blocks with data, drained kDrainBlocks at a time
-    for (int64_t e = e0; e < e1; ++e) nb += a.tc.kc[a.tc.idx[e]] > 0;
+    const int nb = s_nb;  // blocks with data, drained kDrainBlocks at a time
     const int n_groups = (nb + kDrainBlocks - 1) / kDrainBlocks;
     int blk = 0;
     bool ok = true;
