@@ -257,9 +257,20 @@ __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst
 template <typename T>
 __global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t n,
                                                 unsigned long long* __restrict__ out) {
-  double m = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    m = fmax(m, fabs((double)X[i]));
+  // four independent coalesced loads in flight per thread and iteration
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    const double a0 = (double)X[i], a1 = (double)X[i + stride], a2 = (double)X[i + 2 * stride],
+                 a3 = (double)X[i + 3 * stride];
+    m0 = fmax(m0, fabs(a0));
+    m1 = fmax(m1, fabs(a1));
+    m2 = fmax(m2, fabs(a2));
+    m3 = fmax(m3, fabs(a3));
+  }
+  for (; i < n; i += stride) m0 = fmax(m0, fabs((double)X[i]));
+  double m = fmax(fmax(m0, m1), fmax(m2, m3));
   m = block_max_d(m);
   if (threadIdx.x == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
@@ -288,6 +299,13 @@ __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__
   const int64_t q0 = (int64_t)ct * n_t;
   uint8_t* hi_t = out + (g * n_ct + ct) * (int64_t)(2 * n_t * 128);
   uint8_t* lo_t = hi_t + n_t * 128;
+  // the chunk's source rows, looked up once (each X load then waits on shared memory only)
+  __shared__ int64_t src_row[kTcK];
+  if (threadIdx.x < kTcK) {
+    const int k = threadIdx.x;
+    src_row[k] = c * kTcK + k < n_j ? (perm ? perm[row0 + k] : row0 + k) : -1;
+  }
+  __syncthreads();
   for (int x = threadIdx.x; x < n_t * 8; x += blockDim.x) {
     const int kc = x / n_t, n = x % n_t;
     const int64_t gq = q0 + n;
@@ -296,8 +314,8 @@ __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__
     for (int t = 0; t < 8; ++t) {
       const int k = kc * 8 + t;
       float xs = 0.0f;
-      if (c * kTcK + k < n_j && gq < q) {
-        const int64_t src = perm ? perm[row0 + k] : row0 + k;
+      const int64_t src = src_row[k];
+      if (src >= 0 && gq < q) {
         const T v = X[src * q + gq];
         if constexpr (sizeof(T) == 8) {
           xs = __double2float_rn((double)v * sd);
