@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
 }
 
 // Failure-detection self-test: one thread waits, through the routine every wait of
-// k_near_tc uses, on a barrier that nothing arrives at; the wait gives up after
+// k_tc uses, on a barrier that nothing arrives at; the wait gives up after
 // limit_ns and the status word gets HMAT_ETIMEOUT as a stuck evaluation would set it.
 // No copy or MMA is in flight, so returning is all the clean-up there is.
 __global__ void k_wait_selftest(int* status, uint64_t limit_ns) {
