@@ -396,7 +396,8 @@ cudaError_t launch_f32(const Handle& h, const Phase& ph, const float* arena, int
   return cudaGetLastError();
 }
 
-// One launch of a far-field phase in FP32 (tasks with at most one entry each).
+// One launch of a far-field phase in FP32 (tasks with at most one entry each): 32, 64 or
+// (64-row tiles, q > 256) 128 columns per CTA.
 template <typename TY>
 cudaError_t launch_phase_f32(const Handle& h, const Phase& ph, const float* arena, int64_t a_shift, const float* X,
                              const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q, cudaStream_t s) {
@@ -408,7 +409,12 @@ cudaError_t launch_phase_f32(const Handle& h, const Phase& ph, const float* aren
   switch (ph.tile_rows) {
     case 16: { HMAT_GEMM_BN32(16) }
     case 32: { HMAT_GEMM_BN32(32) }
-    default: { HMAT_GEMM_BN32(64) }
+    default: {
+      // wide q: 128-column tiles read each block of A half as often (measured faster for
+      // q = 512, no different for q = 256)
+      if (q > 256) return launch_f32<TY, 64, 128>(h, ph, arena, a_shift, X, x_map, Y, y_map, q, s);
+      HMAT_GEMM_BN32(64)
+    }
   }
 #undef HMAT_GEMM_BN32
 }

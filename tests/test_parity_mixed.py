@@ -51,6 +51,7 @@ CASES = [
     ("h2_imq3d_n262144", 2500, 17, (("admissibility", "none"),)),  # all near
     ("hss_uniform3d_n2048", 1500, 24, (("tol", 0.0), ("max_rank", 10 ** 6))),  # full rank: up to 6 m-tiles per node
     ("h2_invdist3d_n262144", 3000, 1, ()),                       # 1/r kernel, matrix-vector (q = 1)
+    ("h2_gmm8d_n65536", 4096, 300, ()),                          # q > 256: 128-column FP32 far-field tiles
     ("hss_uniform3d_n2048", 1200, 9, (("tol", 1.0),)),           # every rank 0
     ("h2_gmm8d_n65536", 60, 5, ()),                              # a single leaf
 ]
