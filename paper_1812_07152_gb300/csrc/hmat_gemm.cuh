@@ -221,6 +221,10 @@ __device__ __forceinline__ void cp_async4(uint32_t smem_dst, const void* gsrc, b
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_dst), "l"(gsrc), "r"(valid ? 4 : 0)
                : "memory");
 }
+__device__ __forceinline__ void cp_async16(uint32_t smem_dst, const void* gsrc, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_dst), "l"(gsrc), "r"(valid ? 16 : 0)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -242,7 +246,9 @@ struct CfgF32 {
   static_assert(kXPer <= BK, "one map index per row of the chunk");
 };
 
-template <typename TY, int BM, int BN>
+// XV: the rows of X are copied 16 bytes (four columns) at a time; needs q a multiple of 4
+// and X 16-byte aligned.
+template <typename TY, int BM, int BN, bool XV>
 __global__ void __launch_bounds__(CfgF32<BM, BN>::kThreads)
 k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
                    const GemmEntry* __restrict__ entries, const float* __restrict__ arena, int64_t a_shift,
@@ -277,13 +283,16 @@ k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restric
   const int my_chunks = n_chunks > slice ? (n_chunks - slice + C::kSlices - 1) / C::kSlices : 0;
   const float* a = arena + (en.a_off - a_shift);
 
-  // X row of depth gk (through the row map when there is one)
-  int64_t rows_next[C::kXPer];
+  // X row of depth gk (through the row map when there is one); one per copy of XW floats
+  constexpr int XW = XV ? 4 : 1;
+  constexpr int XN = C::kXPer / XW;  // X copies per thread and chunk
+  static_assert(C::kXPer % XW == 0 && BN % XW == 0, "whole vectors");
+  int64_t rows_next[XN];
   auto load_rows = [&](int j, int64_t* rows) {
     const int c = slice + j * C::kSlices;
 #pragma unroll
-    for (int t = 0; t < C::kXPer; ++t) {
-      const int k = (lt + t * NTS) / BN;
+    for (int t = 0; t < XN; ++t) {
+      const int k = (lt + t * NTS) / (BN / XW);
       const int gk = c * BK + k;
       rows[t] = (j < my_chunks && gk < en.k) ? map_row(x_map, en.x_row + gk) : 0;
     }
@@ -304,17 +313,20 @@ k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restric
       cp_async4(as + 4u * (uint32_t)(k * C::kAStride + m), src, ok);
     }
 #pragma unroll
-    for (int t = 0; t < C::kXPer; ++t) {
+    for (int t = 0; t < XN; ++t) {
       const int idx = lt + t * NTS;
-      const int k = idx / BN, n = idx % BN;
+      const int k = idx / (BN / XW), n = (idx % (BN / XW)) * XW;
       const int64_t gq = q0 + n;
-      const bool ok = k0 + k < en.k && gq < q;
+      const bool ok = k0 + k < en.k && gq < q;  // XV: gq < q implies gq + 3 < q
       const float* src = ok ? X + rows[t] * q + gq : X;
-      cp_async4(xs + 4u * (uint32_t)(k * BN + n), src, ok);
+      if (XV)
+        cp_async16(xs + 4u * (uint32_t)(k * BN + n), src, ok);
+      else
+        cp_async4(xs + 4u * (uint32_t)(k * BN + n), src, ok);
     }
   };
 
-  int64_t rows_cur[C::kXPer];
+  int64_t rows_cur[XN];
   load_rows(0, rows_cur);
 #pragma unroll
   for (int st = 0; st < S - 1; ++st) {
@@ -322,7 +334,7 @@ k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restric
     issue(st, st, rows_cur);
     cp_async_commit();
 #pragma unroll
-    for (int t = 0; t < C::kXPer; ++t) rows_cur[t] = rows_next[t];
+    for (int t = 0; t < XN; ++t) rows_cur[t] = rows_next[t];
   }
   for (int j = 0; j < my_chunks; ++j) {
     load_rows(j + S, rows_next);  // indices one chunk ahead of the next copy
@@ -331,7 +343,7 @@ k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restric
     issue(j + S - 1, (j + S - 1) % S, rows_cur);
     cp_async_commit();
 #pragma unroll
-    for (int t = 0; t < C::kXPer; ++t) rows_cur[t] = rows_next[t];
+    for (int t = 0; t < XN; ++t) rows_cur[t] = rows_next[t];
     const float* As = a_st(j % S);
     const float* Xs = x_st(j % S);
 #pragma unroll
@@ -388,11 +400,12 @@ cudaError_t launch_f32(const Handle& h, const Phase& ph, const float* arena, int
   const int64_t n_col = (q + BN - 1) / BN;
   const int64_t blocks = ph.n_tiles * n_col;
   if (blocks > 2147483647LL) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_grouped_gemm_f32<TY, BM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       C::kSmemBytes);
+  const bool xv = q % 4 == 0 && ((uintptr_t)X & 15u) == 0;
+  auto kern = xv ? k_grouped_gemm_f32<TY, BM, BN, true> : k_grouped_gemm_f32<TY, BM, BN, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
-  k_grouped_gemm_f32<TY, BM, BN><<<(unsigned)blocks, C::kThreads, C::kSmemBytes, s>>>(
-      h.tiles + ph.tile_begin, h.tasks, h.entries, arena, a_shift, X, x_map, Y, y_map, q, (int)n_col);
+  kern<<<(unsigned)blocks, C::kThreads, C::kSmemBytes, s>>>(h.tiles + ph.tile_begin, h.tasks, h.entries, arena,
+                                                            a_shift, X, x_map, Y, y_map, q, (int)n_col);
   return cudaGetLastError();
 }
 
