@@ -207,7 +207,8 @@ void free_device(Handle* h) {
   free_tc(&h->tc_near);
   free_tc(&h->tc_far);
   cudaFree(h->arena32);
-  h->arena32 = nullptr; h->has_mixed = false;
+  cudaFree(h->entries32);
+  h->arena32 = nullptr; h->entries32 = nullptr; h->has_mixed = false;
   cudaFree(h->arena);
   cudaFree(h->far_rows);
   h->far_rows = nullptr;
@@ -362,11 +363,14 @@ hmat_status build_tc(Handle* h, const TcSpec& sp, TcProduct* out) {
 
 // Mixed-precision copies of a loaded HMatrix (HMAT_LOAD_MIXED): the near blocks and
 // the coupling blocks as FP16 hi/lo tensor-core tiles (packed on the device from the
-// FP64 arena, one scale exponent per 128-row m-tile of a target) and the bases (the
-// arena from basis_begin to coupling_begin) as FP32.
+// FP64 arena, one scale exponent per 128-row m-tile of a target), and the operand of
+// every FP32 entry (the bases, and the coupling blocks when the coupling runs in FP32)
+// as an FP32 block of its own in the k-major padded layout the FP32 kernel copies 16
+// bytes at a time (a basis is held twice: as read by the upward and by the downward pass).
 hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const std::vector<int64_t>& near_off,
                         const std::vector<int64_t>& far_task_off, const std::vector<int64_t>& far_off,
-                        const std::vector<int64_t>& far_k, int64_t basis_begin, int64_t coupling_begin) {
+                        const std::vector<int64_t>& far_k, const std::vector<GemmTask>& tasks,
+                        const std::vector<GemmEntry>& entries, const std::vector<GemmTile>& tiles) {
   const int64_t nl = v.n_leaves, fl = v.first_leaf;
   {  // near field: targets and sources are the leaves
     TcSpec sp;
@@ -414,17 +418,39 @@ hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const
     if (st != HMAT_OK) return st;
   }
 
-  // FP32 copy of the bases (the upward and downward passes), and of the coupling
-  // blocks when the coupling runs in FP32
+  // FP32 operands: one k-major block per entry of an FP32 phase (each task belongs to
+  // one phase; the FP32 coupling phase has tiles of its own over the coupling tasks)
+  // (an entry of another phase keeps k = 0 there: it contributes nothing)
+  std::vector<GemmEntry> e32(entries.size(), GemmEntry{0, 0, 0, 4, 1, 0});
+  std::vector<F32Job> jobs;
+  std::vector<char> seen(tasks.size(), 0);
+  int64_t n32 = 0;
+  for (const Phase& ph : h->phases32)
+    for (int64_t i = ph.tile_begin; i < ph.tile_begin + ph.n_tiles; ++i) {
+      const int32_t t = tiles[i].task;
+      if (seen[t]) continue;
+      seen[t] = 1;
+      const GemmTask& tk = tasks[t];
+      const int32_t ld = (tk.m + 3) / 4 * 4;
+      for (int32_t e = tk.e_begin; e < tk.e_end; ++e) {
+        const GemmEntry& en = entries[e];
+        jobs.push_back(F32Job{en.a_off, n32, tk.m, en.k, en.lda, ld, en.trans, 0});
+        e32[e] = GemmEntry{n32, en.x_row, en.k, ld, 1, 0};
+        n32 += (int64_t)ld * en.k;
+      }
+    }
   cudaError_t e;
-  h->arena32_shift = basis_begin;
-  const int64_t end32 = h->tc_coupling ? coupling_begin : h->arena_values;
-  const int64_t n32 = std::max<int64_t>(end32 - basis_begin, 1);
-  if ((e = cudaMalloc((void**)&h->arena32, (size_t)n32 * sizeof(float))) != cudaSuccess) return cuda_status(e);
-  h->device_bytes += n32 * (int64_t)sizeof(float);
-  if ((e = launch_to_f32(h->arena + basis_begin, h->arena32, end32 - basis_begin, 0)) != cudaSuccess)
+  if ((e = cudaMalloc((void**)&h->arena32, (size_t)std::max<int64_t>(n32, 4) * sizeof(float))) != cudaSuccess)
     return cuda_status(e);
-  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_status(e);
+  h->device_bytes += std::max<int64_t>(n32, 4) * (int64_t)sizeof(float);
+  if ((e = upload(&h->entries32, e32, &h->device_bytes)) != cudaSuccess) return cuda_status(e);
+  F32Job* d_jobs = nullptr;
+  int64_t scratch = 0;
+  if ((e = upload(&d_jobs, jobs, &scratch)) != cudaSuccess) return cuda_status(e);
+  e = launch_relayout_f32(h->arena, d_jobs, (int64_t)jobs.size(), h->arena32, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(d_jobs);
+  if (e != cudaSuccess) return cuda_status(e);
   h->has_mixed = true;
   return HMAT_OK;
 }
@@ -482,7 +508,6 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
       h->near_values += cnt;
       off = align_up(off + cnt, kAlignValues);
     }
-  const int64_t basis_region_begin = off;
   for (int64_t a = 0; a < v.n_nodes; ++a) {
     if (h->rank[a] == 0) continue;
     basis_off[a] = off;
@@ -490,7 +515,6 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     h->basis_values += cnt;
     off = align_up(off + cnt, kAlignValues);
   }
-  const int64_t coupling_region_begin = off;
   // coupling: the blocks of one target node side by side, B_a = [B_ab1 | B_ab2 | ...]
   // (s_a x K_a, K_a = sum of the partners' ranks), so the far-field reduction of a
   // node is one product B_a [w_b1; w_b2; ...] whose right operand is gathered through
@@ -738,8 +762,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
   std::vector<int> zero(1, 0);
   if ((e = upload(&h->status, zero, &h->device_bytes)) != cudaSuccess) return fail(e);
   if (flags & HMAT_LOAD_MIXED) {
-    hmat_status ms = build_mixed(h.get(), d, v, near_off, far_task_off, far_off, far_k, basis_region_begin,
-                                 coupling_region_begin);
+    hmat_status ms = build_mixed(h.get(), d, v, near_off, far_task_off, far_off, far_k, tasks, entries, tiles);
     if (ms != HMAT_OK) {
       free_device(h.get());
       return ms;

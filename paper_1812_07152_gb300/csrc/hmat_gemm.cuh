@@ -210,7 +210,10 @@ cudaError_t launch_phase(const Handle& h, const Phase& ph, int shape, int64_t n_
 // than FP64 on GB300, so these launches are bound by memory latency along each
 // task's K loop (coupling lists reach hundreds of partners). Every task of the mixed
 // far field has at most one entry (the coupling blocks of a node are concatenated),
-// so chunk c of a task covers depth c * BK. The CTA splits the chunks round-robin
+// so chunk c of a task covers depth c * BK. The entries index the FP32 arena, where
+// every operand is k-major (A(m, k) at a[k * lda + m]) with lda a multiple of 4,
+// zero-padded rows up to lda and a 16-byte aligned start, so A is copied 16 bytes
+// (four rows m) at a time. The CTA splits the chunks round-robin
 // over up to four groups of warps; each group copies its chunks straight into shared
 // memory with cp.async, kAsyncStages - 1 chunks ahead (the row-map indices one more
 // chunk ahead), and at the end the groups' partial sums are added in a fixed order.
@@ -251,7 +254,7 @@ struct CfgF32 {
 template <typename TY, int BM, int BN, bool XV>
 __global__ void __launch_bounds__(CfgF32<BM, BN>::kThreads)
 k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
-                   const GemmEntry* __restrict__ entries, const float* __restrict__ arena, int64_t a_shift,
+                   const GemmEntry* __restrict__ entries, const float* __restrict__ arena,
                    const float* X, const int64_t* __restrict__ x_map, TY* Y, const int64_t* __restrict__ y_map,
                    int64_t q, int n_col_tiles) {
   using C = CfgF32<BM, BN>;
@@ -281,9 +284,11 @@ k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restric
   if (has) en = entries[task.e_begin];
   const int n_chunks = has ? (en.k + BK - 1) / BK : 0;
   const int my_chunks = n_chunks > slice ? (n_chunks - slice + C::kSlices - 1) / C::kSlices : 0;
-  const float* a = arena + (en.a_off - a_shift);
+  const float* a = arena + en.a_off;
 
   // X row of depth gk (through the row map when there is one); one per copy of XW floats
+  constexpr int AV = BM * BK / 4;           // 16-byte A copies per chunk
+  constexpr int AN = (AV + NTS - 1) / NTS;  // per thread (the last ones masked when NTS > AV)
   constexpr int XW = XV ? 4 : 1;
   constexpr int XN = C::kXPer / XW;  // X copies per thread and chunk
   static_assert(C::kXPer % XW == 0 && BN % XW == 0, "whole vectors");
@@ -303,14 +308,14 @@ k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restric
     const uint32_t as = (uint32_t)__cvta_generic_to_shared(a_st(st));
     const uint32_t xs = (uint32_t)__cvta_generic_to_shared(x_st(st));
 #pragma unroll
-    for (int t = 0; t < C::kAPer; ++t) {
+    for (int t = 0; t < AN; ++t) {
       const int idx = lt + t * NTS;
-      int m, k;
-      if (en.trans) { k = idx / BM; m = idx % BM; } else { m = idx / BK; k = idx % BK; }
+      if (AV % NTS != 0 && idx >= AV) break;
+      const int k = idx / (BM / 4), m = (idx % (BM / 4)) * 4;
       const int gm = m0 + m, gk = k0 + k;
-      const bool ok = gm < task.m && gk < en.k;
-      const float* src = ok ? (en.trans ? a + (int64_t)gk * en.lda + gm : a + (int64_t)gm * en.lda + gk) : arena;
-      cp_async4(as + 4u * (uint32_t)(k * C::kAStride + m), src, ok);
+      const bool ok = gm < task.m && gk < en.k;  // gm < task.m <= lda, both multiples of 4
+      const float* src = ok ? a + (int64_t)gk * en.lda + gm : arena;
+      cp_async16(as + 4u * (uint32_t)(k * C::kAStride + m), src, ok);
     }
 #pragma unroll
     for (int t = 0; t < XN; ++t) {
@@ -393,7 +398,7 @@ k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restric
 }
 
 template <typename TY, int BM, int BN>
-cudaError_t launch_f32(const Handle& h, const Phase& ph, const float* arena, int64_t a_shift, const float* X,
+cudaError_t launch_f32(const Handle& h, const Phase& ph, const float* arena, const float* X,
                        const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q, cudaStream_t s) {
   using C = CfgF32<BM, BN>;
   static_assert(C::kSmemBytes >= (C::kSlices - 1) * TM * TN * C::kSliceThreads * 4, "room for the partial sums");
@@ -404,28 +409,28 @@ cudaError_t launch_f32(const Handle& h, const Phase& ph, const float* arena, int
   auto kern = xv ? k_grouped_gemm_f32<TY, BM, BN, true> : k_grouped_gemm_f32<TY, BM, BN, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)blocks, C::kThreads, C::kSmemBytes, s>>>(h.tiles + ph.tile_begin, h.tasks, h.entries, arena,
-                                                            a_shift, X, x_map, Y, y_map, q, (int)n_col);
+  kern<<<(unsigned)blocks, C::kThreads, C::kSmemBytes, s>>>(h.tiles + ph.tile_begin, h.tasks, h.entries32, arena, X,
+                                                            x_map, Y, y_map, q, (int)n_col);
   return cudaGetLastError();
 }
 
 // One launch of a far-field phase in FP32 (tasks with at most one entry each): 32, 64 or
 // (64-row tiles, q > 256) 128 columns per CTA.
 template <typename TY>
-cudaError_t launch_phase_f32(const Handle& h, const Phase& ph, const float* arena, int64_t a_shift, const float* X,
+cudaError_t launch_phase_f32(const Handle& h, const Phase& ph, const float* arena, const float* X,
                              const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q, cudaStream_t s) {
   if (ph.n_tiles == 0 || q == 0) return cudaSuccess;
   if (q > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
 #define HMAT_GEMM_BN32(BMV)                                                                       \
-  if (q <= 32) return launch_f32<TY, BMV, 32>(h, ph, arena, a_shift, X, x_map, Y, y_map, q, s);  \
-  return launch_f32<TY, BMV, 64>(h, ph, arena, a_shift, X, x_map, Y, y_map, q, s);
+  if (q <= 32) return launch_f32<TY, BMV, 32>(h, ph, arena, X, x_map, Y, y_map, q, s);  \
+  return launch_f32<TY, BMV, 64>(h, ph, arena, X, x_map, Y, y_map, q, s);
   switch (ph.tile_rows) {
     case 16: { HMAT_GEMM_BN32(16) }
     case 32: { HMAT_GEMM_BN32(32) }
     default: {
       // wide q: 128-column tiles read each block of A half as often (measured faster for
       // q = 512, no different for q = 256)
-      if (q > 256) return launch_f32<TY, 64, 128>(h, ph, arena, a_shift, X, x_map, Y, y_map, q, s);
+      if (q > 256) return launch_f32<TY, 64, 128>(h, ph, arena, X, x_map, Y, y_map, q, s);
       HMAT_GEMM_BN32(64)
     }
   }

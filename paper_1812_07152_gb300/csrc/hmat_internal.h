@@ -196,9 +196,11 @@ struct Handle {
   TcProduct tc_near;             // near field D_ij on the tensor cores
   TcProduct tc_far;              // coupling B_ab on the tensor cores (when tc_coupling)
   bool tc_coupling = false;      // mixed coupling engine: tensor cores, else FP32 CUDA cores
-  float* arena32 = nullptr;      // FP32 copy of the bases (and of the coupling blocks when
-                                 // the coupling runs in FP32)
-  int64_t arena32_shift = 0;     // FP64-arena offset of arena32[0]
+  float* arena32 = nullptr;      // FP32 operands of the upward and downward passes (and of
+                                 // the coupling when it runs in FP32), one block per entry,
+                                 // k-major: A(m, k) at [a_off + k * lda + m], lda a multiple
+                                 // of 4 (rows m..lda-1 zero), a_off a multiple of 4
+  GemmEntry* entries32 = nullptr;  // the entries with a_off/lda into arena32 (trans = 1)
 
   struct EvalContext* ctx = nullptr;  // the handle's own evaluation state (hmat_eval)
   std::vector<TuneEntry> tuned;       // hmat_autotune results, one per (q, mode)
@@ -268,7 +270,21 @@ cudaError_t launch_tc_scale(const TcLists& tc, const int64_t* blk_off, const int
                             cudaStream_t stream);
 cudaError_t launch_tc_pack(const TcPackJob* jobs, int64_t n_jobs, const double* arena, const int32_t* scale,
                            uint8_t* tiles, cudaStream_t stream);
-cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t stream);
+// One block of the FP64 arena copied to FP32 in the k-major padded layout of arena32:
+// dst[dst_off + k * ld + m] = A(m, k) for m < m_rows, 0 for m_rows <= m < ld, where
+// A(m, k) = src[src_off + k * lda + m] (trans) or src[src_off + m * lda + k].
+struct F32Job {
+  int64_t src_off;
+  int64_t dst_off;
+  int32_t m_rows;
+  int32_t k;
+  int32_t lda;
+  int32_t ld;
+  int32_t trans;
+  int32_t pad;
+};
+cudaError_t launch_relayout_f32(const double* arena, const F32Job* jobs, int64_t n_jobs, float* dst,
+                                cudaStream_t stream);
 // Right-hand operand split: X (n_values values, row-major with q columns; FP64 rows
 // through perm for the near field, FP32 rows in node order for the coupling) ->
 // hi/lo tiles per (source k-chunk, column tile); x32 (may be null) gets the FP32

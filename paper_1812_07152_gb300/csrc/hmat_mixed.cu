@@ -247,9 +247,17 @@ __global__ void __launch_bounds__(256) k_tc_pack(const TcPackJob* __restrict__ j
   }
 }
 
-__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = (float)src[i];
+// one CTA per block
+__global__ void k_relayout_f32(const double* __restrict__ arena, const F32Job* __restrict__ jobs,
+                               float* __restrict__ dst) {
+  const F32Job j = jobs[blockIdx.x];
+  const double* src = arena + j.src_off;
+  float* out = dst + j.dst_off;
+  const int64_t n = (int64_t)j.k * j.ld;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t k = i / j.ld, m = i % j.ld;
+    out[i] = m < j.m_rows ? (float)(j.trans ? src[k * j.lda + m] : src[m * j.lda + k]) : 0.0f;
+  }
 }
 
 // ------------------------------------------------------------------ per-evaluation W split
@@ -656,10 +664,11 @@ cudaError_t launch_tc_pack(const TcPackJob* jobs, int64_t n_jobs, const double* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t stream) {
-  if (n == 0) return cudaSuccess;
-  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
-  k_to_f32<<<(unsigned)blocks, 256, 0, stream>>>(src, dst, n);
+cudaError_t launch_relayout_f32(const double* arena, const F32Job* jobs, int64_t n_jobs, float* dst,
+                                cudaStream_t stream) {
+  if (n_jobs == 0) return cudaSuccess;
+  if (n_jobs > 2147483647LL) return cudaErrorInvalidValue;
+  k_relayout_f32<<<(unsigned)n_jobs, 256, 0, stream>>>(arena, jobs, dst);
   return cudaGetLastError();
 }
 
