@@ -4,7 +4,7 @@
 // that the split step writes; the downward leaf step adds into Y (FP64). The coupling
 // reduction between them runs here too when the ranks are small, else on the tensor
 // cores (hmat_mixed.cu).
-#include "hmat_gemm.cuh"
+#include "hmat_gemm_f32.cuh"
 
 namespace hmat {
 
