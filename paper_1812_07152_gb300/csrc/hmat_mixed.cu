@@ -262,23 +262,43 @@ __global__ void k_relayout_f32(const double* __restrict__ arena, const F32Job* _
 
 // ------------------------------------------------------------------ per-evaluation W split
 
+// |x| as an unsigned integer that orders like |x| (IEEE magnitudes order as their bit
+// patterns), NaN as 0 so that it sets no scale: the maximum then runs on the integer
+// units (FP64 compares and conversions run at 1/64 rate on this GPU).
+__device__ __forceinline__ uint64_t abs_key(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  return b <= 0x7FF0000000000000ull ? b : 0;
+}
+__device__ __forceinline__ uint32_t abs_key(float x) {
+  const uint32_t b = __float_as_uint(x) & 0x7FFFFFFFu;
+  return b <= 0x7F800000u ? b : 0;
+}
+__device__ __forceinline__ double key_value(uint64_t k) { return __longlong_as_double((long long)k); }
+__device__ __forceinline__ double key_value(uint32_t k) { return (double)__uint_as_float(k); }
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t n,
                                                 unsigned long long* __restrict__ out) {
+  using Key = decltype(abs_key(T{}));
   // four independent coalesced loads in flight per thread and iteration
-  double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+  Key m0 = 0, m1 = 0, m2 = 0, m3 = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  auto upd = [](Key& m, T x) {
+    const Key k = abs_key(x);
+    m = k > m ? k : m;
+  };
   for (; i + 3 * stride < n; i += 4 * stride) {
-    const double a0 = (double)X[i], a1 = (double)X[i + stride], a2 = (double)X[i + 2 * stride],
-                 a3 = (double)X[i + 3 * stride];
-    m0 = fmax(m0, fabs(a0));
-    m1 = fmax(m1, fabs(a1));
-    m2 = fmax(m2, fabs(a2));
-    m3 = fmax(m3, fabs(a3));
+    const T a0 = X[i], a1 = X[i + stride], a2 = X[i + 2 * stride], a3 = X[i + 3 * stride];
+    upd(m0, a0);
+    upd(m1, a1);
+    upd(m2, a2);
+    upd(m3, a3);
   }
-  for (; i < n; i += stride) m0 = fmax(m0, fabs((double)X[i]));
-  double m = fmax(fmax(m0, m1), fmax(m2, m3));
+  for (; i < n; i += stride) upd(m0, X[i]);
+  m0 = m0 > m1 ? m0 : m1;
+  m2 = m2 > m3 ? m2 : m3;
+  double m = key_value(m0 > m2 ? m0 : m2);
   m = block_max_d(m);
   if (threadIdx.x == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
@@ -289,8 +309,10 @@ __global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t
 // into x32, the FP32 tree-order copy the far field reads. The coupling's X is the
 // FP32 skeleton weights in node order. A thread owns one column and 8 consecutive
 // rows: one 16-byte chunk of each tile. FP64 arithmetic is 1/64 rate on this GPU, so
-// the split itself is done in FP32 after one scaled conversion (24 bits kept, 22
-// needed); the scale is a power of two, so scaling an FP32 value is exact.
+// the split itself is done in FP32 after one conversion (24 bits kept, 22 needed),
+// scaled in FP32: the scale is a power of two, so RN32(v) * 2^k = RN32(v * 2^k) unless
+// RN32(v) is subnormal, and such values (|v| < 2^-126) scale to below half the smallest
+// FP16 subnormal (both sides give 0) for every k <= 100; larger k take the FP64 path.
 template <typename T>
 __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__ X, const int64_t* __restrict__ perm,
                                                int64_t q, int n_t, int n_ct,
@@ -304,6 +326,7 @@ __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__
   const int k_x = scale_exponent(__longlong_as_double((long long)*xmax));
   const double sd = ldexp(1.0, k_x);
   const float sf = (float)sd;
+  const bool f32_scale = k_x <= 100;
   const int64_t q0 = (int64_t)ct * n_t;
   uint8_t* hi_t = out + (g * n_ct + ct) * (int64_t)(2 * n_t * 128);
   uint8_t* lo_t = hi_t + n_t * 128;
@@ -326,8 +349,9 @@ __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__
       if (src >= 0 && gq < q) {
         const T v = X[src * q + gq];
         if constexpr (sizeof(T) == 8) {
-          xs = __double2float_rn((double)v * sd);
-          if (x32) x32[(row0 + k) * q + gq] = __double2float_rn((double)v);
+          const float f = __double2float_rn((double)v);
+          xs = f32_scale ? f * sf : __double2float_rn((double)v * sd);
+          if (x32) x32[(row0 + k) * q + gq] = f;
         } else {
           xs = (float)v * sf;
         }
@@ -583,6 +607,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
     const int k_a = a.tc.scale[a.tc.mt_base[tgt] + mt];
     const int k_x = scale_exponent(__longlong_as_double((long long)*a.bmax));
     const double sc = ldexp(1.0, -(k_a + k_x));
+    // coupling: FP32 output, combined and scaled in FP32 (exact power-of-two scale while
+    // 2^-(k_a + k_x) is a normal FP32 number); near field: FP64 output, one conversion
+    // fewer by adding the two small terms (|l + v| ~ 2^-11 |hi|) in FP32 first
+    const int e_sc = -(k_a + k_x);
+    const bool f32_out = kFar && e_sc >= -126 && e_sc <= 127;
+    const float scf = f32_out ? __int_as_float((e_sc + 127) << 23) : 0.0f;
     const int64_t out_row = write ? (kFar ? a.tc.begin[tgt] + row : a.perm[a.tc.begin[tgt] + row]) : 0;
     const int64_t c0 = (int64_t)ct * a.n_t + half * 64;
 #pragma unroll
@@ -600,11 +630,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
         const int col = cc * 16 + j;
         const int64_t gc = c0 + col;
         if (write && half * 64 + col < a.n_t && gc < a.q) {
-          const double y = ((double)hi[col] + (double)l[j] + (double)v[j]) * sc;
-          if constexpr (kFar)
-            static_cast<float*>(a.Y)[out_row * a.q + gc] = (float)y;
-          else
-            static_cast<double*>(a.Y)[out_row * a.q + gc] = y;
+          const float t = __fadd_rn(l[j], v[j]);
+          if constexpr (kFar) {
+            static_cast<float*>(a.Y)[out_row * a.q + gc] =
+                f32_out ? __fmul_rn(__fadd_rn(hi[col], t), scf) : (float)(((double)hi[col] + (double)t) * sc);
+          } else {
+            static_cast<double*>(a.Y)[out_row * a.q + gc] = ((double)hi[col] + (double)t) * sc;
+          }
         }
       }
     }
