@@ -5,6 +5,7 @@
 
 #include <cstdint>
 
+#include "hmat_fp.cuh"
 #include "hmat_gemm.cuh"
 
 namespace hmat {
@@ -195,7 +196,13 @@ k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restric
 #pragma unroll
       for (int jj = 0; jj < TN; ++jj) {
         const int64_t c = q0 + tx * TN + jj;
-        if (c < q) dst[c] = task.accumulate ? (TY)(dst[c] + (TY)acc[i][jj]) : (TY)acc[i][jj];
+        if (c >= q) continue;
+        if constexpr (sizeof(TY) == 8) {  // FP64 Y: widened on the integer units, one DADD
+          const double w = widen_f32(acc[i][jj]);
+          dst[c] = task.accumulate ? dst[c] + w : w;
+        } else {
+          dst[c] = task.accumulate ? dst[c] + acc[i][jj] : acc[i][jj];
+        }
       }
     }
   }

@@ -28,6 +28,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "hmat_fp.cuh"
 #include "hmat_internal.h"
 
 namespace hmat {
@@ -309,7 +310,8 @@ __global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t
 // into x32, the FP32 tree-order copy the far field reads. The coupling's X is the
 // FP32 skeleton weights in node order. A thread owns one column and 8 consecutive
 // rows: one 16-byte chunk of each tile. FP64 arithmetic is 1/64 rate on this GPU, so
-// the split itself is done in FP32 after one conversion (24 bits kept, 22 needed),
+// the split itself is done in FP32 after one conversion on the integer units (24 bits
+// kept, 22 needed),
 // scaled in FP32: the scale is a power of two, so RN32(v) * 2^k = RN32(v * 2^k) unless
 // RN32(v) is subnormal, and such values (|v| < 2^-126) scale to below half the smallest
 // FP16 subnormal (both sides give 0) for every k <= 100; larger k take the FP64 path.
@@ -349,7 +351,7 @@ __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__
       if (src >= 0 && gq < q) {
         const T v = X[src * q + gq];
         if constexpr (sizeof(T) == 8) {
-          const float f = __double2float_rn((double)v);
+          const float f = narrow_f64((double)v);
           xs = f32_scale ? f * sf : __double2float_rn((double)v * sd);
           if (x32) x32[(row0 + k) * q + gq] = f;
         } else {
@@ -608,8 +610,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
     const int k_x = scale_exponent(__longlong_as_double((long long)*a.bmax));
     const double sc = ldexp(1.0, -(k_a + k_x));
     // coupling: FP32 output, combined and scaled in FP32 (exact power-of-two scale while
-    // 2^-(k_a + k_x) is a normal FP32 number); near field: FP64 output, one conversion
-    // fewer by adding the two small terms (|l + v| ~ 2^-11 |hi|) in FP32 first
+    // 2^-(k_a + k_x) is a normal FP32 number); near field: FP64 output, the two small
+    // terms (|l + v| ~ 2^-11 |hi|) added in FP32 first, then widened and scaled on the
+    // integer units around one DADD
     const int e_sc = -(k_a + k_x);
     const bool f32_out = kFar && e_sc >= -126 && e_sc <= 127;
     const float scf = f32_out ? __int_as_float((e_sc + 127) << 23) : 0.0f;
@@ -635,7 +638,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
             static_cast<float*>(a.Y)[out_row * a.q + gc] =
                 f32_out ? __fmul_rn(__fadd_rn(hi[col], t), scf) : (float)(((double)hi[col] + (double)t) * sc);
           } else {
-            static_cast<double*>(a.Y)[out_row * a.q + gc] = ((double)hi[col] + (double)t) * sc;
+            static_cast<double*>(a.Y)[out_row * a.q + gc] =
+                scale_pow2(widen_f32(hi[col]) + widen_f32(t), e_sc, sc);
           }
         }
       }

@@ -1,10 +1,45 @@
-// Device capability probe: the FP64 FMA rate of the current GPU, the ceiling of
-// the FP64 evaluation mode (its kernels are bound by DFMA issue on GB300).
+// Device probes: the FP64 FMA rate of the current GPU, the ceiling of the FP64
+// evaluation mode (its kernels are bound by DFMA issue on GB300), and a bitwise check
+// of the integer-unit FP32 <-> FP64 conversions of the mixed mode against the
+// hardware's.
 #include <cuda_runtime.h>
 
+#include "hmat_fp.cuh"
 #include "hmat_internal.h"
 
+using namespace hmat;
+
 namespace {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// Sample i: random bit patterns (every exponent, subnormals, infinities, NaN), every
+// fourth double with its 29 low bits at the rounding tie of the narrowing.
+__global__ void __launch_bounds__(256) k_conv_check(int64_t n, uint64_t seed, unsigned long long* bad) {
+  unsigned long long b_w = 0, b_n = 0, b_s = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t r1 = splitmix64(seed ^ (2 * (uint64_t)i)), r2 = splitmix64(seed ^ (2 * (uint64_t)i + 1));
+    const uint64_t bits = (i & 3) == 0 ? ((r1 & ~0x1FFFFFFFull) | 0x10000000ull) : r1;
+    const double d = __longlong_as_double((long long)bits);
+    const float f = __uint_as_float((uint32_t)r2);
+    const int e = (int)((r2 >> 32) % 601) - 300;
+    const double sc = ldexp(1.0, e);
+    const double w0 = widen_f32(f), w1 = (double)f;
+    const float n0 = narrow_f64(d), n1 = __double2float_rn(d);
+    const double s0 = scale_pow2(d, e, sc), s1 = d * sc;
+    b_w += !(__double_as_longlong(w0) == __double_as_longlong(w1) || (w0 != w0 && w1 != w1));
+    b_n += !(__float_as_uint(n0) == __float_as_uint(n1) || (n0 != n0 && n1 != n1));
+    b_s += !(__double_as_longlong(s0) == __double_as_longlong(s1) || (s0 != s0 && s1 != s1));
+  }
+  if (b_w) atomicAdd(bad, b_w);
+  if (b_n) atomicAdd(bad + 1, b_n);
+  if (b_s) atomicAdd(bad + 2, b_s);
+}
 
 __global__ void __launch_bounds__(256) k_dfma_loop(double* out, int iters, double b, double c) {
   double a[8];
@@ -52,4 +87,24 @@ extern "C" hmat_status hmat_measure_fp64_peak(double* gflops) {
   if (e1) cudaEventDestroy(e1);
   cudaFree(out);
   return st;
+}
+
+extern "C" hmat_status hmat_selftest_conversions(int64_t n, uint64_t seed, int64_t* mismatches) {
+  if (!mismatches || n < 0) return HMAT_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HMAT_ECUDA;
+  unsigned long long* bad = nullptr;
+  if (cudaMalloc((void**)&bad, 3 * sizeof(unsigned long long)) != cudaSuccess) return HMAT_ENOMEM;
+  unsigned long long host[3] = {0, 0, 0};
+  cudaError_t e = cudaMemset(bad, 0, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess && n > 0) {
+    k_conv_check<<<sms * 8, 256>>>(n, seed, bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(host, bad, sizeof(host), cudaMemcpyDeviceToHost);
+  cudaFree(bad);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int i = 0; i < 3; ++i) mismatches[i] = (int64_t)host[i];
+  return HMAT_OK;
 }

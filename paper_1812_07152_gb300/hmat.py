@@ -159,6 +159,7 @@ def library() -> ctypes.CDLL:
         lib.hmat_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.POINTER(HmatTuneReport)]
         lib.hmat_selftest_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        lib.hmat_selftest_conversions.argtypes = [ctypes.c_int64, ctypes.c_uint64, _c_i64p]
         lib.hmat_plan_create.argtypes = [ctypes.POINTER(HmatPlanParams), ctypes.POINTER(ctypes.c_void_p)]
         lib.hmat_plan_build.argtypes = [ctypes.c_void_p, ctypes.POINTER(HmatCompressParams), ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_void_p)]
@@ -170,7 +171,7 @@ def library() -> ctypes.CDLL:
                      "hmat_measure_fp64_peak", "hmat_batch_create", "hmat_batch_eval", "hmat_batch_free",
                      "hmat_server_create", "hmat_server_submit", "hmat_server_wait", "hmat_server_stats",
                      "hmat_server_free", "hmat_autotune", "hmat_selftest_timeout", "hmat_plan_create", "hmat_plan_build",
-                     "hmat_plan_free"):
+                     "hmat_plan_free", "hmat_selftest_conversions"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -354,6 +355,14 @@ def hmat_selftest_timeout(handle: int, limit_ns: int, stream=None) -> None:
     """Enqueue one bounded device wait that runs out after limit_ns and latches
     HMAT_ETIMEOUT in the handle's status word (read it with hmat_status_poll)."""
     _check(library().hmat_selftest_timeout(handle, int(limit_ns), _stream(stream)), "hmat_selftest_timeout")
+
+
+def hmat_selftest_conversions(n: int, seed: int = 0) -> dict:
+    """Bitwise check of the mixed mode's integer-unit FP32 <-> FP64 conversions against the
+    hardware's on n hashed samples; returns the mismatch counts per conversion."""
+    out = (ctypes.c_int64 * 3)()
+    _check(library().hmat_selftest_conversions(int(n), int(seed) & (2**64 - 1), out), "hmat_selftest_conversions")
+    return {"widen": out[0], "narrow": out[1], "scale": out[2]}
 
 
 def hmat_info(handle: int) -> dict:

@@ -154,3 +154,11 @@ def test_eval_host_pipelined_mixed_and_fp64():
             assert np.array_equal(Yh.numpy(), _eval(h, W, hp.HMAT_MODE_FP64))
     finally:
         hp.hmat_free(h)
+
+
+def test_integer_unit_conversions_match_hardware():
+    """The mixed mode widens, narrows and rescales on the integer units (FP64 runs at 1/64
+    rate): bitwise equal to the hardware conversions and multiply on 2^24 hashed samples."""
+    bad = hp.hmat_selftest_conversions(1 << 24, seed=12345)
+    print(f"integer-unit conversions, mismatches on 2^24 samples: {bad}")
+    assert bad == {"widen": 0, "narrow": 0, "scale": 0}
