@@ -303,10 +303,13 @@ hmat_status hmat_measure_fp64_peak(double* gflops);
  * hmat_selftest_conversions - checks, on the current device, the integer-unit
  * conversions the mixed mode uses (binary32 -> binary64 widening, round-to-nearest-
  * even binary64 -> binary32 narrowing, scaling a binary64 value by 2^e) bitwise
- * against the hardware conversion and multiply, on n samples drawn from `seed`
- * (random bit patterns of every exponent class, a quarter of the doubles at a
- * rounding tie, scale exponents in [-300, 300]). mismatches[0..2] receive the
- * number of differing widenings, narrowings and scalings (NaN matches any NaN).
+ * against the hardware conversion and multiply, on n samples: the first 144 pair
+ * special values (signed zeros, infinities, NaN, ends of the normal and subnormal
+ * ranges), the rest are drawn from `seed` (random bit patterns of every exponent
+ * class, a quarter of the doubles at a rounding tie, scale exponents in [-300, 300]).
+ * Each conversion is checked in both of its forms (hardware fallback inline and out
+ * of line); mismatches[0..2] receive the number of differing widenings, narrowings
+ * and scalings over both forms (NaN matches any NaN).
  * Synchronous; HMAT_EINVAL for n < 0 or a null mismatches.
  */
 hmat_status hmat_selftest_conversions(int64_t n, uint64_t seed, int64_t* mismatches);

@@ -351,8 +351,8 @@ __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__
       if (src >= 0 && gq < q) {
         const T v = X[src * q + gq];
         if constexpr (sizeof(T) == 8) {
-          const float f = narrow_f64((double)v);
-          xs = f32_scale ? f * sf : __double2float_rn((double)v * sd);
+          const float f = narrow_f64<true>((double)v);
+          xs = f32_scale ? f * sf : narrow_f64_hw(mul_f64_hw((double)v, sd));
           if (x32) x32[(row0 + k) * q + gq] = f;
         } else {
           xs = (float)v * sf;
@@ -368,6 +368,11 @@ __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__
 }
 
 // ------------------------------------------------------------------ the tensor-core product kernel
+
+// coupling output when 2^-(k_a + k_x) is no normal FP32 number (out of line: see hmat_fp.cuh)
+static __device__ __noinline__ float far_out_hw(float hi, float t, double sc) {
+  return __double2float_rn(((double)hi + (double)t) * sc);
+}
 
 struct TcArgs {
   TcLists tc;
@@ -636,7 +641,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
           const float t = __fadd_rn(l[j], v[j]);
           if constexpr (kFar) {
             static_cast<float*>(a.Y)[out_row * a.q + gc] =
-                f32_out ? __fmul_rn(__fadd_rn(hi[col], t), scf) : (float)(((double)hi[col] + (double)t) * sc);
+                f32_out ? __fmul_rn(__fadd_rn(hi[col], t), scf) : far_out_hw(hi[col], t, sc);
           } else {
             static_cast<double*>(a.Y)[out_row * a.q + gc] =
                 scale_pow2(widen_f32(hi[col]) + widen_f32(t), e_sc, sc);

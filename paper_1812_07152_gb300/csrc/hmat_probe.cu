@@ -18,23 +18,41 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return x ^ (x >> 31);
 }
 
-// Sample i: random bit patterns (every exponent, subnormals, infinities, NaN), every
-// fourth double with its 29 low bits at the rounding tie of the narrowing.
+// Sample i: the first ones special values (signed zeros, infinities, NaN, the ends of
+// the normal and subnormal ranges), then random bit patterns (every exponent class),
+// every fourth double with its 29 low bits at the rounding tie of the narrowing.
+__constant__ uint64_t kSpecial64[] = {0x0ull, 0x8000000000000000ull, 0x7FF0000000000000ull, 0xFFF0000000000000ull,
+                                      0x7FF8000000000000ull, 0x3810000000000000ull, 0x380FFFFFFFFFFFFFull,
+                                      0x47EFFFFFE0000000ull, 0x47EFFFFFF0000000ull, 0x0000000000000001ull,
+                                      0x3FF0000010000000ull, 0x3FF0000030000000ull};
+__constant__ uint32_t kSpecial32[] = {0x0u, 0x80000000u, 0x7F800000u, 0xFF800000u, 0x7FC00000u, 0x00800000u,
+                                      0x007FFFFFu, 0x7F7FFFFFu, 0x00000001u, 0x3F800000u, 0x80800000u, 0x807FFFFFu};
+constexpr int kSpecials = 12;
+
 __global__ void __launch_bounds__(256) k_conv_check(int64_t n, uint64_t seed, unsigned long long* bad) {
   unsigned long long b_w = 0, b_n = 0, b_s = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t r1 = splitmix64(seed ^ (2 * (uint64_t)i)), r2 = splitmix64(seed ^ (2 * (uint64_t)i + 1));
-    const uint64_t bits = (i & 3) == 0 ? ((r1 & ~0x1FFFFFFFull) | 0x10000000ull) : r1;
+    uint64_t r1 = splitmix64(seed ^ (2 * (uint64_t)i)), r2 = splitmix64(seed ^ (2 * (uint64_t)i + 1));
+    if (i < kSpecials * kSpecials) {
+      r1 = kSpecial64[i / kSpecials];
+      r2 = (r2 & 0xFFFFFFFF00000000ull) | kSpecial32[i % kSpecials];
+    }
+    const uint64_t bits = (i & 3) == 0 && i >= kSpecials * kSpecials ? ((r1 & ~0x1FFFFFFFull) | 0x10000000ull) : r1;
     const double d = __longlong_as_double((long long)bits);
     const float f = __uint_as_float((uint32_t)r2);
     const int e = (int)((r2 >> 32) % 601) - 300;
     const double sc = ldexp(1.0, e);
-    const double w0 = widen_f32(f), w1 = (double)f;
-    const float n0 = narrow_f64(d), n1 = __double2float_rn(d);
-    const double s0 = scale_pow2(d, e, sc), s1 = d * sc;
-    b_w += !(__double_as_longlong(w0) == __double_as_longlong(w1) || (w0 != w0 && w1 != w1));
-    b_n += !(__float_as_uint(n0) == __float_as_uint(n1) || (n0 != n0 && n1 != n1));
-    b_s += !(__double_as_longlong(s0) == __double_as_longlong(s1) || (s0 != s0 && s1 != s1));
+    const double w1 = (double)f;
+    const float n1 = __double2float_rn(d);
+    const double s1 = d * sc;
+    const double w0 = widen_f32<false>(f), w0o = widen_f32<true>(f);
+    const float n0 = narrow_f64<false>(d), n0o = narrow_f64<true>(d);
+    const double s0 = scale_pow2<false>(d, e, sc), s0o = scale_pow2<true>(d, e, sc);
+    auto same_d = [](double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b) || (a != a && b != b); };
+    auto same_f = [](float a, float b) { return __float_as_uint(a) == __float_as_uint(b) || (a != a && b != b); };
+    b_w += !same_d(w0, w1) + !same_d(w0o, w1);
+    b_n += !same_f(n0, n1) + !same_f(n0o, n1);
+    b_s += !same_d(s0, s1) + !same_d(s0o, s1);
   }
   if (b_w) atomicAdd(bad, b_w);
   if (b_n) atomicAdd(bad + 1, b_n);
