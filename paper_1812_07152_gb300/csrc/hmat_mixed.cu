@@ -266,42 +266,60 @@ __global__ void k_relayout_f32(const double* __restrict__ arena, const F32Job* _
 // |x| as an unsigned integer that orders like |x| (IEEE magnitudes order as their bit
 // patterns), NaN as 0 so that it sets no scale: the maximum then runs on the integer
 // units (FP64 compares and conversions run at 1/64 rate on this GPU).
-__device__ __forceinline__ uint64_t abs_key(double x) {
-  const uint64_t b = (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+__device__ __forceinline__ uint64_t abs_key_bits(uint64_t bits) {
+  const uint64_t b = bits & 0x7FFFFFFFFFFFFFFFull;
   return b <= 0x7FF0000000000000ull ? b : 0;
 }
-__device__ __forceinline__ uint32_t abs_key(float x) {
-  const uint32_t b = __float_as_uint(x) & 0x7FFFFFFFu;
+__device__ __forceinline__ uint32_t abs_key_bits(uint32_t bits) {
+  const uint32_t b = bits & 0x7FFFFFFFu;
   return b <= 0x7F800000u ? b : 0;
 }
+__device__ __forceinline__ uint64_t abs_key(double x) { return abs_key_bits((uint64_t)__double_as_longlong(x)); }
+__device__ __forceinline__ uint32_t abs_key(float x) { return abs_key_bits(__float_as_uint(x)); }
 __device__ __forceinline__ double key_value(uint64_t k) { return __longlong_as_double((long long)k); }
 __device__ __forceinline__ double key_value(uint32_t k) { return (double)__uint_as_float(k); }
 
+// max |X| over n values: 16-byte loads, four in flight per thread and iteration (few
+// registers, so that every SM holds enough loads in flight to stream at HBM rate)
 template <typename T>
 __global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t n,
                                                 unsigned long long* __restrict__ out) {
   using Key = decltype(abs_key(T{}));
-  // four independent coalesced loads in flight per thread and iteration
-  Key m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+  constexpr int kPer = 16 / (int)sizeof(T);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  auto upd = [](Key& m, T x) {
-    const Key k = abs_key(x);
-    m = k > m ? k : m;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n_vec = ((uintptr_t)X & 15u) == 0 ? n / kPer : 0;
+  const uint4* V = reinterpret_cast<const uint4*>(X);
+  Key m = 0;
+  auto upd = [&m](const uint4& u) {
+    Key k[kPer];
+    if constexpr (sizeof(T) == 8) {
+      k[0] = abs_key_bits((uint64_t)u.x | ((uint64_t)u.y << 32));
+      k[1] = abs_key_bits((uint64_t)u.z | ((uint64_t)u.w << 32));
+    } else {
+      k[0] = abs_key_bits(u.x);
+      k[1] = abs_key_bits(u.y);
+      k[2] = abs_key_bits(u.z);
+      k[3] = abs_key_bits(u.w);
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) m = k[j] > m ? k[j] : m;
   };
-  for (; i + 3 * stride < n; i += 4 * stride) {
-    const T a0 = X[i], a1 = X[i + stride], a2 = X[i + 2 * stride], a3 = X[i + 3 * stride];
-    upd(m0, a0);
-    upd(m1, a1);
-    upd(m2, a2);
-    upd(m3, a3);
+  int64_t i = tid;
+  for (; i + 3 * stride < n_vec; i += 4 * stride) {
+    const uint4 a = V[i], b = V[i + stride], c = V[i + 2 * stride], d = V[i + 3 * stride];
+    upd(a);
+    upd(b);
+    upd(c);
+    upd(d);
   }
-  for (; i < n; i += stride) upd(m0, X[i]);
-  m0 = m0 > m1 ? m0 : m1;
-  m2 = m2 > m3 ? m2 : m3;
-  double m = key_value(m0 > m2 ? m0 : m2);
-  m = block_max_d(m);
-  if (threadIdx.x == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+  for (; i < n_vec; i += stride) upd(V[i]);
+  for (int64_t j = n_vec * kPer + tid; j < n; j += stride) {
+    const Key k = abs_key(X[j]);
+    m = k > m ? k : m;
+  }
+  const double mm = block_max_d(key_value(m));
+  if (threadIdx.x == 0 && mm > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(mm));
 }
 
 // One (source k-chunk, column tile): 64 rows of X x n_t columns -> B-operand tiles:
@@ -331,7 +349,9 @@ __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__
   const bool f32_scale = k_x <= 100;
   const int64_t q0 = (int64_t)ct * n_t;
   uint8_t* hi_t = out + (g * n_ct + ct) * (int64_t)(2 * n_t * 128);
-  uint8_t* lo_t = hi_t + n_t * 128;
+  // the tile pair is assembled in shared memory and written out with linear 16-byte
+  // stores (a thread's own chunks are one per 128-byte row)
+  __shared__ __align__(128) uint8_t tile[2 * kMaxNt * 128];
   // the chunk's source rows, looked up once (each X load then waits on shared memory only)
   __shared__ int64_t src_row[kTcK];
   if (threadIdx.x < kTcK) {
@@ -362,9 +382,13 @@ __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__
       lv[t] = __float2half_rn(xs - __half2float(hv[t]));
     }
     const int off = sw128_chunk(n, kc);
-    *reinterpret_cast<uint4*>(hi_t + off) = *reinterpret_cast<const uint4*>(hv);
-    *reinterpret_cast<uint4*>(lo_t + off) = *reinterpret_cast<const uint4*>(lv);
+    *reinterpret_cast<uint4*>(tile + off) = *reinterpret_cast<const uint4*>(hv);
+    *reinterpret_cast<uint4*>(tile + n_t * 128 + off) = *reinterpret_cast<const uint4*>(lv);
   }
+  __syncthreads();
+  const uint4* src = reinterpret_cast<const uint4*>(tile);
+  uint4* dst = reinterpret_cast<uint4*>(hi_t);
+  for (int i = threadIdx.x; i < n_t * 16; i += blockDim.x) dst[i] = src[i];
 }
 
 // ------------------------------------------------------------------ the tensor-core product kernel
