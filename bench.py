@@ -51,6 +51,8 @@ def parse_args():
                          "(short: 4 matrices N = 16K..128K, 6 s; full: 8 matrices N = 16K..1M, 2000 req/s, 60 s)")
     ap.add_argument("--precision", choices=["on", "off"], default="on",
                     help="time the precision-mode recipe (N=262144 inverse multiquadric, q=512), FP64 vs mixed")
+    ap.add_argument("--otf", choices=["on", "off"], default="on",
+                    help="near blocks evaluated on the fly (FP64) on the headline recipe")
     ap.add_argument("--matvec", choices=["on", "off"], default="on",
                     help="time the matrix-vector recipe (N=262144, kernel 1/r, q=1), FP64 vs mixed")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
@@ -305,6 +307,8 @@ def run_gpu(args, dist: Dist) -> None:
     dev.close()
 
     line["inspector_reuse"] = run_inspector_reuse(w, X)
+    if args.otf == "on":
+        line["near_on_the_fly"] = run_near_otf(w, X, dist, ms, info)
     if args.precision == "on":
         line["precision"] = run_precision(args, dist)
     if args.matvec == "on":
@@ -393,6 +397,46 @@ def run_inspector_reuse(w, X) -> dict:
     finally:
         hp.hmat_plan_free(plan)
     return out
+
+
+def run_near_otf(w, X, dist, stored_ms, stored_info) -> dict:
+    """Near blocks evaluated on the fly (HMAT_BUILD_NEAR_OTF) on the headline recipe, FP64 mode: the
+    handle holds the points instead of the near blocks; time per evaluation (autotuned, 2 steps after
+    a warm-up) against the stored form, and the device bytes each holds."""
+    import torch
+    import paper_1812_07152_gb300 as hp
+    from workloads import normal_rhs
+    q = w.q
+    t0 = time.perf_counter()
+    h = hp.hmat_build(X, flags=hp.HMAT_BUILD_NEAR_OTF, **build_params(w))
+    t_build = time.perf_counter() - t0
+    try:
+        info = hp.hmat_info(h)
+        stream = torch.cuda.current_stream()
+        W = torch.from_numpy(normal_rhs(w.n, q, w.rhs_seed)).cuda()
+        Y = torch.empty_like(W)
+        tune = hp.hmat_autotune(h, q, hp.HMAT_MODE_FP64, stream)
+        hp.hmat_eval(h, W, Y, q, hp.HMAT_MODE_FP64, stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        steps = 2
+        e0.record(stream)
+        for _ in range(steps):
+            hp.hmat_eval(h, W, Y, q, hp.HMAT_MODE_FP64, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = dist.max(e0.elapsed_time(e1) / steps)
+        if hp.hmat_status_poll(h) != hp.HMAT_OK:
+            raise RuntimeError("device status error in the on-the-fly steps")
+        return {"mode": "fp64", "value": round(dist.world * q / (ms / 1e3), 3), "unit": "cols/s",
+                "ms_per_step": round(ms, 3), "steps": steps, "stored_ms_per_step": round(stored_ms, 3),
+                "device_bytes": info["device_bytes"], "near_block_bytes_not_held": 8 * info["near_values"],
+                "stored_handle_device_bytes_incl_mixed_copy": stored_info["device_bytes"],
+                "build_s": round(t_build, 2), "autotune": tune}
+    finally:
+        hp.hmat_free(h)
 
 
 def run_precision(args, dist) -> dict:

@@ -156,7 +156,10 @@ typedef struct {
  * children's skeletons otherwise; C = the points whose interaction with the node
  * is approximated, or a seeded uniform sample of max(4 max_rank, 512) of them).
  * The near blocks D and coupling blocks B are evaluated on the GPU directly into
- * the packed device arena. Synchronous; host threads as requested.
+ * the packed device arena (with HMAT_BUILD_NEAR_OTF the near blocks are not stored
+ * but evaluated inside every FP64 evaluation). `flags`: any of HMAT_LOAD_MIXED,
+ * HMAT_BUILD_ID_GPU, HMAT_BUILD_NEAR_OTF (not with HMAT_LOAD_MIXED); other bits:
+ * HMAT_EUNSUPPORTED. Synchronous; host threads as requested.
  */
 hmat_status hmat_build(const hmat_build_params* params, int flags, hmat_t* out);
 
@@ -218,6 +221,15 @@ hmat_status hmat_structure(hmat_t h, int64_t* perm, int32_t* rank, int64_t* near
    per node of a tree level (same algorithm as on the host; sums in another order, so a
    pivot may differ where two candidates are within rounding of each other). */
 #define HMAT_BUILD_ID_GPU 2
+
+/* Build flag (hmat_build, hmat_plan_build): the near blocks D_ij are not stored. The
+   FP64 near field evaluates each entry K(x_i, x_j) from the points inside its kernel,
+   with the formula the build uses to store them, so the result is bitwise that of a
+   handle built without the flag; the handle keeps the points (8 B x dim per point)
+   instead of the near blocks (8 B per near value), and pays the kernel evaluations in
+   time, once per column tile of the product. FP64 mode only: with HMAT_LOAD_MIXED the
+   build returns HMAT_EUNSUPPORTED, and so does hmat_load (it has no points). */
+#define HMAT_BUILD_NEAR_OTF 4
 
 /* Load flags (hmat_load, hmat_build). */
 #define HMAT_LOAD_MIXED 1           /* also keep the tensor-core copy of the near blocks (FP16 hi/lo,
@@ -458,12 +470,14 @@ hmat_status hmat_status_poll(hmat_t h, void* stream);
 hmat_status hmat_selftest_timeout(hmat_t h, int64_t limit_ns, void* stream);
 
 /* hmat_info - sizes of the loaded HMatrix: out[0] = n_points, out[1] = levels,
- * out[2] = near entries, out[3] = far entries, out[4] = stored near values,
+ * out[2] = near entries, out[3] = far entries, out[4] = near values (stored, or
+ * evaluated on the fly under HMAT_BUILD_NEAR_OTF, see out[10]),
  * out[5] = stored basis values, out[6] = stored coupling values,
  * out[7] = sum of ranks, out[8] = device bytes held by the handle,
  * out[9] = engine of the mixed mode's coupling reduction: 0 no mixed copy, 1 FP32
  * CUDA cores, 2 tensor cores (chosen at load: tensor cores when the stored coupling
- * values fill at least a quarter of the padded 128 x 64 tiles they would occupy). */
+ * values fill at least a quarter of the padded 128 x 64 tiles they would occupy),
+ * out[10] = 1 when the near blocks are evaluated on the fly, else 0. */
 hmat_status hmat_info(hmat_t h, int64_t* out, int n_out);
 
 /* hmat_free - release every device and host resource of the handle (synchronises the device). */

@@ -210,6 +210,8 @@ void free_device(Handle* h) {
   cudaFree(h->entries32);
   h->arena32 = nullptr; h->entries32 = nullptr; h->has_mixed = false;
   cudaFree(h->arena);
+  cudaFree(h->pts_tree);
+  h->pts_tree = nullptr;
   cudaFree(h->far_rows);
   h->far_rows = nullptr;
   cudaFree(h->perm);
@@ -467,7 +469,10 @@ hmat_status cuda_status(cudaError_t e) {
 
 hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flags, hmat_handle** out) {
   *out = nullptr;
-  if (flags & ~HMAT_LOAD_MIXED) return HMAT_EUNSUPPORTED;
+  if (flags & ~(HMAT_LOAD_MIXED | HMAT_BUILD_NEAR_OTF)) return HMAT_EUNSUPPORTED;
+  // blocks evaluated on the fly need the points (a build), and the FP64 mode
+  if ((flags & HMAT_BUILD_NEAR_OTF) && (!src || (flags & HMAT_LOAD_MIXED))) return HMAT_EUNSUPPORTED;
+  const bool near_otf = (flags & HMAT_BUILD_NEAR_OTF) != 0;
   Validated v;
   hmat_status st = validate(d, src == nullptr, &v);
   if (st != HMAT_OK) return st;
@@ -503,10 +508,10 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
   int64_t off = 0;
   for (int64_t i = 0; i < v.n_leaves; ++i)
     for (int64_t e = d->near_ptr[i]; e < d->near_ptr[i + 1]; ++e) {
-      near_off[e] = off;
       const int64_t cnt = h->size[fl + i] * h->size[fl + d->near_idx[e]];
       h->near_values += cnt;
-      off = align_up(off + cnt, kAlignValues);
+      near_off[e] = near_otf ? 0 : off;  // on the fly: nothing stored, the offset unused
+      if (!near_otf) off = align_up(off + cnt, kAlignValues);
     }
   for (int64_t a = 0; a < v.n_nodes; ++a) {
     if (h->rank[a] == 0) continue;
@@ -719,9 +724,9 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     if (ce != cudaSuccess) return fail(ce);
     if (!finite) { free_device(h.get()); return HMAT_EINVAL; }
   }
-  if (src) {  // evaluate D and B on the device from the points
+  if (src) {  // evaluate D (unless on the fly) and B on the device from the points
     std::vector<BlockJob> jobs;
-    for (int64_t i = 0; i < v.n_leaves; ++i)
+    for (int64_t i = 0; i < v.n_leaves && !near_otf; ++i)
       for (int64_t ee = d->near_ptr[i]; ee < d->near_ptr[i + 1]; ++ee) {
         const int64_t a = fl + i, b = fl + d->near_idx[ee];
         if (h->size[a] * h->size[b] == 0) continue;
@@ -748,7 +753,16 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
       ce = launch_eval_blocks(djobs, (int64_t)jobs.size(), dpts, src->dim, dskel, src->kernel, src->kernel_param,
                               h->arena, 0);
     if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
-    cudaFree(dpts);
+    if (ce == cudaSuccess && near_otf) {  // the near field keeps the points
+      h->near_otf = true;
+      h->pts_tree = dpts;
+      h->dim = src->dim;
+      h->kernel = src->kernel;
+      h->kernel_param = src->kernel_param;
+      h->device_bytes += (int64_t)pts.size() * (int64_t)sizeof(double);
+    } else {
+      cudaFree(dpts);
+    }
     cudaFree(dskel);
     cudaFree(djobs);
     if (ce != cudaSuccess) return fail(ce);
@@ -824,9 +838,10 @@ extern "C" hmat_status hmat_info(hmat_t h, int64_t* out, int n_out) {
   if (!h || !out || n_out < 0) return HMAT_EINVAL;
   const int64_t held = h->device_bytes + (h->ctx ? h->ctx->block_bytes + 16 * h->ctx->host_cap : 0);
   const int64_t engine = !h->has_mixed ? 0 : (h->tc_coupling ? 2 : 1);
-  const int64_t vals[10] = {h->n_points, h->levels, h->n_near, h->n_far, h->near_values,
-                            h->basis_values, h->coupling_values, h->sum_rank, held, engine};
-  for (int i = 0; i < n_out && i < 10; ++i) out[i] = vals[i];
+  const int64_t vals[11] = {h->n_points, h->levels,          h->n_near,          h->n_far,
+                            h->near_values, h->basis_values, h->coupling_values, h->sum_rank,
+                            held,           engine,          h->near_otf ? 1 : 0};
+  for (int i = 0; i < n_out && i < 11; ++i) out[i] = vals[i];
   return HMAT_OK;
 }
 

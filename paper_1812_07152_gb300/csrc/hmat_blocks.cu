@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "hmat_internal.h"
+#include "hmat_kernels.cuh"
 
 namespace hmat {
 namespace {
@@ -17,27 +18,12 @@ k_eval_blocks(const BlockJob* __restrict__ jobs, const double* __restrict__ pts,
   const BlockJob job = jobs[blockIdx.x];
   double* out = arena + job.a_off;
   const int64_t total = (int64_t)job.rows * job.cols;
-  const double two_h2 = 2.0 * param * param;
-  const double c2 = param * param;
+  const KernelSpec ks = kernel_spec(kernel, param);
   for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
     const int r = (int)(e / job.cols), c = (int)(e % job.cols);
     const int64_t pr = job.row_skel ? skel[job.row_off + r] : job.row_off + r;
     const int64_t pc = job.col_skel ? skel[job.col_off + c] : job.col_off + c;
-    const double* x = pts + pr * dim;
-    const double* y = pts + pc * dim;
-    double r2 = 0.0;
-    for (int k = 0; k < dim; ++k) {
-      const double diff = x[k] - y[k];
-      r2 = __dadd_rn(r2, __dmul_rn(diff, diff));
-    }
-    double k;
-    if (kernel == HMAT_KERNEL_GAUSSIAN)
-      k = exp(-r2 / two_h2);
-    else if (kernel == HMAT_KERNEL_IMQ)
-      k = 1.0 / sqrt(r2 + c2);
-    else
-      k = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;  // 1/r, 0 for coincident points
-    out[r * job.ld + c] = k;
+    out[r * job.ld + c] = kernel_entry(ks, pts + pr * dim, pts + pc * dim, dim);
   }
 }
 

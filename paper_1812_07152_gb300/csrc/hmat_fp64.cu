@@ -13,6 +13,8 @@ namespace hmat {
 cudaError_t launch_fp64_phase(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map,
                               double* Y, const int64_t* y_map, int64_t q, int shape, int64_t n_tiles,
                               cudaStream_t stream) {
+  if (h.near_otf && ph.kind == PH_NEAR)  // hmat_fp64_otf.cu
+    return launch_fp64_near_otf(h, ph, X, x_map, Y, y_map, q, shape, n_tiles, stream);
   return gemm::launch_phase<double, double, double, double>(h, ph, shape, n_tiles, h.arena, 0, X, x_map, Y, y_map,
                                                             q, stream);
 }

@@ -9,9 +9,25 @@
 #include <cuda_runtime.h>
 
 #include "hmat_internal.h"
+#include "hmat_kernels.cuh"
 
 namespace hmat {
 namespace gemm {
+
+// Near blocks evaluated on the fly: A(m, k) of a near entry is K(x_{out_row + m},
+// x_{x_row + k}) over the tree-ordered points.
+struct OtfArgs {
+  const double* pts;
+  int32_t dim;
+  KernelSpec ks;
+};
+
+// out of line: inlined into every unrolled operand load of every tile shape, the kernel
+// functions made the translation unit take minutes to compile; an entry costs tens of
+// FP64 operations, so the call adds little
+static __device__ __noinline__ double otf_entry(const OtfArgs& otf, int64_t row, int64_t col) {
+  return kernel_entry(otf.ks, otf.pts + row * otf.dim, otf.pts + col * otf.dim, otf.dim);
+}
 
 constexpr int BK = 16;   // depth of one operand chunk
 constexpr int TM = 4;    // FP32 kernel: outputs per thread, TM rows x TN columns
@@ -41,13 +57,14 @@ __device__ __forceinline__ int64_t map_row(const int64_t* __restrict__ m, int64_
 //
 // TA: stored block type, TX / TY: input / output matrix types, TC: the type of the
 // products and sums. Entry offsets index the FP64 arena; a_shift maps them into an
-// arena that holds only the values from a_shift on (the FP32 far-field copy).
-template <typename TA, typename TX, typename TY, typename TC, int BM, int BN, int CTM, int CTN>
+// arena that holds only the values from a_shift on. kOtf: the blocks are not read but
+// evaluated from the points (`otf`), entry by entry, as the build evaluates them.
+template <typename TA, typename TX, typename TY, typename TC, int BM, int BN, int CTM, int CTN, bool kOtf>
 __global__ void __launch_bounds__(Cfg<BM, BN, CTM, CTN>::kThreads)
 k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
                const GemmEntry* __restrict__ entries, const TA* __restrict__ arena, int64_t a_shift,
                const TX* X, const int64_t* __restrict__ x_map,
-               TY* Y, const int64_t* __restrict__ y_map, int64_t q, int n_col_tiles) {
+               TY* Y, const int64_t* __restrict__ y_map, int64_t q, int n_col_tiles, OtfArgs otf) {
   using C = Cfg<BM, BN, CTM, CTN>;
   constexpr int NT = C::kThreads;
   constexpr int TM = CTM, TN = CTN;
@@ -83,8 +100,12 @@ k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ 
       if (en.trans) { k = idx / BM; m = idx % BM; } else { m = idx / BK; k = idx % BK; }
       const int gm = m0 + m, gk = kk0 + k;
       TC v = TC(0);
-      if (gm < task.m && gk < en.k)
-        v = (TC)(en.trans ? a[(int64_t)gk * en.lda + gm] : a[(int64_t)gm * en.lda + gk]);
+      if (gm < task.m && gk < en.k) {
+        if constexpr (kOtf)
+          v = (TC)otf_entry(otf, task.out_row + gm, en.x_row + gk);
+        else
+          v = (TC)(en.trans ? a[(int64_t)gk * en.lda + gm] : a[(int64_t)gm * en.lda + gk]);
+      }
       ra[t] = v;
     }
 #pragma unroll
@@ -154,14 +175,16 @@ k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ 
   }
 }
 
-template <typename TA, typename TX, typename TY, typename TC, int BM, int BN, int CTM, int CTN>
+template <typename TA, typename TX, typename TY, typename TC, int BM, int BN, int CTM, int CTN, bool kOtf>
 cudaError_t launch(const Handle& h, const Phase& ph, int64_t n_tiles, const TA* arena, int64_t a_shift, const TX* X,
                    const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q, cudaStream_t s) {
   const int64_t n_col = (q + BN - 1) / BN;
   const int64_t blocks = n_tiles * n_col;
   if (blocks > 2147483647LL) return cudaErrorInvalidValue;
-  k_grouped_gemm<TA, TX, TY, TC, BM, BN, CTM, CTN><<<(unsigned)blocks, Cfg<BM, BN, CTM, CTN>::kThreads, 0, s>>>(
-      h.tiles + ph.tile_begin, h.tasks, h.entries, arena, a_shift, X, x_map, Y, y_map, q, (int)n_col);
+  if (kOtf && !h.pts_tree) return cudaErrorInvalidValue;
+  const OtfArgs otf{h.pts_tree, h.dim, kernel_spec(h.kernel, h.kernel_param)};
+  k_grouped_gemm<TA, TX, TY, TC, BM, BN, CTM, CTN, kOtf><<<(unsigned)blocks, Cfg<BM, BN, CTM, CTN>::kThreads, 0, s>>>(
+      h.tiles + ph.tile_begin, h.tasks, h.entries, arena, a_shift, X, x_map, Y, y_map, q, (int)n_col, otf);
   return cudaGetLastError();
 }
 
@@ -176,7 +199,7 @@ inline int default_col_shape(int64_t q) {
 // into kColBN, or -1 for the default) the column tile. `n_tiles` (at most the phase's)
 // limits the launch to the first tiles of the phase, the longest ones (the tuner times
 // such prefixes of long phases).
-template <typename TA, typename TX, typename TY, typename TC>
+template <typename TA, typename TX, typename TY, typename TC, bool kOtf = false>
 cudaError_t launch_phase(const Handle& h, const Phase& ph, int shape, int64_t n_tiles, const TA* arena,
                          int64_t a_shift, const TX* X, const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q,
                          cudaStream_t s) {
@@ -186,7 +209,7 @@ cudaError_t launch_phase(const Handle& h, const Phase& ph, int shape, int64_t n_
   if (shape < 0) shape = default_col_shape(q);
   if (shape >= kColShapes) return cudaErrorInvalidValue;
 #define HMAT_GEMM_L(BMV, BNV, TMV, TNV) \
-  return launch<TA, TX, TY, TC, BMV, BNV, TMV, TNV>(h, ph, n_tiles, arena, a_shift, X, x_map, Y, y_map, q, s)
+  return launch<TA, TX, TY, TC, BMV, BNV, TMV, TNV, kOtf>(h, ph, n_tiles, arena, a_shift, X, x_map, Y, y_map, q, s)
 #define HMAT_GEMM_BN(BMV)                      \
   switch (shape) {                             \
     case 0: HMAT_GEMM_L(BMV, 1, 1, 1);         \

@@ -202,6 +202,14 @@ struct Handle {
                                  // of 4 (rows m..lda-1 zero), a_off a multiple of 4
   GemmEntry* entries32 = nullptr;  // the entries with a_off/lda into arena32 (trans = 1)
 
+  // near blocks evaluated on the fly (HMAT_BUILD_NEAR_OTF): the arena holds no near
+  // blocks; the near phase computes K(x_i, x_j) from the tree-ordered points
+  bool near_otf = false;
+  double* pts_tree = nullptr;  // device, n_points x dim, tree order
+  int32_t dim = 0;
+  int32_t kernel = 0;
+  double kernel_param = 0.0;
+
   struct EvalContext* ctx = nullptr;  // the handle's own evaluation state (hmat_eval)
   std::vector<TuneEntry> tuned;       // hmat_autotune results, one per (q, mode)
 
@@ -321,6 +329,9 @@ hmat_status cuda_status(cudaError_t e);
 cudaError_t launch_fp64_phase(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map,
                               double* Y, const int64_t* y_map, int64_t q, int shape, int64_t n_tiles,
                               cudaStream_t stream);
+// the near phase of a handle built with HMAT_BUILD_NEAR_OTF (hmat_fp64_otf.cu)
+cudaError_t launch_fp64_near_otf(const Handle& h, const Phase& ph, const double* X, const int64_t* x_map, double* Y,
+                                 const int64_t* y_map, int64_t q, int shape, int64_t n_tiles, cudaStream_t stream);
 int fp64_default_shape(int64_t q);
 int fp64_shape_columns(int shape);
 

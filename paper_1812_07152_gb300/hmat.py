@@ -65,6 +65,7 @@ HMAT_ADM_NONE = 2
 HMAT_ADM_TAU = 3
 HMAT_ADM_BUDGET = 4
 HMAT_BUILD_ID_GPU = 2
+HMAT_BUILD_NEAR_OTF = 4
 HMAT_TREE_KD = 0
 HMAT_TREE_TWO_MEANS = 1
 
@@ -366,10 +367,10 @@ def hmat_selftest_conversions(n: int, seed: int = 0) -> dict:
 
 
 def hmat_info(handle: int) -> dict:
-    out = (ctypes.c_int64 * 10)()
-    _check(library().hmat_info(handle, out, 10), "hmat_info")
+    out = (ctypes.c_int64 * 11)()
+    _check(library().hmat_info(handle, out, 11), "hmat_info")
     keys = ("n_points", "levels", "near_entries", "far_entries", "near_values", "basis_values",
-            "coupling_values", "sum_rank", "device_bytes", "coupling_engine")
+            "coupling_values", "sum_rank", "device_bytes", "coupling_engine", "near_on_the_fly")
     return dict(zip(keys, [int(v) for v in out]))
 
 
