@@ -55,6 +55,8 @@ def parse_args():
                     help="near blocks evaluated on the fly (FP64) on the headline recipe")
     ap.add_argument("--matvec", choices=["on", "off"], default="on",
                     help="time the matrix-vector recipe (N=262144, kernel 1/r, q=1), FP64 vs mixed")
+    ap.add_argument("--hss", choices=["on", "off"], default="on",
+                    help="time the latency-bound HSS recipe (N=2048, q=16, FP64): microseconds per evaluation")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
     return ap.parse_args()
 
@@ -285,7 +287,7 @@ def run_gpu(args, dist: Dist) -> None:
             "parallelism": f"replicas x{dist.world}",
         },
         "gflops": round(total_flops / (ms / 1e3) / 1e9, 2),
-        "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
+        "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items() if v[1] > 0},
         "roofline": {
             "bound": "alu", "kernel": "k_grouped_gemm<double> (near field, tuned column tile)",
             "launches_per_eval": near_launches // args.steps,
@@ -293,7 +295,8 @@ def run_gpu(args, dist: Dist) -> None:
             "frac": round(achieved_tflops / (peak_gflops / 1e3), 4),
             "traffic": measured_traffic("fp64_near", info["near_values"]),
             "peak_source": "FP64 DFMA loop measured in this run (hmat_measure_fp64_peak); nominal 1.25",
-            "step_bytes": bytes_step, "step_hbm_bound_ms": round(bytes_step / 6797.2e9 * 1e3, 3),
+            "step_bytes": bytes_step,
+            "step_hbm_bound_ms": round(bytes_step / (measured_peaks()["hbm_gbs"] * 1e9) * 1e3, 3),
         },
         "e2e": {"value": round(e2e_value, 3), "unit": "cols/s", "h2d_bytes_per_step": int(W_host.numel() * 8),
                 "d2h_bytes_per_step": int(Y_host.numel() * 8)},
@@ -310,10 +313,12 @@ def run_gpu(args, dist: Dist) -> None:
     if args.otf == "on":
         line["near_on_the_fly"] = run_near_otf(w, X, dist, ms, info)
     if args.precision == "on":
-        line["precision"] = run_precision(args, dist)
+        line["precision"] = run_precision(args, dist, peak_gflops)
     if args.matvec == "on":
         line["matvec"] = run_matvec(args, dist, peak_gflops)
 
+    if args.hss == "on":
+        line["hss"] = run_hss(args, dist)
     if args.batch == "on":
         line["batch"] = run_batch(args, dist)
     if args.serve != "off":
@@ -353,27 +358,60 @@ def run_mixed(args, dev, W, Y64, q, info, stream, dist) -> dict:
     if dev.poll() != hp.HMAT_OK:
         raise RuntimeError("device status error during the mixed-precision steps")
     err = float(torch.linalg.norm(Ym - Y64) / torch.linalg.norm(Y64))
-    near_ms = phases["near"][0] / args.steps
+    serial = serial_phases(dev.handle, W, Ym, q, hp.HMAT_MODE_MIXED, stream, args.steps)
+    roof = tc_near_roofline(info, q, serial["near"])
+    roof["near_ms_beside_far_chain"] = round(phases["near"][0] / args.steps, 4)
+    return {"value": round(dist.world * q / (ms / 1e3), 3), "unit": "cols/s", "ms_per_step": round(ms, 4),
+            "error_vs_fp64": err, "dtype": "f16 hi+lo split, f32 accumulate",
+            "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items() if v[1] > 0},
+            "phases_serialised_ms_per_step": serial,
+            "launches_per_eval": sum(c for _, c in phases.values()) // args.steps,
+            "gpu_launches": sum(c for _, c in phases.values()), "roofline": roof, "autotune": tune}
+
+
+def serial_phases(dev_handle, W, Y, q, mode, stream, steps: int) -> dict:
+    """Per-launch device times with the mixed mode's far chain serialised on the caller's stream (hmat_profile
+    mode 2), so that each launch is timed alone: {phase: ms per evaluation}."""
+    import torch
+    import paper_1812_07152_gb300 as hp
+    hp.hmat_profile(dev_handle, 2)
+    for _ in range(steps):
+        hp.hmat_eval(dev_handle, W, Y, q, mode, stream)
+    torch.cuda.synchronize()
+    ph = hp.hmat_phase_times(dev_handle)
+    hp.hmat_profile(dev_handle, False)
+    return {k: round(v[0] / steps, 4) for k, v in ph.items() if v[1] > 0}
+
+
+def tc_near_roofline(info, q: int, near_ms: float) -> dict:
+    """Roofline of the tensor-core near field (k_tc<0>) over one evaluation: executed flops (three FP16
+    products per stored value), useful flops (one product, what the FP64 form computes) and the algorithmic
+    bytes (D hi/lo once, the W split once, Y written once in FP64), each against its measured peak."""
     nv = info["near_values"]
-    exec_flops = 3 * 2.0 * q * nv                       # three FP16 products per stored value
-    alg_bytes = 4.0 * nv + 4.0 * w_rows(info) * q + 8.0 * w_rows(info) * q   # D hi/lo once, W split once, Y once
+    n = w_rows(info)
+    exec_flops = 3 * 2.0 * q * nv
+    useful_flops = 2.0 * q * nv
+    alg_bytes = 4.0 * nv + 4.0 * n * q + 8.0 * n * q
     peaks = measured_peaks()
     t_tensor = exec_flops / (peaks["bf16_tflops"] * 1e12) * 1e3
     t_hbm = alg_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
+    sec = near_ms / 1e3
+    tensor_achieved = exec_flops / sec / 1e12
+    hbm_achieved = alg_bytes / sec / 1e9
     if t_tensor >= t_hbm:
-        roof = {"bound": "tensor", "achieved": round(exec_flops / (near_ms / 1e3) / 1e12, 2),
-                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s"}
+        roof = {"bound": "tensor", "achieved": round(tensor_achieved, 2), "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s"}
     else:
-        roof = {"bound": "hbm", "achieved": round(alg_bytes / (near_ms / 1e3) / 1e9, 1), "peak": peaks["hbm_gbs"],
-                "unit": "GB/s"}
+        roof = {"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     roof.update({"frac": round(roof["achieved"] / roof["peak"], 4),
-                 "traffic": measured_traffic("mixed_near", nv), "algorithmic_bytes": alg_bytes,
-                 "kernel": "k_tc<0> (tcgen05 near field)", "peak_source": peaks["source"],
+                 "tensor_frac_executed": round(tensor_achieved / peaks["bf16_tflops"], 4),
+                 "tensor_frac_useful": round(useful_flops / sec / 1e12 / peaks["bf16_tflops"], 4),
+                 "hbm_frac": round(hbm_achieved / peaks["hbm_gbs"], 4),
+                 "near_ms_per_eval": round(near_ms, 4), "traffic": measured_traffic("mixed_near", nv),
+                 "algorithmic_bytes": alg_bytes, "executed_flops": exec_flops,
+                 "kernel": "k_tc<0> (tcgen05 near field)", "peak_source": peaks["source"] + " (MEASURED_PEAKS.json)",
                  "t_tensor_ms": round(t_tensor, 4), "t_hbm_ms": round(t_hbm, 4)})
-    return {"value": round(dist.world * q / (ms / 1e3), 3), "unit": "cols/s", "ms_per_step": round(ms, 4),
-            "error_vs_fp64": err, "dtype": "f16 hi+lo split, f32 accumulate",
-            "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
-            "gpu_launches": sum(c for _, c in phases.values()), "roofline": roof, "autotune": tune}
+    return roof
 
 
 def run_inspector_reuse(w, X) -> dict:
@@ -439,7 +477,7 @@ def run_near_otf(w, X, dist, stored_ms, stored_info) -> dict:
         hp.hmat_free(h)
 
 
-def run_precision(args, dist) -> dict:
+def run_precision(args, dist, fp64_peak: float) -> dict:
     """Precision mode on its own recipe: N = 262144 uniform points in [0,1]^3, inverse multiquadric
     1/sqrt(r^2 + 0.01), geometric admissibility, leaf 256, ID tol 1e-7, q = 512. The mixed form (FP16 hi+lo
     tensor-core near field, FP32 far field, FP64 output sums) against the FP64 form on the same GPU; its error
@@ -462,11 +500,15 @@ def run_precision(args, dist) -> dict:
            "tol": w.tol, "max_rank": w.max_rank, "near_values": info["near_values"], "sum_rank": info["sum_rank"],
            "inspector_s": round(t_build, 2), "unit": "cols/s"}
     tunes = {}
-    for name, mode, Y, steps in (("fp64", hp.HMAT_MODE_FP64, Y64, 2), ("mixed", hp.HMAT_MODE_MIXED, Ym, args.steps)):
+    # both forms are timed over --steps evaluations (an FP64 evaluation takes about 1.6 s)
+    for name, mode, Y in (("fp64", hp.HMAT_MODE_FP64, Y64), ("mixed", hp.HMAT_MODE_MIXED, Ym)):
+        steps = args.steps
         tunes[name] = hp.hmat_autotune(dev.handle, q, mode, stream)
-        hp.hmat_eval(dev.handle, W, Y, q, mode, stream)          # warm-up (FP64 takes about a second)
+        for _ in range(1 if mode == hp.HMAT_MODE_FP64 else args.warmup):
+            hp.hmat_eval(dev.handle, W, Y, q, mode, stream)
         torch.cuda.synchronize()
         dist.barrier()
+        hp.hmat_profile(dev.handle, True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -475,9 +517,24 @@ def run_precision(args, dist) -> dict:
         e1.record(stream)
         torch.cuda.synchronize()
         ms = dist.max(e0.elapsed_time(e1) / steps)
+        phases = hp.hmat_phase_times(dev.handle)
+        hp.hmat_profile(dev.handle, False)
         if dev.poll() != hp.HMAT_OK:
             raise RuntimeError(f"device status error in the precision-mode {name} steps")
-        out[name] = {"value": round(dist.world * q / (ms / 1e3), 2), "ms_per_step": round(ms, 4), "steps": steps}
+        near_ms = phases["near"][0] / steps
+        out[name] = {"value": round(dist.world * q / (ms / 1e3), 2), "ms_per_step": round(ms, 4), "steps": steps,
+                     "phases_ms_per_step": {k: round(v[0] / steps, 4) for k, v in phases.items() if v[1] > 0},
+                     "launches_per_eval": sum(c for _, c in phases.values()) // steps}
+        if mode == hp.HMAT_MODE_FP64:
+            achieved = 2.0 * q * info["near_values"] / (near_ms / 1e3) / 1e12
+            out[name]["roofline"] = {"bound": "alu", "achieved": round(achieved, 4), "unit": "TFLOP/s",
+                                     "peak": round(fp64_peak / 1e3, 4), "frac": round(achieved / (fp64_peak / 1e3), 4),
+                                     "kernel": "k_grouped_gemm<double> (near field)"}
+        else:
+            serial = serial_phases(dev.handle, W, Y, q, mode, stream, steps)
+            out[name]["phases_serialised_ms_per_step"] = serial
+            out[name]["roofline"] = tc_near_roofline(info, q, serial["near"])
+            out[name]["roofline"]["near_ms_beside_far_chain"] = round(near_ms, 4)
     out["mixed"]["error_vs_fp64"] = float(torch.linalg.norm(Ym - Y64) / torch.linalg.norm(Y64))
     out["mixed_over_fp64"] = round(out["mixed"]["value"] / out["fp64"]["value"], 2)
     out["autotune"] = tunes
@@ -541,16 +598,76 @@ def run_matvec(args, dist, peak_gflops: float) -> dict:
                     "unit": "TFLOP/s", "frac": round(achieved / (peak_gflops / 1e3), 4),
                     "kernel": "k_grouped_gemm<double> 1-column tiles (near field)"}
         else:
+            serial = serial_phases(dev.handle, W, Ys[name], q, mode, stream, steps)
+            near_ms = serial["near"]
             alg = 4.0 * nv + 8.0 * w.n * q * 2
             achieved = alg / (near_ms / 1e3) / 1e9
             roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": round(achieved / peaks["hbm_gbs"], 4), "algorithmic_bytes": alg,
                     "kernel": "k_tc (tcgen05 near field, 16-column tile)", "peak_source": peaks["source"]}
         out[name] = {"value": round(dist.world * q / (ms / 1e3), 1), "ms_per_step": round(ms, 4), "steps": steps,
-                     "phases_ms_per_step": {k: round(v[0] / steps, 4) for k, v in phases.items()}, "roofline": roof}
+                     "phases_ms_per_step": {k: round(v[0] / steps, 4) for k, v in phases.items() if v[1] > 0},
+                     "launches_per_eval": sum(c for _, c in phases.values()) // steps, "roofline": roof}
+        if mode == hp.HMAT_MODE_MIXED:
+            out[name]["phases_serialised_ms_per_step"] = serial
     out["mixed"]["error_vs_fp64"] = float(torch.linalg.norm(Ys["mixed"] - Ys["fp64"]) / torch.linalg.norm(Ys["fp64"]))
     dev.close()
     return out
+
+
+def run_hss(args, dist) -> dict:
+    """Latency of the small HSS recipe: N = 2048 uniform points in [0,1]^3, weak admissibility (every pair of
+    siblings far), Gaussian h = 0.5, leaf 64, ID tol 1e-6, rank <= 64, q = 16, FP64. Its work is a few MFLOP, so
+    the time is launch latency: microseconds per evaluation through hmat_eval, and replayed as a one-member
+    batch (one CUDA graph launch per evaluation)."""
+    import torch
+    import paper_1812_07152_gb300 as hp
+    from workloads import WORKLOADS, make_points, normal_rhs
+    w = WORKLOADS["hss_uniform3d_n2048"]
+    h = hp.hmat_build(make_points(w), **build_params(w))
+    try:
+        info = hp.hmat_info(h)
+        q = w.q
+        W = torch.from_numpy(normal_rhs(w.n, q, w.rhs_seed)).cuda()
+        Y = torch.empty_like(W)
+        stream = torch.cuda.current_stream()
+        hp.hmat_reserve(h, q)
+        steps = max(200, 10 * args.steps)
+
+        def timed(fn):
+            for _ in range(max(args.warmup, 10)):
+                fn()
+            torch.cuda.synchronize()
+            dist.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return dist.max(e0.elapsed_time(e1) / steps)
+
+        hp.hmat_profile(h, True)
+        hp.hmat_eval(h, W, Y, q, hp.HMAT_MODE_FP64, stream)
+        launches = sum(c for _, c in hp.hmat_phase_times(h).values())
+        hp.hmat_profile(h, False)
+        ms_eval = timed(lambda: hp.hmat_eval(h, W, Y, q, hp.HMAT_MODE_FP64, stream))
+        b = hp.hmat_batch_create([h], hp.HMAT_MODE_FP64)
+        try:
+            ms_graph = timed(lambda: hp.hmat_batch_eval(b, [W], [Y], stream))
+        finally:
+            hp.hmat_batch_free(b)
+        if hp.hmat_status_poll(h) != hp.HMAT_OK:
+            raise RuntimeError("device status error in the HSS steps")
+        flops = 2.0 * q * (info["near_values"] + 2 * info["basis_values"] + info["coupling_values"])
+        return {"workload": w.name, "n": w.n, "q": q, "mode": "fp64", "levels": info["levels"],
+                "sum_rank": info["sum_rank"], "steps": steps, "launches_per_eval": launches,
+                "us_per_eval": round(ms_eval * 1e3, 2), "us_per_eval_graph": round(ms_graph * 1e3, 2),
+                "value": round(dist.world * q / (ms_eval / 1e3), 1), "unit": "cols/s",
+                "gflops": round(flops / (ms_eval / 1e3) / 1e9, 2)}
+    finally:
+        hp.hmat_free(h)
 
 
 def run_batch(args, dist) -> dict:

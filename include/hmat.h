@@ -284,6 +284,10 @@ hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int 
 /*
  * hmat_profile - enable (1) or disable (0) CUDA-event timing of every kernel
  * launch of later evaluations on this handle; enabling clears earlier records.
+ * enable = 2 times the same launches with the mixed mode's far chain moved from its
+ * side stream onto the caller's stream, so that every launch's time is its own
+ * and not shared with a launch running beside it (the evaluation is otherwise
+ * unchanged; its result is bitwise the same).
  * hmat_phase_times - synchronise on the recorded events and return, for phase
  * kind k < n, the summed device time in ms[k] and the number of launches in
  * launches[k] since profiling was enabled; then clear the records. Phase kinds:
@@ -291,7 +295,12 @@ hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int 
  * at the leaves), HMAT_PHASE_UP_TRANSFER (w = P^T [w_l; w_r], one launch per
  * level), HMAT_PHASE_COUPLING (u = sum B w), HMAT_PHASE_DOWN_TRANSFER
  * ([u_l; u_r] += P u, one launch per level), HMAT_PHASE_DOWN_LEAF (Y += P u),
- * HMAT_PHASE_SPLIT (mixed mode only: scale and split W into FP16 hi/lo tiles).
+ * HMAT_PHASE_SPLIT (mixed mode only: scale and split W into FP16 hi/lo tiles),
+ * HMAT_PHASE_FAR_UP (mixed mode: one persistent launch of the upward pass over
+ * every level; when the coupling runs in FP32 it also holds the coupling and the
+ * downward transfers), HMAT_PHASE_FAR_DOWN (mixed mode: one persistent launch of the
+ * downward transfers after the tensor-core coupling). In the mixed mode the downward
+ * leaf step is one persistent launch too (HMAT_PHASE_DOWN_LEAF).
  */
 #define HMAT_PHASE_NEAR 0
 #define HMAT_PHASE_UP_LEAF 1
@@ -300,7 +309,9 @@ hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int 
 #define HMAT_PHASE_DOWN_TRANSFER 4
 #define HMAT_PHASE_DOWN_LEAF 5
 #define HMAT_PHASE_SPLIT 6          /* mixed mode: max |W| and the FP16 hi/lo split of W */
-#define HMAT_PHASE_COUNT 7
+#define HMAT_PHASE_FAR_UP 7         /* mixed mode: persistent far-chain launch, upward pass (+ FP32 coupling) */
+#define HMAT_PHASE_FAR_DOWN 8       /* mixed mode: persistent far-chain launch, downward transfers */
+#define HMAT_PHASE_COUNT 9
 hmat_status hmat_profile(hmat_t h, int enable);
 hmat_status hmat_phase_times(hmat_t h, double* ms, int64_t* launches, int n);
 
@@ -337,19 +348,19 @@ hmat_status hmat_selftest_conversions(int64_t n, uint64_t seed, int64_t* mismatc
  *
  * The skeleton workspaces (the upward weights w and the downward potentials u,
  * sum of ranks x q values each) live in one static device array of
- * HMAT_NOALLOC_SCRATCH_VALUES doubles (16 MiB) compiled into libhmat.so, which
- * every GPU that loads the library holds until the process exits. The call
- * returns HMAT_EINVAL when 2 x (sum of ranks) x q exceeds that size (the sum of
- * ranks is out[7] of hmat_info). It calls no cudaMalloc or cudaFree and no
- * allocating library routine; the handle must already exist (hmat_load and
- * hmat_build do allocate).
+ * HMAT_NOALLOC_SCRATCH_VALUES doubles (16 MiB) compiled into libhmat.so. The
+ * first hmat_load or hmat_build on a device loads that array onto the device
+ * (both allocate anyway) and every load stores its device address in the handle;
+ * the device then holds the array until the process exits. The call returns
+ * HMAT_EINVAL when 2 x (sum of ranks) x q exceeds that size (the sum of ranks is
+ * out[7] of hmat_info). It calls no cudaMalloc or cudaFree and no allocating
+ * library routine, and looks nothing up: the handle must already exist, and its
+ * own workspace (hmat_info out[8]) is neither used nor grown.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Every call shares the one array and leaves its
- * last contents behind; every workspace row is written before it is read, so
- * nothing needs clearing. Calls whose work overlaps on the GPU (other streams,
- * other handles, other host threads) race on the array: order them.
+ * Every call shares the one array and leaves its last contents behind; every
+ * workspace row is written before it is read, so nothing needs clearing. Calls
+ * whose work overlaps on the GPU (other streams, other handles, other host
+ * threads) race on the array: order them.
  * Arguments and results are those of hmat_eval.
  */
 #define HMAT_NOALLOC_SCRATCH_VALUES 2097152
@@ -374,7 +385,9 @@ hmat_status hmat_eval_noalloc(hmat_t h, const double* W, double* Y, int64_t q, v
  * already tuned replaces the earlier choice. `report` (may be NULL) receives the
  * number of launches tuned, the summed time of those launches with the default and
  * with the chosen shapes (ms; a long launch timed on a prefix counts at full
- * length, scaled by its tile count) and the chosen near-field width in columns.
+ * length, scaled by its tile count; in the mixed mode, when it has a far field, the
+ * time of a whole evaluation), the chosen near-field width in columns and the
+ * chosen far-chain grid.
  */
 typedef struct {
   int64_t q;
@@ -383,8 +396,21 @@ typedef struct {
   double default_ms;
   double tuned_ms;
   int32_t near_cols;
+  int32_t chain_grid;        /* mixed mode: CTAs of the persistent far chain, 0 = every resident CTA */
 } hmat_tune_report;
 hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream, hmat_tune_report* report);
+
+/*
+ * hmat_tune_apply - install a mixed-mode choice without timing (for example one that
+ * hmat_autotune reported in an earlier process): for evaluations of h with
+ * choice->q columns, choice->near_cols columns per tensor-core CTA (0: the default;
+ * else one of the widths hmat_autotune tries for that q, else HMAT_EINVAL) and
+ * choice->chain_grid CTAs for the persistent far chain (0: every resident CTA; any
+ * positive count is valid: the chain completes with any number of CTAs, even one).
+ * Results are bitwise the same for every choice. choice->mode must be
+ * HMAT_MODE_MIXED (else HMAT_EUNSUPPORTED); the other fields are ignored.
+ */
+hmat_status hmat_tune_apply(hmat_t h, const hmat_tune_report* choice);
 
 /*
  * Batches: many HMatrices (uneven sizes, ranks and q) evaluated together. A batch
@@ -468,6 +494,20 @@ hmat_status hmat_status_poll(hmat_t h, void* stream);
  * tensor memory, so the CUDA context stays usable afterwards.
  */
 hmat_status hmat_selftest_timeout(hmat_t h, int64_t limit_ns, void* stream);
+
+/*
+ * hmat_selftest_chain_timeout - failure-detection self-test of the mixed mode's
+ * persistent far chain (no counterpart in the paper). Enqueues on `stream` the
+ * chain's first launch for q columns (on the handle's own workspace, which it
+ * reserves like hmat_eval) with every dependency requirement raised by one, so
+ * that no wait can be met: each wait gives up after limit_ns nanoseconds
+ * (0 < limit_ns <= 10 s, else HMAT_EINVAL), latches HMAT_ETIMEOUT in h's status
+ * word and stops the launch, which reads and writes no workspace before its
+ * waits. The next hmat_status_poll returns HMAT_ETIMEOUT; the context stays
+ * usable. HMAT_EUNSUPPORTED without HMAT_LOAD_MIXED, HMAT_EINVAL when the HMatrix
+ * has no far field.
+ */
+hmat_status hmat_selftest_chain_timeout(hmat_t h, int64_t q, int64_t limit_ns, void* stream);
 
 /* hmat_info - sizes of the loaded HMatrix: out[0] = n_points, out[1] = levels,
  * out[2] = near entries, out[3] = far entries, out[4] = near values (stored, or

@@ -208,6 +208,9 @@ void free_device(Handle* h) {
   free_tc(&h->tc_far);
   cudaFree(h->arena32);
   cudaFree(h->entries32);
+  cudaFree(h->chain.items);
+  cudaFree(h->chain.expect);
+  h->chain = ChainPlan{};
   h->arena32 = nullptr; h->entries32 = nullptr; h->has_mixed = false;
   cudaFree(h->arena);
   cudaFree(h->pts_tree);
@@ -457,6 +460,77 @@ hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const
   return HMAT_OK;
 }
 
+// The far field of the mixed mode as chain items (hmat_chain.cu): every tile of the
+// FP32 phases, ordered so that every item's dependencies come before it, and the
+// number of items per node and kind that a dependent item waits for.
+hmat_status build_chain(Handle* h, const Validated& v, const std::vector<GemmTile>& tiles,
+                        const std::vector<int32_t>& task_node) {
+  const int L = h->levels;
+  const int64_t n = v.n_nodes;
+  std::vector<std::vector<ChainItem>> up(L + 1), cpl(L + 1), dn(L + 1);
+  std::vector<ChainItem> leaf;
+  for (const Phase& ph : h->phases32) {
+    const uint8_t cls = ph.tile_rows == 16 ? 0 : (ph.tile_rows == 32 ? 1 : 2);
+    for (int64_t i = ph.tile_begin; i < ph.tile_begin + ph.n_tiles; ++i) {
+      const int32_t node = task_node[tiles[i].task];
+      const int lvl = level_of(node);
+      ChainItem it{(int32_t)i, node, 0, cls, (uint8_t)lvl, (uint8_t)(ph.xmap == XMAP_FAR ? 1 : 0)};
+      switch (ph.kind) {
+        case PH_UP_LEAF:
+        case PH_UP_TRANS: it.kind = CK_UP; up[lvl].push_back(it); break;
+        case PH_COUPLING: it.kind = CK_CPL; cpl[lvl].push_back(it); break;
+        case PH_DOWN_TRANS: it.kind = CK_DN; dn[lvl].push_back(it); break;
+        case PH_DOWN_LEAF: it.kind = CK_LEAF; leaf.push_back(it); break;
+        default: return HMAT_EINVAL;
+      }
+    }
+  }
+  std::vector<ChainItem> items;
+  auto append = [&](const std::vector<ChainItem>& b) { items.insert(items.end(), b.begin(), b.end()); };
+  ChainPlan& cp = h->chain;
+  // A: the upward pass, each level's coupling after the next level up has been queued
+  // (so that the CTAs that take it find its inputs ready), then the downward transfers
+  cp.begin[0] = 0;
+  append(up[L]);
+  for (int l = L - 1; l >= 1; --l) {
+    append(up[l]);
+    if (!h->tc_coupling) append(cpl[l + 1]);
+  }
+  if (!h->tc_coupling && L >= 1) append(cpl[1]);
+  if (!h->tc_coupling)
+    for (int l = 1; l < L; ++l) append(dn[l]);
+  cp.count[0] = (int32_t)items.size();
+  cp.waits[0] = h->tc_coupling ? kWaitUp : (kWaitUp | kWaitLevel | kWaitCpl | kWaitDn);
+  // B: the downward transfers after the tensor-core coupling (which the stream orders)
+  cp.begin[1] = (int32_t)items.size();
+  if (h->tc_coupling)
+    for (int l = 1; l < L; ++l) append(dn[l]);
+  cp.count[1] = (int32_t)items.size() - cp.begin[1];
+  cp.waits[1] = kWaitDn;
+  // C: the downward leaf step, after the near field has written Y (ordered by the stream)
+  cp.begin[2] = (int32_t)items.size();
+  append(leaf);
+  cp.count[2] = (int32_t)items.size() - cp.begin[2];
+  cp.waits[2] = 0;
+  if (items.size() > (size_t)INT32_MAX) return HMAT_EUNSUPPORTED;
+  std::vector<int32_t> expect(3 * n + L + 1, 0);
+  for (const ChainItem& it : items) {
+    if (it.kind == CK_UP) {
+      expect[it.node] += 1;
+      expect[3 * n + it.level] += 1;
+    } else if (it.kind == CK_CPL) {
+      expect[n + it.node] += 1;
+    } else if (it.kind == CK_DN) {
+      expect[2 * n + it.node] += 1;
+    }
+  }
+  cp.n_ctr = kChainCtrHead + (int64_t)expect.size();
+  cudaError_t e = chain_prepare(nullptr, nullptr);
+  if (e == cudaSuccess) e = upload(&cp.items, items, &h->device_bytes);
+  if (e == cudaSuccess) e = upload(&cp.expect, expect, &h->device_bytes);
+  return cuda_status(e);
+}
+
 }  // namespace
 
 namespace hmat {
@@ -611,8 +685,10 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     ph.n_tiles = (int64_t)tiles.size() - ph.tile_begin;
     if (ph.n_tiles > 0) h->phases32.push_back(ph);
   };
-  auto new_task = [&](int64_t out_row, int64_t m, int accumulate) -> int32_t {
+  std::vector<int32_t> task_node;  // the tree node of each task (the chain's counters)
+  auto new_task = [&](int64_t out_row, int64_t m, int accumulate, int64_t node) -> int32_t {
     tasks.push_back(GemmTask{out_row, (int32_t)m, (int32_t)entries.size(), (int32_t)entries.size(), accumulate});
+    task_node.push_back((int32_t)node);
     return (int32_t)tasks.size() - 1;
   };
   auto add_entry = [&](int32_t t, int64_t a_off, int64_t x_row, int64_t k, int64_t lda, int trans) {
@@ -626,7 +702,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     for (int64_t i = 0; i < v.n_leaves; ++i) {
       const int64_t a = fl + i;
       if (h->size[a] == 0) continue;
-      const int32_t t = new_task(h->begin[a], h->size[a], 0);
+      const int32_t t = new_task(h->begin[a], h->size[a], 0, a);
       for (int64_t e = d->near_ptr[i]; e < d->near_ptr[i + 1]; ++e) {
         const int64_t b = fl + d->near_idx[e];
         add_entry(t, near_off[e], h->begin[b], h->size[b], h->size[b], 0);
@@ -639,7 +715,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     std::vector<int32_t> ids;
     for (int64_t a = fl; a < v.n_nodes; ++a) {
       if (h->rank[a] == 0) continue;
-      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0);
+      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0, a);
       add_entry(t, basis_off[a], h->begin[a], h->size[a], h->rank[a], 1);
       ids.push_back(t);
     }
@@ -649,7 +725,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     std::vector<int32_t> ids;
     for (int64_t a = ((int64_t)1 << level) - 1; a < ((int64_t)2 << level) - 1; ++a) {
       if (h->rank[a] == 0) continue;
-      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0);
+      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0, a);
       add_entry(t, basis_off[a], h->skel_off[2 * a + 1], rows_of(a), h->rank[a], 1);
       ids.push_back(t);
     }
@@ -659,7 +735,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     std::vector<int32_t> ids;
     for (int64_t a = 1; a < v.n_nodes; ++a) {
       if (h->rank[a] == 0) continue;
-      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0);
+      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0, a);
       if (far_task_off[a] >= 0) add_entry(t, far_task_off[a], far_rows_off[a], far_k[a], far_k[a], 0);
       ids.push_back(t);
     }
@@ -669,7 +745,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     std::vector<int32_t> ids;
     for (int64_t a = ((int64_t)1 << level) - 1; a < ((int64_t)2 << level) - 1; ++a) {
       if (h->rank[a] == 0 || rows_of(a) == 0) continue;
-      const int32_t t = new_task(h->skel_off[2 * a + 1], rows_of(a), 1);
+      const int32_t t = new_task(h->skel_off[2 * a + 1], rows_of(a), 1, a);
       add_entry(t, basis_off[a], h->skel_off[a], h->rank[a], h->rank[a], 0);
       ids.push_back(t);
     }
@@ -679,7 +755,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     std::vector<int32_t> ids;
     for (int64_t a = fl; a < v.n_nodes; ++a) {
       if (h->rank[a] == 0 || h->size[a] == 0) continue;
-      const int32_t t = new_task(h->begin[a], h->size[a], 1);
+      const int32_t t = new_task(h->begin[a], h->size[a], 1, a);
       add_entry(t, basis_off[a], h->skel_off[a], h->rank[a], h->rank[a], 0);
       ids.push_back(t);
     }
@@ -777,11 +853,13 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
   if ((e = upload(&h->status, zero, &h->device_bytes)) != cudaSuccess) return fail(e);
   if (flags & HMAT_LOAD_MIXED) {
     hmat_status ms = build_mixed(h.get(), d, v, near_off, far_task_off, far_off, far_k, tasks, entries, tiles);
+    if (ms == HMAT_OK) ms = build_chain(h.get(), v, tiles, task_node);
     if (ms != HMAT_OK) {
       free_device(h.get());
       return ms;
     }
   }
+  if ((e = noalloc_scratch_address(&h->noalloc_scratch)) != cudaSuccess) return fail(e);
   {
     hmat_status cs = ctx_create(*h, &h->ctx);
     if (cs != HMAT_OK) {

@@ -111,10 +111,10 @@ extern "C" hmat_status hmat_batch_eval(hmat_batch_t b, const double* const* W, d
       b->exec = nullptr;
     }
     // capture every member's evaluation as a branch forked from the capture stream
-    std::vector<bool> profiling(n);
+    std::vector<int> profiling(n);
     for (int i = 0; i < n; ++i) {
       profiling[i] = b->handles[i]->profiling;
-      b->handles[i]->profiling = false;
+      b->handles[i]->profiling = 0;
     }
     hmat_status st = HMAT_OK;
     cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);

@@ -6,8 +6,10 @@
 //
 // Mixed mode: W is split into FP16 hi/lo tensor-core tiles (and an FP32 tree-order
 // copy); the near field runs on the tensor cores on the caller's stream while the far
-// chain (upward pass, coupling, downward transfers) runs in FP32 on a high-priority
-// side stream; the downward leaf step, which adds into Y, follows both.
+// chain (upward pass, coupling, downward transfers) runs on a high-priority side stream
+// as persistent FP32 launches over every tree level (hmat_chain.cu), the coupling on the
+// tensor cores between two of them when its ranks fill the tiles; the downward leaf
+// step, which adds into Y, follows both as one more persistent launch.
 //
 // The per-evaluation state lives in an EvalContext, so several evaluations of the
 // same HMatrix can be in flight at once (batches, the server).
@@ -144,7 +146,8 @@ int64_t ctx_bytes(const Handle& h, int64_t q, int mode) {
     const int64_t cols = mixed_cols_bound(q);
     return 2 * align_up(sizeof(unsigned long long)) + align_up(h.tc_near.n_chunks * cols * 256) +
            align_up(h.tc_far.n_chunks * cols * 256) +
-           align_up(std::max<int64_t>(h.n_points, 1) * q * 4) + 2 * align_up(r * q * 4);
+           align_up(std::max<int64_t>(h.n_points, 1) * q * 4) + 2 * align_up(r * q * 4) +
+           align_up(h.chain.n_ctr * 4);
   }
   return 2 * align_up(r * q * 8);
 }
@@ -161,6 +164,7 @@ void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* bas
   c->wmax = c->smax = nullptr;
   c->wsplit = c->ssplit = nullptr;
   c->w32 = c->ws32 = c->us32 = nullptr;
+  c->chain_ctr = nullptr;
   if (mode == HMAT_MODE_MIXED) {
     const int64_t cols = mixed_cols_bound(q);
     c->wmax = (unsigned long long*)take(sizeof(unsigned long long));
@@ -170,6 +174,7 @@ void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* bas
     c->w32 = (float*)take(std::max<int64_t>(h.n_points, 1) * q * 4);
     c->ws32 = (float*)take(r * q * 4);
     c->us32 = (float*)take(r * q * 4);
+    c->chain_ctr = (int32_t*)take(h.chain.n_ctr * 4);
   } else {
     c->ws = (double*)take(r * q * 8);
     c->us = (double*)take(r * q * 8);
@@ -194,6 +199,48 @@ hmat_status ctx_reserve(const Handle& h, EvalContext* c, int64_t q, int mode) {
   return HMAT_OK;
 }
 
+ChainMember chain_member(const Handle& h, const EvalContext* c, double* Y, int64_t q) {
+  ChainMember m{};
+  m.tiles = h.tiles;
+  m.tasks = h.tasks;
+  m.entries = h.entries32;
+  m.arena = h.arena32;
+  m.w32 = c->w32;
+  m.ws32 = c->ws32;
+  m.us32 = c->us32;
+  m.Y = Y;
+  m.perm = h.perm;
+  m.far_rows = h.far_rows;
+  m.items = h.chain.items;
+  m.expect = h.chain.expect;
+  m.ctr = c->chain_ctr + kChainCtrHead;
+  m.status = h.status;
+  m.q = q;
+  m.bn = chain_bn(q);
+  m.n_ct = (int32_t)((q + m.bn - 1) / m.bn);
+  m.n_nodes = (int32_t)h.n_nodes;
+  m.first_leaf = (int32_t)(h.n_leaves - 1);
+  m.xv = q % 4 == 0 ? 1 : 0;
+  return m;
+}
+
+ChainLaunch chain_launch(const Handle& h, const EvalContext* c, int part, int32_t extra, uint64_t limit_ns) {
+  ChainLaunch l{};
+  l.item_begin = h.chain.begin[part];
+  l.n_items = h.chain.count[part];
+  l.ticket = c->chain_ctr + part;
+  l.abort_flag = c->chain_ctr + 3;
+  l.waits = h.chain.waits[part];
+  l.extra = extra;
+  l.limit_ns = limit_ns;
+  return l;
+}
+
+int chain_grid_cap(const Handle& h, int64_t q) {
+  const TuneEntry* t = find_tuned(h, q, HMAT_MODE_MIXED);
+  return t ? t->chain_grid : 0;
+}
+
 hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int64_t q, int mode, cudaStream_t s) {
   Handle::ProfRecord rec{};
   hmat_status st = HMAT_OK;
@@ -206,45 +253,45 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
     e = launch_split_f64(h->tc_near, W, h->n_points * q, h->perm, q, n_t, (int)n_ct, c->wmax, c->wsplit, c->w32, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;
-    if (cudaEventRecord(c->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->ev_fork, 0) != cudaSuccess)
+    // the far chain on the side stream (beside the near field), or on s when profiling
+    // serialised (each launch's events then time that launch alone)
+    const bool serial = h->profiling == 2;
+    cudaStream_t far = serial ? s : c->aux;
+    if (!serial &&
+        (cudaEventRecord(c->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->ev_fork, 0) != cudaSuccess))
       return HMAT_ECUDA;
-    auto far_launch = [&](const Phase& ph, cudaStream_t strm) -> hmat_status {
-      const float* X = ph.x == MAT_USER ? c->w32 : (ph.x == MAT_SKEL_W ? c->ws32 : c->us32);
-      void* Yd = ph.y == MAT_USER ? (void*)Y : (ph.y == MAT_SKEL_W ? (void*)c->ws32 : (void*)c->us32);
-      const int64_t* xm = ph.xmap == XMAP_FAR ? h->far_rows : nullptr;  // the FP32 copy of W is in tree order
-      const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
-      if (!prof_begin(h, (int32_t)ph.kind, strm, &rec)) return HMAT_ECUDA;
-      e = launch_f32_phase(*h, ph, X, xm, Yd, ph.y == MAT_USER, ym, q, strm);
+    ChainMember cm = chain_member(*h, c, Y, q);
+    auto chain = [&](int part, int32_t kind, cudaStream_t strm) -> hmat_status {
+      if (h->chain.count[part] == 0) return HMAT_OK;
+      if (!prof_begin(h, kind, strm, &rec)) return HMAT_ECUDA;
+      e = launch_chain(cm, chain_launch(*h, c, part, 0, kChainWaitNs), chain_grid_cap(*h, q), strm);
       if (e != cudaSuccess) return cuda_status(e);
       return prof_end(h, rec, strm) ? HMAT_OK : HMAT_ECUDA;
     };
-    // far chain on the side stream: upward pass, coupling (on the tensor cores after
-    // splitting the skeleton weights, or in FP32), downward transfers
-    for (const Phase& ph : h->phases32)
-      if (ph.kind == PH_UP_LEAF || ph.kind == PH_UP_TRANS || ph.kind == PH_COUPLING)
-        if ((st = far_launch(ph, c->aux)) != HMAT_OK) return st;
+    if ((e = cudaMemsetAsync(c->chain_ctr, 0, (size_t)h->chain.n_ctr * 4, far)) != cudaSuccess) return cuda_status(e);
+    // upward pass (with the FP32 coupling: also the coupling and the downward transfers)
+    if ((st = chain(0, HMAT_PHASE_FAR_UP, far)) != HMAT_OK) return st;
     if (h->tc_coupling && h->tc_far.n_work > 0) {
-      if (!prof_begin(h, HMAT_PHASE_SPLIT, c->aux, &rec)) return HMAT_ECUDA;
+      if (!prof_begin(h, HMAT_PHASE_SPLIT, far, &rec)) return HMAT_ECUDA;
       e = launch_split_f32(h->tc_far, c->ws32, std::max<int64_t>(h->sum_rank, 1) * q, q, n_t, (int)n_ct, c->smax,
-                           c->ssplit, c->aux);
+                           c->ssplit, far);
       if (e != cudaSuccess) return cuda_status(e);
-      if (!prof_end(h, rec, c->aux)) return HMAT_ECUDA;
-      if (!prof_begin(h, HMAT_PHASE_COUPLING, c->aux, &rec)) return HMAT_ECUDA;
-      e = launch_tc_far(h->tc_far, c->ssplit, c->smax, c->us32, q, n_t, (int)n_ct, h->status, c->aux);
+      if (!prof_end(h, rec, far)) return HMAT_ECUDA;
+      if (!prof_begin(h, HMAT_PHASE_COUPLING, far, &rec)) return HMAT_ECUDA;
+      e = launch_tc_far(h->tc_far, c->ssplit, c->smax, c->us32, q, n_t, (int)n_ct, h->status, far);
       if (e != cudaSuccess) return cuda_status(e);
-      if (!prof_end(h, rec, c->aux)) return HMAT_ECUDA;
+      if (!prof_end(h, rec, far)) return HMAT_ECUDA;
     }
-    for (const Phase& ph : h->phases32)
-      if (ph.kind == PH_DOWN_TRANS && (st = far_launch(ph, c->aux)) != HMAT_OK) return st;
-    if (cudaEventRecord(c->ev_join, c->aux) != cudaSuccess) return HMAT_ECUDA;
+    // downward transfers after the tensor-core coupling
+    if ((st = chain(1, HMAT_PHASE_FAR_DOWN, far)) != HMAT_OK) return st;
+    if (!serial && cudaEventRecord(c->ev_join, c->aux) != cudaSuccess) return HMAT_ECUDA;
     if (!prof_begin(h, HMAT_PHASE_NEAR, s, &rec)) return HMAT_ECUDA;
     e = launch_tc_near(h->tc_near, c->wsplit, c->wmax, h->perm, Y, q, n_t, (int)n_ct, h->status, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;
-    if (cudaStreamWaitEvent(s, c->ev_join, 0) != cudaSuccess) return HMAT_ECUDA;
-    for (const Phase& ph : h->phases32)
-      if (ph.kind == PH_DOWN_LEAF && (st = far_launch(ph, s)) != HMAT_OK) return st;
-    return HMAT_OK;
+    if (!serial && cudaStreamWaitEvent(s, c->ev_join, 0) != cudaSuccess) return HMAT_ECUDA;
+    // downward leaf step: adds into Y after the near field has written it
+    return chain(2, HMAT_PHASE_DOWN_LEAF, s);
   }
   const TuneEntry* tuned = find_tuned(*h, q, HMAT_MODE_FP64);
   for (size_t i = 0; i < h->phases.size(); ++i) {
@@ -364,6 +411,23 @@ extern "C" hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int6
   return cuda_status(e);
 }
 
+extern "C" hmat_status hmat_selftest_chain_timeout(hmat_t h, int64_t q, int64_t limit_ns, void* stream) {
+  if (!h || q <= 0 || limit_ns <= 0 || limit_ns > 10000000000LL) return HMAT_EINVAL;
+  if (!h->has_mixed) return HMAT_EUNSUPPORTED;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
+  if (dev != h->device) return HMAT_EINVAL;
+  if (h->chain.count[0] == 0) return HMAT_EINVAL;  // no far field: nothing to wait on
+  hmat_status st = ctx_reserve(*h, h->ctx, q, HMAT_MODE_MIXED);
+  if (st != HMAT_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(h->ctx->chain_ctr, 0, (size_t)h->chain.n_ctr * 4, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  // the workspaces are not filled: the launch waits before it reads or writes any of them
+  const ChainMember m = chain_member(*h, h->ctx, nullptr, q);
+  return cuda_status(launch_chain(m, chain_launch(*h, h->ctx, 0, 1, (uint64_t)limit_ns), 0, s));
+}
+
 extern "C" hmat_status hmat_profile(hmat_t h, int enable) {
   if (!h) return HMAT_EINVAL;
   for (auto& r : h->prof) {
@@ -371,7 +435,7 @@ extern "C" hmat_status hmat_profile(hmat_t h, int enable) {
     h->event_pool.push_back(r.stop);
   }
   h->prof.clear();
-  h->profiling = enable != 0;
+  h->profiling = enable == 2 ? 2 : (enable != 0 ? 1 : 0);
   return HMAT_OK;
 }
 

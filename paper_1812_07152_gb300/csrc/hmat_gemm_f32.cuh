@@ -54,27 +54,30 @@ struct CfgF32 {
   static_assert(kXPer <= BK, "one map index per row of the chunk");
 };
 
+// One CTA tile of the FP32 grouped GEMM: output rows m0 .. m0 + BM - 1 of the tile's
+// task, columns q0 .. q0 + BN - 1. Threads from C::kThreads on (when the CTA is wider
+// than the shape) take no part but pass the CTA-wide barriers, so the persistent far
+// chain can run every shape with one block size. smf: C::kSmemBytes of shared memory.
 // XV: the rows of X are copied 16 bytes (four columns) at a time; needs q a multiple of 4
 // and X 16-byte aligned.
 template <typename TY, int BM, int BN, bool XV>
-__global__ void __launch_bounds__(CfgF32<BM, BN>::kThreads)
-k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
-                   const GemmEntry* __restrict__ entries, const float* __restrict__ arena,
-                   const float* X, const int64_t* __restrict__ x_map, TY* Y, const int64_t* __restrict__ y_map,
-                   int64_t q, int n_col_tiles) {
+__device__ __forceinline__ void gemm_tile_f32(const GemmTile tile, const GemmTask* __restrict__ tasks,
+                                              const GemmEntry* __restrict__ entries,
+                                              const float* __restrict__ arena, const float* X,
+                                              const int64_t* __restrict__ x_map, TY* Y,
+                                              const int64_t* __restrict__ y_map, int64_t q, int64_t q0,
+                                              float* smf) {
   using C = CfgF32<BM, BN>;
   constexpr int NTS = C::kSliceThreads;
   constexpr int CX = BN / TN;
   constexpr int S = kAsyncStages;
-  extern __shared__ __align__(16) float smf[];
 
-  const GemmTile tile = tiles[blockIdx.x / n_col_tiles];
   const GemmTask task = tasks[tile.task];
   const int m0 = tile.m0;
-  const int64_t q0 = (int64_t)(blockIdx.x % n_col_tiles) * BN;
+  const bool active = threadIdx.x < C::kThreads;
   const int slice = threadIdx.x / NTS, lt = threadIdx.x % NTS;
   const int ty = lt / CX, tx = lt % CX;
-  float* my = smf + slice * S * C::kStageFloats;  // this slice's stages
+  float* my = smf + (active ? slice : 0) * S * C::kStageFloats;  // this slice's stages
   auto a_st = [&](int st) { return my + st * C::kStageFloats; };
   auto x_st = [&](int st) { return my + st * C::kStageFloats + BK * C::kAStride; };
 
@@ -88,7 +91,7 @@ k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restric
   GemmEntry en{};
   if (has) en = entries[task.e_begin];
   const int n_chunks = has ? (en.k + BK - 1) / BK : 0;
-  const int my_chunks = n_chunks > slice ? (n_chunks - slice + C::kSlices - 1) / C::kSlices : 0;
+  const int my_chunks = active && n_chunks > slice ? (n_chunks - slice + C::kSlices - 1) / C::kSlices : 0;
   const float* a = arena + en.a_off;
 
   // X row of depth gk (through the row map when there is one); one per copy of XW floats
@@ -136,52 +139,54 @@ k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restric
     }
   };
 
-  int64_t rows_cur[XN];
-  load_rows(0, rows_cur);
+  if (active) {
+    int64_t rows_cur[XN];
+    load_rows(0, rows_cur);
 #pragma unroll
-  for (int st = 0; st < S - 1; ++st) {
-    load_rows(st + 1, rows_next);
-    issue(st, st, rows_cur);
-    cp_async_commit();
+    for (int st = 0; st < S - 1; ++st) {
+      load_rows(st + 1, rows_next);
+      issue(st, st, rows_cur);
+      cp_async_commit();
 #pragma unroll
-    for (int t = 0; t < XN; ++t) rows_cur[t] = rows_next[t];
-  }
-  for (int j = 0; j < my_chunks; ++j) {
-    load_rows(j + S, rows_next);  // indices one chunk ahead of the next copy
-    cp_async_wait<S - 2>();
-    bar_sync(1 + slice, NTS);     // chunk j landed for the slice; stage (j - 1) % S is free
-    issue(j + S - 1, (j + S - 1) % S, rows_cur);
-    cp_async_commit();
-#pragma unroll
-    for (int t = 0; t < XN; ++t) rows_cur[t] = rows_next[t];
-    const float* As = a_st(j % S);
-    const float* Xs = x_st(j % S);
-#pragma unroll
-    for (int k = 0; k < BK; ++k) {
-      float av[TM], xv[TN];
-#pragma unroll
-      for (int i = 0; i < TM; ++i) av[i] = As[k * C::kAStride + ty * TM + i];
-#pragma unroll
-      for (int jj = 0; jj < TN; ++jj) xv[jj] = Xs[k * BN + tx * TN + jj];
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int jj = 0; jj < TN; ++jj) acc[i][jj] = fmaf(av[i], xv[jj], acc[i][jj]);
+      for (int t = 0; t < XN; ++t) rows_cur[t] = rows_next[t];
     }
+    for (int j = 0; j < my_chunks; ++j) {
+      load_rows(j + S, rows_next);  // indices one chunk ahead of the next copy
+      cp_async_wait<S - 2>();
+      bar_sync(1 + slice, NTS);     // chunk j landed for the slice; stage (j - 1) % S is free
+      issue(j + S - 1, (j + S - 1) % S, rows_cur);
+      cp_async_commit();
+#pragma unroll
+      for (int t = 0; t < XN; ++t) rows_cur[t] = rows_next[t];
+      const float* As = a_st(j % S);
+      const float* Xs = x_st(j % S);
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        float av[TM], xv[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) av[i] = As[k * C::kAStride + ty * TM + i];
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) xv[jj] = Xs[k * BN + tx * TN + jj];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int jj = 0; jj < TN; ++jj) acc[i][jj] = fmaf(av[i], xv[jj], acc[i][jj]);
+      }
+    }
+    cp_async_wait<0>();
   }
-  cp_async_wait<0>();
   __syncthreads();
 
   // add the slices' partial sums in a fixed order (slice 0 + 1 + 2 + 3)
   float* red = smf;  // kSlices - 1 partial tiles, reusing the stage buffers
-  if (slice > 0) {
+  if (active && slice > 0) {
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int jj = 0; jj < TN; ++jj) red[((slice - 1) * TM * TN + i * TN + jj) * NTS + lt] = acc[i][jj];
   }
   __syncthreads();
-  if (slice == 0) {
+  if (active && slice == 0) {
 #pragma unroll
     for (int sl = 1; sl < C::kSlices; ++sl)
 #pragma unroll
@@ -206,46 +211,6 @@ k_grouped_gemm_f32(const GemmTile* __restrict__ tiles, const GemmTask* __restric
       }
     }
   }
-}
-
-template <typename TY, int BM, int BN>
-cudaError_t launch_f32(const Handle& h, const Phase& ph, const float* arena, const float* X,
-                       const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q, cudaStream_t s) {
-  using C = CfgF32<BM, BN>;
-  static_assert(C::kSmemBytes >= (C::kSlices - 1) * TM * TN * C::kSliceThreads * 4, "room for the partial sums");
-  const int64_t n_col = (q + BN - 1) / BN;
-  const int64_t blocks = ph.n_tiles * n_col;
-  if (blocks > 2147483647LL) return cudaErrorInvalidValue;
-  const bool xv = q % 4 == 0 && ((uintptr_t)X & 15u) == 0;
-  auto kern = xv ? k_grouped_gemm_f32<TY, BM, BN, true> : k_grouped_gemm_f32<TY, BM, BN, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)blocks, C::kThreads, C::kSmemBytes, s>>>(h.tiles + ph.tile_begin, h.tasks, h.entries32, arena, X,
-                                                            x_map, Y, y_map, q, (int)n_col);
-  return cudaGetLastError();
-}
-
-// One launch of a far-field phase in FP32 (tasks with at most one entry each): 32, 64 or
-// (64-row tiles, q > 256) 128 columns per CTA.
-template <typename TY>
-cudaError_t launch_phase_f32(const Handle& h, const Phase& ph, const float* arena, const float* X,
-                             const int64_t* x_map, TY* Y, const int64_t* y_map, int64_t q, cudaStream_t s) {
-  if (ph.n_tiles == 0 || q == 0) return cudaSuccess;
-  if (q > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
-#define HMAT_GEMM_BN32(BMV)                                                                       \
-  if (q <= 32) return launch_f32<TY, BMV, 32>(h, ph, arena, X, x_map, Y, y_map, q, s);  \
-  return launch_f32<TY, BMV, 64>(h, ph, arena, X, x_map, Y, y_map, q, s);
-  switch (ph.tile_rows) {
-    case 16: { HMAT_GEMM_BN32(16) }
-    case 32: { HMAT_GEMM_BN32(32) }
-    default: {
-      // wide q: 128-column tiles read each block of A half as often (measured faster for
-      // q = 512, no different for q = 256)
-      if (q > 256) return launch_f32<TY, 64, 128>(h, ph, arena, X, x_map, Y, y_map, q, s);
-      HMAT_GEMM_BN32(64)
-    }
-  }
-#undef HMAT_GEMM_BN32
 }
 
 }  // namespace gemm

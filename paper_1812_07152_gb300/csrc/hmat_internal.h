@@ -130,6 +130,92 @@ struct TcProduct {
   int64_t n_chunks = 0;        // source k-chunks
 };
 
+// ---- the far chain of the mixed mode (hmat_chain.cu)
+//
+// The upward pass, the FP32 coupling reduction, the downward transfers and the
+// downward leaf step run as persistent launches over one list of CTA tiles ("items")
+// instead of one launch per phase and tree level (the role of coarsening,
+// Algorithm 2: no SM idles at a level boundary while the thin top levels run). A CTA
+// takes the next item with an atomic ticket, waits (bounded) until the items it
+// depends on are complete, computes its tile and counts it complete. Tickets are
+// taken in list order and every dependency points to an earlier item, so the item
+// with the lowest unfinished ticket can always run: no deadlock at any grid size.
+enum ChainKind : uint8_t {
+  CK_UP = 0,    // w_a = P_a^T W_a (leaf) or P_a^T [w_l; w_r]: needs the children's CK_UP
+  CK_CPL = 1,   // u_a = sum_b B_ab w_b: needs every CK_UP item of a's level
+  CK_DN = 2,    // [u_l; u_r] += P_a u_a: needs CK_CPL of a and of its children, CK_DN of its parent
+  CK_LEAF = 3   // Y_i += P_i u_i (FP64 Y through perm): needs CK_CPL of i, CK_DN of its parent
+};
+struct ChainItem {
+  int32_t tile;    // into Handle::tiles
+  int32_t node;    // the task's tree node (whose counter the item advances)
+  uint8_t kind;    // ChainKind
+  uint8_t cls;     // row tile: 0 -> 16 rows, 1 -> 32, 2 -> 64
+  uint8_t level;   // tree level of node
+  uint8_t xmap;    // 1: X rows through the coupling row map
+};
+// Which dependencies a launch waits for (the others are ordered by the stream).
+constexpr uint32_t kWaitUp = 1, kWaitLevel = 2, kWaitCpl = 4, kWaitDn = 8;
+
+// Everything an item needs of one evaluation of one HMatrix.
+struct ChainMember {
+  const GemmTile* tiles;
+  const GemmTask* tasks;
+  const GemmEntry* entries;   // FP32 entries (arena32 offsets)
+  const float* arena;         // arena32
+  const float* w32;           // W in tree order, FP32 (upward leaf input)
+  float* ws32;                // skeleton weights w
+  float* us32;                // skeleton potentials u
+  double* Y;                  // caller's output (CK_LEAF adds into it through perm)
+  const int64_t* perm;
+  const int64_t* far_rows;
+  const ChainItem* items;
+  const int32_t* expect;      // items per node of CK_UP, CK_CPL, CK_DN, then CK_UP items per level
+  int32_t* ctr;               // completed items (x column tiles), same layout as expect
+  int* status;                // the handle's status word
+  int64_t q;
+  int32_t n_ct;               // column tiles of bn columns
+  int32_t bn;                 // 32 or 64
+  int32_t n_nodes;
+  int32_t first_leaf;
+  int32_t xv;                 // q % 4 == 0: X rows copied 16 bytes at a time
+  int32_t pad;
+};
+
+// One persistent launch: tickets item_begin .. item_begin + n_items - 1 of member m,
+// each times m.n_ct column tiles.
+struct ChainLaunch {
+  int32_t item_begin;
+  int32_t n_items;
+  int32_t* ticket;            // this launch's ticket counter (zeroed before the evaluation)
+  int32_t* abort_flag;        // set by the first wait that gives up (zeroed likewise)
+  uint32_t waits;             // kWait* mask
+  int32_t extra;              // self-test: added to every requirement, so that every wait runs out
+  uint64_t limit_ns;          // a wait gives up after this long and latches HMAT_ETIMEOUT
+};
+
+// Ranges of a handle's chain items per launch: A (upward pass; with the FP32 coupling
+// also the coupling and the downward transfers), B (downward transfers after the
+// tensor-core coupling), C (downward leaf step).
+struct ChainPlan {
+  ChainItem* items = nullptr;     // device
+  int32_t* expect = nullptr;      // device, 3 * n_nodes + levels + 1
+  int32_t begin[3] = {0, 0, 0};
+  int32_t count[3] = {0, 0, 0};
+  uint32_t waits[3] = {0, 0, 0};
+  int64_t n_ctr = 0;              // counters: 4 (tickets A, B, C, abort) + the expect layout
+};
+constexpr int kChainCtrHead = 4;
+
+cudaError_t launch_chain(const ChainMember& m, const ChainLaunch& l, int grid_cap, cudaStream_t stream);
+// Sets the chain kernels' attributes on the current device (once) and returns the CTAs
+// that fit on it at once (16-byte X copies, 4-byte X copies; either may be null);
+// called at load, so that no launch (or graph capture) does it.
+cudaError_t chain_prepare(int* grid_v, int* grid_s);
+constexpr uint64_t kChainWaitNs = 2000000000ull;  // a chain wait gives up after 2 s
+// columns per chain tile for q
+inline int chain_bn(int64_t q) { return q <= 32 ? 32 : 64; }
+
 // The state one evaluation needs besides the read-only HMatrix: the workspaces
 // (carved from one device block for a given q and mode) and, for the mixed mode, a
 // side stream with its fork/join events. A handle owns a default context; a batch
@@ -146,6 +232,7 @@ struct EvalContext {
   float* w32 = nullptr;          // mixed: FP32 copy of W in tree order
   float* ws32 = nullptr;         // mixed: FP32 skeleton workspaces
   float* us32 = nullptr;
+  int32_t* chain_ctr = nullptr;  // mixed: tickets and completion counters of the far chain
   double* host_w = nullptr;      // device copies of W / Y for hmat_eval_host
   double* host_y = nullptr;
   int64_t host_cap = 0;          // values
@@ -162,6 +249,7 @@ struct TuneEntry {
   int mode = 0;
   std::vector<int8_t> shape;   // FP64: column shape (index into kColBN) per entry of Handle::phases
   int n_t = 0;                 // mixed: columns per tensor-core CTA
+  int chain_grid = 0;          // mixed: CTAs of the persistent far chain (0: every resident CTA)
   double default_ms = 0, tuned_ms = 0;
 };
 
@@ -201,6 +289,7 @@ struct Handle {
                                  // k-major: A(m, k) at [a_off + k * lda + m], lda a multiple
                                  // of 4 (rows m..lda-1 zero), a_off a multiple of 4
   GemmEntry* entries32 = nullptr;  // the entries with a_off/lda into arena32 (trans = 1)
+  ChainPlan chain;                 // the far field of the mixed mode as persistent launches
 
   // near blocks evaluated on the fly (HMAT_BUILD_NEAR_OTF): the arena holds no near
   // blocks; the near phase computes K(x_i, x_j) from the tree-ordered points
@@ -210,6 +299,7 @@ struct Handle {
   int32_t kernel = 0;
   double kernel_param = 0.0;
 
+  double* noalloc_scratch = nullptr;  // device address of hmat_eval_noalloc's static array
   struct EvalContext* ctx = nullptr;  // the handle's own evaluation state (hmat_eval)
   std::vector<TuneEntry> tuned;       // hmat_autotune results, one per (q, mode)
 
@@ -218,7 +308,7 @@ struct Handle {
     int32_t kind;
     cudaEvent_t start, stop;
   };
-  bool profiling = false;
+  int profiling = 0;               // 1: events around every launch; 2: the same, far chain serialised
   std::vector<ProfRecord> prof;
   std::vector<cudaEvent_t> event_pool;
   int64_t device_bytes = 0;
@@ -310,9 +400,10 @@ cudaError_t launch_tc_far(const TcProduct& p, const uint8_t* bsplit, const unsig
                           int64_t q, int n_t, int n_ct, int* status, cudaStream_t stream);
 // One bounded wait that nothing completes: sets HMAT_ETIMEOUT in *status after limit_ns.
 cudaError_t launch_wait_selftest(int* status, uint64_t limit_ns, cudaStream_t stream);
-// FP32 grouped GEMM of one far-field phase of the mixed mode (hmat_far32.cu).
-cudaError_t launch_f32_phase(const Handle& h, const Phase& ph, const float* X, const int64_t* x_map, void* Y,
-                             bool y_is_f64, const int64_t* y_map, int64_t q, cudaStream_t stream);
+
+// Device address of hmat_eval_noalloc's static workspace array on the current device
+// (hmat_noalloc.cu); looked up by every load, never by the evaluation itself.
+cudaError_t noalloc_scratch_address(double** out);
 
 // Evaluation contexts (hmat_eval.cpp).
 hmat_status ctx_create(const Handle& h, EvalContext** out);
@@ -322,6 +413,12 @@ void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* bas
 hmat_status ctx_reserve(const Handle& h, EvalContext* c, int64_t q, int mode);      // grow the own block
 // Enqueue Y = K~ W on `s` with the workspaces of `c` (bound for q and mode by the caller).
 hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int64_t q, int mode, cudaStream_t s);
+// The far chain of one mixed evaluation with the workspaces of c (bound for q): the
+// member description, launch `part` (0, 1, 2 = ChainPlan ranges A, B, C) and the grid cap
+// chosen by the autotuner.
+ChainMember chain_member(const Handle& h, const EvalContext* c, double* Y, int64_t q);
+ChainLaunch chain_launch(const Handle& h, const EvalContext* c, int part, int32_t extra, uint64_t limit_ns);
+int chain_grid_cap(const Handle& h, int64_t q);
 hmat_status cuda_status(cudaError_t e);
 
 // Launch the FP64 grouped GEMM of one phase on `stream`: column shape `shape` (-1:

@@ -3,36 +3,32 @@
 // allocate device memory during an evaluation (see include/hmat.h).
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "hmat_internal.h"
 
 namespace {
 
 constexpr int64_t kScratchValues = HMAT_NOALLOC_SCRATCH_VALUES;
-constexpr int kMaxDevices = 64;
 
 // The workspace of every no-alloc evaluation in this process on this device:
 // the first half holds the upward weights w, the second the downward potentials u.
 static __device__ __align__(256) double g_noalloc_scratch[kScratchValues];
 
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+}  // namespace
 
-// Device address of the array on device `dev` (looked up once per device, with it current).
-cudaError_t scratch_address(int dev, double** out) {
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = static_cast<double*>(g_scratch_addr[dev]);
-  return cudaSuccess;
+namespace hmat {
+
+// Device address of the array on the current device. Called by hmat_load and
+// hmat_build (which allocate anyway) with the handle's device current: under lazy
+// module loading the lookup is what loads this file's module and allocates the
+// array, so it must not happen inside hmat_eval_noalloc.
+cudaError_t noalloc_scratch_address(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  *out = e == cudaSuccess ? static_cast<double*>(p) : nullptr;
+  return e;
 }
 
-}  // namespace
+}  // namespace hmat
 
 using namespace hmat;
 
@@ -49,9 +45,8 @@ extern "C" hmat_status hmat_eval_noalloc(hmat_t h, const double* W, double* Y, i
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
   if (dev != h->device) return HMAT_EINVAL;
-  if (dev < 0 || dev >= kMaxDevices) return HMAT_EUNSUPPORTED;
-  double* base = nullptr;
-  if (scratch_address(dev, &base) != cudaSuccess) return HMAT_ECUDA;
+  double* base = h->noalloc_scratch;  // resolved when the handle was loaded
+  if (!base) return HMAT_ECUDA;
   double* ws = base;
   double* us = base + half;
   cudaStream_t s = (cudaStream_t)stream;

@@ -4,7 +4,8 @@
 // FP64 mode: per launch of the evaluation (one per phase and row-tile size), the
 // column tile of the grouped GEMM among the widths 1..64 that waste less than half
 // of a tile on padding. Mixed mode: the column width of the tensor-core near-field
-// CTAs (the number of CTAs that share one D tile). Every candidate sums each output
+// CTAs (the number of CTAs that share one D tile), then the number of CTAs of the
+// persistent far chain, timed on whole evaluations. Every candidate sums each output
 // in the same order, so a tuned evaluation gives bitwise the result of an untuned one;
 // only launch shapes change.
 #include <algorithm>
@@ -76,7 +77,7 @@ extern "C" hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
   if (dev != h->device) return HMAT_EINVAL;
-  if (report) *report = hmat_tune_report{q, mode, 0, 0.0, 0.0, 0};
+  if (report) *report = hmat_tune_report{q, mode, 0, 0.0, 0.0, 0, 0};
   if (h->n_points == 0) return HMAT_OK;
   cudaStream_t s = (cudaStream_t)stream;
 
@@ -203,6 +204,48 @@ extern "C" hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream
     entry.tuned_ms = t_best;
     near_cols = best;
     n_tuned = 1;
+    // the persistent far chain runs beside the near field and holds its CTAs until its
+    // last item: how many it should take is timed on whole evaluations (the default is
+    // every resident CTA); the result does not depend on it
+    if (h->chain.count[0] + h->chain.count[1] + h->chain.count[2] > 0) {
+      auto prev = std::find_if(h->tuned.begin(), h->tuned.end(),
+                               [&](const TuneEntry& t) { return t.q == q && t.mode == mode; });
+      const bool had = prev != h->tuned.end();
+      const TuneEntry saved = had ? *prev : TuneEntry{};
+      if (!had) h->tuned.push_back(entry);
+      TuneEntry* live = &*std::find_if(h->tuned.begin(), h->tuned.end(),
+                                       [&](const TuneEntry& t) { return t.q == q && t.mode == mode; });
+      *live = entry;
+      const int prof = h->profiling;
+      h->profiling = 0;
+      double c_def = -1, c_best = 1e30;
+      int g_best = 0;
+      for (int g : {0, 2 * sms, sms, sms / 2, sms / 4}) {
+        live->chain_grid = g;
+        const double t = timer.best([&] { return eval_impl(h, c, W, Y, q, mode, s) == HMAT_OK ? cudaSuccess
+                                                                                              : cudaErrorUnknown; });
+        if (t < 0) break;
+        if (g == 0) c_def = t;
+        if (t < c_best) {
+          c_best = t;
+          g_best = g;
+        }
+      }
+      h->profiling = prof;
+      if (had) {
+        *live = saved;
+      } else {
+        h->tuned.erase(h->tuned.begin() + (live - &h->tuned[0]));
+      }
+      if (c_def < 0) {
+        cleanup();
+        return HMAT_ECUDA;
+      }
+      entry.chain_grid = g_best;
+      entry.default_ms = c_def;
+      entry.tuned_ms = c_best;
+      n_tuned = 2;
+    }
   }
   cleanup();
   // a wait that ran out inside a timed launch is an error of the call
@@ -216,6 +259,28 @@ extern "C" hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream
     *it = entry;
   else
     h->tuned.push_back(entry);
-  if (report) *report = hmat_tune_report{q, mode, n_tuned, entry.default_ms, entry.tuned_ms, near_cols};
+  if (report)
+    *report = hmat_tune_report{q, mode, n_tuned, entry.default_ms, entry.tuned_ms, near_cols, entry.chain_grid};
+  return HMAT_OK;
+}
+
+extern "C" hmat_status hmat_tune_apply(hmat_t h, const hmat_tune_report* choice) {
+  if (!h || !choice || choice->q <= 0) return HMAT_EINVAL;
+  if (choice->mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
+  if (!h->has_mixed) return HMAT_EUNSUPPORTED;
+  const std::vector<int> cand = mixed_nt_candidates(choice->q);
+  const int n_t = choice->near_cols == 0 ? cand[0] : choice->near_cols;
+  if (std::find(cand.begin(), cand.end(), n_t) == cand.end() || choice->chain_grid < 0) return HMAT_EINVAL;
+  TuneEntry entry;
+  entry.q = choice->q;
+  entry.mode = choice->mode;
+  entry.n_t = n_t;
+  entry.chain_grid = choice->chain_grid;
+  auto it = std::find_if(h->tuned.begin(), h->tuned.end(),
+                         [&](const TuneEntry& t) { return t.q == entry.q && t.mode == entry.mode; });
+  if (it != h->tuned.end())
+    *it = entry;
+  else
+    h->tuned.push_back(entry);
   return HMAT_OK;
 }

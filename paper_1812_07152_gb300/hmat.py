@@ -27,7 +27,7 @@ HMAT_MODE_FP64 = 0
 HMAT_MODE_MIXED = 1
 HMAT_LOAD_MIXED = 1
 
-PHASES = ("near", "up_leaf", "up_transfer", "coupling", "down_transfer", "down_leaf", "split")
+PHASES = ("near", "up_leaf", "up_transfer", "coupling", "down_transfer", "down_leaf", "split", "far_up", "far_down")
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "lib", "libhmat.so")
@@ -112,7 +112,8 @@ class HmatServerParams(ctypes.Structure):
 
 class HmatTuneReport(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int64), ("mode", ctypes.c_int32), ("launches_tuned", ctypes.c_int32),
-                ("default_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double), ("near_cols", ctypes.c_int32)]
+                ("default_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double), ("near_cols", ctypes.c_int32),
+                ("chain_grid", ctypes.c_int32)]
 
 
 class HmatError(RuntimeError):
@@ -160,6 +161,8 @@ def library() -> ctypes.CDLL:
         lib.hmat_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.POINTER(HmatTuneReport)]
         lib.hmat_selftest_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        lib.hmat_tune_apply.argtypes = [ctypes.c_void_p, ctypes.POINTER(HmatTuneReport)]
+        lib.hmat_selftest_chain_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
         lib.hmat_selftest_conversions.argtypes = [ctypes.c_int64, ctypes.c_uint64, _c_i64p]
         lib.hmat_plan_create.argtypes = [ctypes.POINTER(HmatPlanParams), ctypes.POINTER(ctypes.c_void_p)]
         lib.hmat_plan_build.argtypes = [ctypes.c_void_p, ctypes.POINTER(HmatCompressParams), ctypes.c_int,
@@ -171,7 +174,8 @@ def library() -> ctypes.CDLL:
                      "hmat_info", "hmat_free", "hmat_eval_host", "hmat_profile", "hmat_phase_times",
                      "hmat_measure_fp64_peak", "hmat_batch_create", "hmat_batch_eval", "hmat_batch_free",
                      "hmat_server_create", "hmat_server_submit", "hmat_server_wait", "hmat_server_stats",
-                     "hmat_server_free", "hmat_autotune", "hmat_selftest_timeout", "hmat_plan_create", "hmat_plan_build",
+                     "hmat_server_free", "hmat_autotune", "hmat_selftest_timeout", "hmat_selftest_chain_timeout", "hmat_tune_apply",
+                     "hmat_plan_create", "hmat_plan_build",
                      "hmat_plan_free", "hmat_selftest_conversions"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -314,8 +318,11 @@ def hmat_eval_host(handle: int, W: np.ndarray, Y: np.ndarray, mode: int = HMAT_M
     _check(library().hmat_eval_host(handle, wp, yp, q, int(mode), _stream(stream)), "hmat_eval_host")
 
 
-def hmat_profile(handle: int, enable: bool = True) -> None:
-    _check(library().hmat_profile(handle, 1 if enable else 0), "hmat_profile")
+def hmat_profile(handle: int, enable=True) -> None:
+    """enable: True/1 (event timing of every launch), 2 (the same with the mixed mode's far chain serialised
+    on the caller's stream, so that each launch is timed alone) or False/0."""
+    _check(library().hmat_profile(handle, int(enable) if not isinstance(enable, bool) else (1 if enable else 0)),
+           "hmat_profile")
 
 
 def hmat_phase_times(handle: int) -> dict:
@@ -340,7 +347,16 @@ def hmat_autotune(handle: int, q: int, mode: int = HMAT_MODE_FP64, stream=None) 
     rep = HmatTuneReport()
     _check(library().hmat_autotune(handle, int(q), int(mode), _stream(stream), ctypes.byref(rep)), "hmat_autotune")
     return {"q": int(rep.q), "mode": int(rep.mode), "launches_tuned": int(rep.launches_tuned),
-            "default_ms": float(rep.default_ms), "tuned_ms": float(rep.tuned_ms), "near_cols": int(rep.near_cols)}
+            "default_ms": float(rep.default_ms), "tuned_ms": float(rep.tuned_ms), "near_cols": int(rep.near_cols),
+            "chain_grid": int(rep.chain_grid)}
+
+
+def hmat_tune_apply(handle: int, q: int, near_cols: int = 0, chain_grid: int = 0,
+                    mode: int = HMAT_MODE_MIXED) -> None:
+    """Install a mixed-mode choice for q columns without timing: near-field CTA width (0: default) and the
+    persistent far chain's CTAs (0: every resident CTA)."""
+    rep = HmatTuneReport(int(q), int(mode), 0, 0.0, 0.0, int(near_cols), int(chain_grid))
+    _check(library().hmat_tune_apply(handle, ctypes.byref(rep)), "hmat_tune_apply")
 
 
 def hmat_reserve(handle: int, q_max: int) -> None:
@@ -356,6 +372,13 @@ def hmat_selftest_timeout(handle: int, limit_ns: int, stream=None) -> None:
     """Enqueue one bounded device wait that runs out after limit_ns and latches
     HMAT_ETIMEOUT in the handle's status word (read it with hmat_status_poll)."""
     _check(library().hmat_selftest_timeout(handle, int(limit_ns), _stream(stream)), "hmat_selftest_timeout")
+
+
+def hmat_selftest_chain_timeout(handle: int, q: int, limit_ns: int, stream=None) -> None:
+    """Enqueue the mixed mode's persistent far-chain launch with requirements no item can meet: every wait
+    runs out after limit_ns and latches HMAT_ETIMEOUT in the handle's status word."""
+    _check(library().hmat_selftest_chain_timeout(handle, int(q), int(limit_ns), _stream(stream)),
+           "hmat_selftest_chain_timeout")
 
 
 def hmat_selftest_conversions(n: int, seed: int = 0) -> dict:

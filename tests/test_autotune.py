@@ -54,7 +54,9 @@ def test_mixed_autotune_is_bitwise_neutral(base, n, q):
     try:
         Y0 = _eval(h, W, hp.HMAT_MODE_MIXED)
         rep = hp.hmat_autotune(h, q, hp.HMAT_MODE_MIXED)
-        assert rep["launches_tuned"] == 1 and rep["near_cols"] % 16 == 0 and 16 <= rep["near_cols"] <= 128
+        # the near-field width, then (with a far field) the persistent far chain's grid on whole evaluations
+        assert rep["launches_tuned"] in (1, 2) and rep["near_cols"] % 16 == 0 and 16 <= rep["near_cols"] <= 128
+        assert rep["chain_grid"] >= 0
         assert 0 < rep["tuned_ms"] <= rep["default_ms"]
         Y1 = _eval(h, W, hp.HMAT_MODE_MIXED)
         assert np.array_equal(Y0, Y1)
