@@ -46,7 +46,7 @@ def parse_args():
                     help="also time the mixed-precision tensor-core mode on the same HMatrix")
     ap.add_argument("--batch", choices=["on", "off"], default="on",
                     help="also time the batched mode: 64 HMatrices of uneven N, d, kernel, leaf size and q")
-    ap.add_argument("--serve", choices=["short", "full", "off"], default="short",
+    ap.add_argument("--serve", choices=["short", "full", "off"], default="full",
                     help="also run the serving mode: a Poisson request stream on resident HMatrices "
                          "(short: 4 matrices N = 16K..128K, 6 s; full: 8 matrices N = 16K..1M, 2000 req/s, 60 s)")
     ap.add_argument("--precision", choices=["on", "off"], default="on",
@@ -726,9 +726,12 @@ def run_batch(args, dist) -> dict:
 
 
 def run_serving(args, dist) -> dict:
-    """Serving mode: resident HMatrices (d = 3 uniform points, Gaussian h = 0.5, tol 1e-6, leaf 256), a Poisson
-    stream of requests of q uniform in 1..256 on a random matrix, mixed precision, memory-bounded admission and
-    continuous batching; p50/p99 latency from submit to the result in pinned host memory."""
+    """Serving mode: resident HMatrices (d = 3 uniform points, Gaussian h = 0.5, tol 1e-6, leaf 256), loaded
+    mixed-only (the FP64 blocks dropped), a Poisson stream of requests of q uniform in 1..256 on a random matrix,
+    half of them FP32 and half FP64, memory-bounded admission, continuous batching and load shedding (a bounded
+    queue: a request that finds it full is refused and counted as dropped); p50/p99 latency from submit to the
+    result in pinned host memory, overall and per matrix. After the stream ends (60 s full, 6 s short) the queue
+    drains and the run stops."""
     import numpy as np
     import torch
     import paper_1812_07152_gb300 as hp
@@ -738,21 +741,26 @@ def run_serving(args, dist) -> dict:
     else:
         ws, rate, seconds = serving_workloads((16384, 32768, 65536, 131072)), 1000.0, 6.0
     t0 = time.perf_counter()
-    handles = [hp.hmat_build(make_points(w), flags=hp.HMAT_LOAD_MIXED, **build_params(w)) for w in ws]
+    handles = [hp.hmat_build(make_points(w), flags=hp.HMAT_LOAD_MIXED_ONLY, **build_params(w)) for w in ws]
     t_build = time.perf_counter() - t0
+    resident = sum(hp.hmat_info(h)["device_bytes"] for h in handles)
     q_max = 256
     rng = np.random.default_rng(7)
-    # one pinned W per matrix (read-only, shared by its requests) and a ring of pinned Y buffers
-    Wp = [torch.from_numpy(rng.standard_normal((w.n, q_max))).pin_memory() for w in ws]
-    ring = 16
-    Yp = [[torch.empty((w.n, q_max), dtype=torch.float64).pin_memory() for _ in range(ring)] for w in ws]
+    # one pinned W and one pinned Y per matrix and dtype: the requests on a matrix read column slices of its W and
+    # write column slices of its Y (concurrent requests overwrite each other's results there: this run measures
+    # time, the tests check results)
+    Wp = [{dt: torch.from_numpy(rng.standard_normal((w.n, q_max))).to(dt).pin_memory()
+           for dt in (torch.float64, torch.float32)} for w in ws]
+    Yp = [{dt: torch.empty((w.n, q_max), dtype=dt).pin_memory() for dt in (torch.float64, torch.float32)}
+          for w in ws]
     budget = 48 << 30
-    sv = hp.hmat_server_create(handles, slots=4, memory_budget=budget, max_q=4 * q_max, mode=hp.HMAT_MODE_MIXED)
-    ring_ids = [[None] * ring for _ in ws]
-    ring_pos = [0] * len(ws)
+    max_pending = 16
+    sv = hp.hmat_server_create(handles, slots=4, memory_budget=budget, max_q=4 * q_max, mode=hp.HMAT_MODE_MIXED,
+                               max_pending=max_pending)
+    ids = []
     t_start = time.perf_counter()
     t_next = t_start
-    submitted = cols = 0
+    offered = accepted = dropped = cols = 0
     while True:
         t_next += rng.exponential(1.0 / rate)
         if t_next - t_start > seconds:
@@ -762,28 +770,36 @@ def run_serving(args, dist) -> dict:
             time.sleep(t_next - now)
         m = int(rng.integers(0, len(ws)))
         q = int(rng.integers(1, q_max + 1))
-        k = ring_pos[m]
-        ring_pos[m] = (k + 1) % ring
-        if ring_ids[m][k] is not None:  # the ring slot's previous request must be done before its Y is reused
-            hp.hmat_server_wait(sv, ring_ids[m][k])
-        ring_ids[m][k] = hp.hmat_server_submit(sv, m, Wp[m][:, :q], Yp[m][k][:, :q])
-        submitted += 1
+        dt = torch.float32 if rng.random() < 0.5 else torch.float64
+        offered += 1
+        try:
+            ids.append(hp.hmat_server_submit(sv, m, Wp[m][dt][:, :q], Yp[m][dt][:, :q]))
+        except hp.HmatError as e:
+            if e.status != hp.HMAT_EBUSY:
+                raise
+            dropped += 1
+            continue
+        accepted += 1
         cols += q
-    for ids in ring_ids:
-        for rid in ids:
-            if rid is not None:
-                hp.hmat_server_wait(sv, rid)
+    t_stream = time.perf_counter() - t_start
+    failed = sum(hp.hmat_server_wait(sv, rid) != hp.HMAT_OK for rid in ids)
     elapsed = time.perf_counter() - t_start
     st = hp.hmat_server_stats(sv)
+    per = [dict(n=w.n, **hp.hmat_server_matrix_stats(sv, i)) for i, w in enumerate(ws)]
     hp.hmat_server_free(sv)
     for h in handles:
         hp.hmat_free(h)
     return {"matrices": [w.n for w in ws], "offered_req_per_s": rate, "seconds": seconds,
-            "requests": submitted, "value": round(cols / elapsed, 1), "unit": "cols/s",
-            "req_per_s": round(submitted / elapsed, 1), "p50_ms": round(st["p50_ms"], 3),
-            "p99_ms": round(st["p99_ms"], 3), "requests_per_evaluation": round(st["requests_per_evaluation"], 3),
-            "peak_device_bytes": int(st["peak_bytes"]), "memory_budget": budget, "slots": 4,
-            "mode": "mixed", "inspector_s": round(t_build, 2)}
+            "offered": offered, "served": accepted, "dropped": dropped, "failed": failed,
+            "value": round(cols / elapsed, 1), "unit": "cols/s",
+            "served_req_per_s": round(accepted / elapsed, 1), "stream_s": round(t_stream, 2),
+            "drain_s": round(elapsed - t_stream, 2),
+            "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+            "per_matrix": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in d.items()} for d in per],
+            "requests_per_evaluation": round(st["requests_per_evaluation"], 3),
+            "peak_device_bytes": int(st["peak_bytes"]), "resident_bytes": int(resident), "memory_budget": budget,
+            "max_pending": max_pending, "slots": 4, "mode": "mixed (FP64 blocks dropped)",
+            "dtypes": "half FP32, half FP64 W and Y", "inspector_s": round(t_build, 2)}
 
 
 def measured_traffic(key: str, near_values: int):

@@ -36,7 +36,8 @@ typedef enum {
   HMAT_ECUDA = -3,           /* a CUDA runtime call failed */
   HMAT_ETIMEOUT = -4,        /* a bounded device-side wait gave up */
   HMAT_EUNSUPPORTED = -5,    /* valid request that this build does not support */
-  HMAT_EDEVICE = -6          /* a kernel detected an inconsistent index or size */
+  HMAT_EDEVICE = -6,         /* a kernel detected an inconsistent index or size */
+  HMAT_EBUSY = -7            /* the server's queue is full: the request was not accepted */
 } hmat_status;
 
 /*
@@ -158,7 +159,8 @@ typedef struct {
  * The near blocks D and coupling blocks B are evaluated on the GPU directly into
  * the packed device arena (with HMAT_BUILD_NEAR_OTF the near blocks are not stored
  * but evaluated inside every FP64 evaluation). `flags`: any of HMAT_LOAD_MIXED,
- * HMAT_BUILD_ID_GPU, HMAT_BUILD_NEAR_OTF (not with HMAT_LOAD_MIXED); other bits:
+ * HMAT_LOAD_MIXED_ONLY, HMAT_BUILD_ID_GPU, HMAT_BUILD_NEAR_OTF (not with either
+ * mixed flag); other bits:
  * HMAT_EUNSUPPORTED. Synchronous; host threads as requested.
  */
 hmat_status hmat_build(const hmat_build_params* params, int flags, hmat_t* out);
@@ -235,6 +237,11 @@ hmat_status hmat_structure(hmat_t h, int64_t* perm, int32_t* rank, int64_t* near
 #define HMAT_LOAD_MIXED 1           /* also keep the tensor-core copy of the near blocks (FP16 hi/lo,
                                        4 bytes per value) and an FP32 copy of the bases and coupling
                                        blocks, for HMAT_MODE_MIXED */
+#define HMAT_LOAD_MIXED_ONLY 8      /* HMAT_LOAD_MIXED, then drop the FP64 blocks (8 bytes per stored
+                                       value): the handle serves HMAT_MODE_MIXED only (HMAT_MODE_FP64,
+                                       its autotuning and hmat_eval_noalloc return HMAT_EUNSUPPORTED), in
+                                       a third of the device memory; for memory-bound serving of many
+                                       resident matrices */
 
 /*
  * hmat_load - validate an HMatrix description, pack its blocks per tree level
@@ -243,8 +250,8 @@ hmat_status hmat_structure(hmat_t h, int64_t* perm, int32_t* rank, int64_t* near
  * Synchronous. Validation (HMAT_EINVAL, nothing allocated on failure): tree
  * shape and index ranges, CSR pointers non-decreasing, list ids in range, far
  * partners on the same level and distinct, perm a bijection, every non-empty
- * block pointer non-NULL and every stored value finite. `flags` is 0 or
- * HMAT_LOAD_MIXED (any other bit: HMAT_EUNSUPPORTED).
+ * block pointer non-NULL and every stored value finite. `flags` is 0,
+ * HMAT_LOAD_MIXED or HMAT_LOAD_MIXED_ONLY (any other bit: HMAT_EUNSUPPORTED).
  * The device is the one current at the call. Returns HMAT_ENOMEM when the
  * arena does not fit.
  */
@@ -265,6 +272,27 @@ hmat_status hmat_load(const hmat_desc* desc, int flags, hmat_t* out);
  */
 hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream);
 
+/*
+ * Element types of W and Y for the *_typed entry points (the evaluation mode is
+ * independent of them).
+ * HMAT_DTYPE_F64 - double.
+ * HMAT_DTYPE_F32 - float. In HMAT_MODE_FP64 the evaluation is the FP64 one of the
+ *   widened W (every sum in FP64) and Y is its value rounded to nearest once. In
+ *   HMAT_MODE_MIXED W is read as it is (the split and the far field start from FP32
+ *   anyway) and Y is written as the FP32 rounding of the mode's result. The
+ *   workspace of an FP64-mode evaluation with FP32 W and Y holds FP64 copies of both
+ *   (2 x n_points x q doubles more).
+ */
+#define HMAT_DTYPE_F64 0
+#define HMAT_DTYPE_F32 1
+
+/*
+ * hmat_eval_typed - hmat_eval for W and Y of element type `dtype` (n_points x q,
+ * device pointers, caller order); HMAT_EINVAL for another dtype. hmat_eval(h, W, Y,
+ * q, mode, stream) is hmat_eval_typed(h, W, Y, q, mode, HMAT_DTYPE_F64, stream).
+ */
+hmat_status hmat_eval_typed(hmat_t h, const void* W, void* Y, int64_t q, int mode, int dtype, void* stream);
+
 /* hmat_reserve - size the workspace for right-hand sides of up to q_max columns. */
 hmat_status hmat_reserve(hmat_t h, int64_t q_max);
 
@@ -280,6 +308,8 @@ hmat_status hmat_reserve(hmat_t h, int64_t q_max);
  * rounding (within the mixed mode's accuracy).
  */
 hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream);
+/* hmat_eval_host_typed - hmat_eval_host for host W and Y of element type `dtype`. */
+hmat_status hmat_eval_host_typed(hmat_t h, const void* W, void* Y, int64_t q, int mode, int dtype, void* stream);
 
 /*
  * hmat_profile - enable (1) or disable (0) CUDA-event timing of every kernel
@@ -432,6 +462,10 @@ typedef struct hmat_batch* hmat_batch_t;
 hmat_status hmat_batch_create(const hmat_t* handles, int count, int mode, hmat_batch_t* out);
 hmat_status hmat_batch_eval(hmat_batch_t b, const double* const* W, double* const* Y, const int64_t* q,
                             void* stream);
+/* hmat_batch_eval_typed - hmat_batch_eval with every member's W and Y of element type
+ * `dtype` (a call with another dtype than the captured graph's captures a new one). */
+hmat_status hmat_batch_eval_typed(hmat_batch_t b, const void* const* W, void* const* Y, const int64_t* q, int dtype,
+                                  void* stream);
 hmat_status hmat_batch_free(hmat_batch_t b);
 
 /*
@@ -460,7 +494,15 @@ hmat_status hmat_batch_free(hmat_batch_t b);
  * is forgotten once waited on (waiting again: HMAT_EINVAL).
  * hmat_server_stats - out[0] completed requests, out[1] p50 and out[2] p99
  * latency in ms (submit to result in host memory), out[3] mean requests per
- * evaluation, out[4] evaluations, out[5] peak device bytes in flight.
+ * evaluation, out[4] evaluations, out[5] peak device bytes in flight, out[6]
+ * requests refused with HMAT_EBUSY.
+ * hmat_server_matrix_stats - for one matrix: out[0] completed requests, out[1] p50
+ * and out[2] p99 latency in ms.
+ *
+ * Load shedding: with max_pending > 0, hmat_server_submit returns HMAT_EBUSY (and
+ * queues nothing) while max_pending requests wait for admission; a request stream
+ * beyond the device's rate is then served at that rate with bounded queueing delay
+ * instead of an unbounded queue.
  */
 typedef struct hmat_server* hmat_server_t;
 typedef struct {
@@ -468,13 +510,20 @@ typedef struct {
   int64_t memory_budget;    /* device bytes of the requests in flight (> 0) */
   int64_t max_q;            /* columns of one merged evaluation (>= 1) */
   int mode;                 /* HMAT_MODE_FP64 or HMAT_MODE_MIXED */
+  int64_t max_pending;      /* requests waiting for admission at most (0: no limit) */
 } hmat_server_params;
 hmat_status hmat_server_create(const hmat_t* handles, int count, const hmat_server_params* params,
                                hmat_server_t* out);
 hmat_status hmat_server_submit(hmat_server_t s, int matrix, const double* W, int64_t ldw, double* Y, int64_t ldy,
                                int64_t q, int64_t* id);
+/* hmat_server_submit_typed - hmat_server_submit for W and Y of element type `dtype`
+ * (strides in values of that type). Requests merge only with requests of the same
+ * matrix and dtype. */
+hmat_status hmat_server_submit_typed(hmat_server_t s, int matrix, const void* W, int64_t ldw, void* Y, int64_t ldy,
+                                     int64_t q, int dtype, int64_t* id);
 hmat_status hmat_server_wait(hmat_server_t s, int64_t id, int timeout_ms);
 hmat_status hmat_server_stats(hmat_server_t s, double* out, int n);
+hmat_status hmat_server_matrix_stats(hmat_server_t s, int matrix, double* out, int n);
 hmat_status hmat_server_free(hmat_server_t s);
 
 /*

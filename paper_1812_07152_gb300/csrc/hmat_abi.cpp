@@ -543,7 +543,8 @@ hmat_status cuda_status(cudaError_t e) {
 
 hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flags, hmat_handle** out) {
   *out = nullptr;
-  if (flags & ~(HMAT_LOAD_MIXED | HMAT_BUILD_NEAR_OTF)) return HMAT_EUNSUPPORTED;
+  if (flags & ~(HMAT_LOAD_MIXED | HMAT_LOAD_MIXED_ONLY | HMAT_BUILD_NEAR_OTF)) return HMAT_EUNSUPPORTED;
+  if (flags & HMAT_LOAD_MIXED_ONLY) flags |= HMAT_LOAD_MIXED;
   // blocks evaluated on the fly need the points (a build), and the FP64 mode
   if ((flags & HMAT_BUILD_NEAR_OTF) && (!src || (flags & HMAT_LOAD_MIXED))) return HMAT_EUNSUPPORTED;
   const bool near_otf = (flags & HMAT_BUILD_NEAR_OTF) != 0;
@@ -854,6 +855,13 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
   if (flags & HMAT_LOAD_MIXED) {
     hmat_status ms = build_mixed(h.get(), d, v, near_off, far_task_off, far_off, far_k, tasks, entries, tiles);
     if (ms == HMAT_OK) ms = build_chain(h.get(), v, tiles, task_node);
+    if (ms == HMAT_OK && (flags & HMAT_LOAD_MIXED_ONLY)) {
+      // the mixed mode reads only its own copies: the FP64 blocks are dropped
+      cudaFree(h->arena);
+      h->arena = nullptr;
+      h->device_bytes -= h->arena_values * (int64_t)sizeof(double);
+      h->has_fp64 = false;
+    }
     if (ms != HMAT_OK) {
       free_device(h.get());
       return ms;
@@ -914,7 +922,7 @@ extern "C" hmat_status hmat_selftest_timeout(hmat_t h, int64_t limit_ns, void* s
 
 extern "C" hmat_status hmat_info(hmat_t h, int64_t* out, int n_out) {
   if (!h || !out || n_out < 0) return HMAT_EINVAL;
-  const int64_t held = h->device_bytes + (h->ctx ? h->ctx->block_bytes + 16 * h->ctx->host_cap : 0);
+  const int64_t held = h->device_bytes + (h->ctx ? h->ctx->block_bytes + 2 * h->ctx->host_cap : 0);
   const int64_t engine = !h->has_mixed ? 0 : (h->tc_coupling ? 2 : 1);
   const int64_t vals[11] = {h->n_points, h->levels,          h->n_near,          h->n_far,
                             h->near_values, h->basis_values, h->coupling_values, h->sum_rank,
@@ -940,6 +948,7 @@ extern "C" const char* hmat_strerror(hmat_status s) {
     case HMAT_ETIMEOUT: return "a bounded device-side wait gave up";
     case HMAT_EUNSUPPORTED: return "unsupported request";
     case HMAT_EDEVICE: return "a kernel found an inconsistent index or size";
+    case HMAT_EBUSY: return "the server's queue is full";
   }
   return "unknown status";
 }

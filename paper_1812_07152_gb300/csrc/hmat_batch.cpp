@@ -19,9 +19,10 @@ struct hmat_batch {
   cudaEvent_t fork = nullptr;
   // the captured graph and the arguments it was captured for
   cudaGraphExec_t exec = nullptr;
-  std::vector<const double*> key_w;
-  std::vector<double*> key_y;
+  std::vector<const void*> key_w;
+  std::vector<void*> key_y;
   std::vector<int64_t> key_q;
+  int key_dtype = HMAT_DTYPE_F64;
 };
 
 namespace {
@@ -49,6 +50,7 @@ extern "C" hmat_status hmat_batch_create(const hmat_t* handles, int count, int m
   for (int i = 0; i < count; ++i) {
     if (!handles[i] || handles[i]->device != dev) return HMAT_EINVAL;
     if (mode == HMAT_MODE_MIXED && !handles[i]->has_mixed) return HMAT_EUNSUPPORTED;
+    if (mode == HMAT_MODE_FP64 && !handles[i]->has_fp64) return HMAT_EUNSUPPORTED;
   }
   hmat_batch* b = new (std::nothrow) hmat_batch();
   if (!b) return HMAT_ENOMEM;
@@ -80,9 +82,10 @@ extern "C" hmat_status hmat_batch_create(const hmat_t* handles, int count, int m
   return HMAT_OK;
 }
 
-extern "C" hmat_status hmat_batch_eval(hmat_batch_t b, const double* const* W, double* const* Y, const int64_t* q,
-                                       void* stream) {
+extern "C" hmat_status hmat_batch_eval_typed(hmat_batch_t b, const void* const* W, void* const* Y, const int64_t* q,
+                                             int dtype, void* stream) {
   if (!b || !W || !Y || !q) return HMAT_EINVAL;
+  if (dtype != HMAT_DTYPE_F64 && dtype != HMAT_DTYPE_F32) return HMAT_EINVAL;
   const int n = (int)b->handles.size();
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
@@ -95,14 +98,14 @@ extern "C" hmat_status hmat_batch_eval(hmat_batch_t b, const double* const* W, d
       if (b->mode == HMAT_MODE_MIXED && (q[i] + 127) / 128 > 65535) return HMAT_EUNSUPPORTED;
     }
   }
-  const bool same = b->exec && std::equal(W, W + n, b->key_w.begin()) && std::equal(Y, Y + n, b->key_y.begin()) &&
-                    std::equal(q, q + n, b->key_q.begin());
+  const bool same = b->exec && dtype == b->key_dtype && std::equal(W, W + n, b->key_w.begin()) &&
+                    std::equal(Y, Y + n, b->key_y.begin()) && std::equal(q, q + n, b->key_q.begin());
   cudaStream_t s = (cudaStream_t)stream;
   if (!same) {
     // workspaces first: allocation cannot happen inside a capture
     for (int i = 0; i < n; ++i) {
       if (q[i] == 0 || b->handles[i]->n_points == 0) continue;
-      hmat_status st = ctx_reserve(*b->handles[i], b->ctx[i], q[i], b->mode);
+      hmat_status st = ctx_reserve(*b->handles[i], b->ctx[i], q[i], b->mode, dtype);
       if (st != HMAT_OK) return st;
     }
     if (b->exec) {
@@ -123,7 +126,7 @@ extern "C" hmat_status hmat_batch_eval(hmat_batch_t b, const double* const* W, d
       if (q[i] == 0 || b->handles[i]->n_points == 0) continue;
       e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
       if (e != cudaSuccess) break;
-      st = eval_impl(b->handles[i], b->ctx[i], W[i], Y[i], q[i], b->mode, b->branch[i]);
+      st = eval_impl(b->handles[i], b->ctx[i], W[i], Y[i], q[i], b->mode, dtype, b->branch[i]);
       if (st != HMAT_OK) break;
       e = cudaEventRecord(b->join[i], b->branch[i]);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(b->capture, b->join[i], 0);
@@ -142,8 +145,15 @@ extern "C" hmat_status hmat_batch_eval(hmat_batch_t b, const double* const* W, d
     b->key_w.assign(W, W + n);
     b->key_y.assign(Y, Y + n);
     b->key_q.assign(q, q + n);
+    b->key_dtype = dtype;
   }
   return cuda_status(cudaGraphLaunch(b->exec, s));
+}
+
+extern "C" hmat_status hmat_batch_eval(hmat_batch_t b, const double* const* W, double* const* Y, const int64_t* q,
+                                       void* stream) {
+  return hmat_batch_eval_typed(b, reinterpret_cast<const void* const*>(W), reinterpret_cast<void* const*>(Y), q,
+                               HMAT_DTYPE_F64, stream);
 }
 
 extern "C" hmat_status hmat_batch_free(hmat_batch_t b) {

@@ -187,7 +187,12 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__
         break;
       case CK_CPL: chain_tile_bn<float, XV>(m, it, q0, m.ws32, m.far_rows, m.us32, nullptr, smf); break;
       case CK_DN: chain_tile_bn<float, XV>(m, it, q0, m.us32, nullptr, m.us32, nullptr, smf); break;
-      default: chain_tile_bn<double, XV>(m, it, q0, m.us32, nullptr, m.Y, m.perm, smf); break;
+      default:
+        if (m.y_f32)
+          chain_tile_bn<float, XV>(m, it, q0, m.us32, nullptr, static_cast<float*>(m.Y), m.perm, smf);
+        else
+          chain_tile_bn<double, XV>(m, it, q0, m.us32, nullptr, static_cast<double*>(m.Y), m.perm, smf);
+        break;
     }
     __syncthreads();  // the tile's outputs are written and its shared memory is free again
     if (threadIdx.x == 0 && it.kind != CK_LEAF) {  // nothing waits for a leaf item

@@ -50,15 +50,17 @@ bool prof_end(Handle* h, const Handle::ProfRecord& rec, cudaStream_t s) {
   return true;
 }
 
-hmat_status check_call(const Handle* h, const double* W, const double* Y, int64_t q, int mode) {
+hmat_status check_call(const Handle* h, const void* W, const void* Y, int64_t q, int mode, int dtype) {
   if (!h || q < 0) return HMAT_EINVAL;
+  if (dtype != HMAT_DTYPE_F64 && dtype != HMAT_DTYPE_F32) return HMAT_EINVAL;
   if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
   if (mode == HMAT_MODE_MIXED && !h->has_mixed) return HMAT_EUNSUPPORTED;
+  if (mode == HMAT_MODE_FP64 && !h->has_fp64) return HMAT_EUNSUPPORTED;
   if (q == 0 || h->n_points == 0) return HMAT_OK;
   if (!W || !Y || W == Y) return HMAT_EINVAL;
   const char* w0 = (const char*)W;
   const char* y0 = (const char*)Y;
-  const int64_t bytes = h->n_points * q * (int64_t)sizeof(double);
+  const int64_t bytes = h->n_points * q * dtype_bytes(dtype);
   if (w0 < y0 + bytes && y0 < w0 + bytes) return HMAT_EINVAL;  // W and Y overlap
   if (mode == HMAT_MODE_MIXED && (q + 127) / 128 > 65535) return HMAT_EUNSUPPORTED;
   int dev = -1;
@@ -140,7 +142,7 @@ void ctx_destroy(EvalContext* c) {
   delete c;
 }
 
-int64_t ctx_bytes(const Handle& h, int64_t q, int mode) {
+int64_t ctx_bytes(const Handle& h, int64_t q, int mode, int dtype) {
   const int64_t r = std::max<int64_t>(h.sum_rank, 1);
   if (mode == HMAT_MODE_MIXED) {
     const int64_t cols = mixed_cols_bound(q);
@@ -149,10 +151,11 @@ int64_t ctx_bytes(const Handle& h, int64_t q, int mode) {
            align_up(std::max<int64_t>(h.n_points, 1) * q * 4) + 2 * align_up(r * q * 4) +
            align_up(h.chain.n_ctr * 4);
   }
-  return 2 * align_up(r * q * 8);
+  const int64_t io = dtype == HMAT_DTYPE_F32 ? 2 * align_up(std::max<int64_t>(h.n_points, 1) * q * 8) : 0;
+  return 2 * align_up(r * q * 8) + io;
 }
 
-void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* base) {
+void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* base, int dtype) {
   const int64_t r = std::max<int64_t>(h.sum_rank, 1);
   uint8_t* p = base;
   auto take = [&](int64_t bytes) {
@@ -161,6 +164,7 @@ void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* bas
     return x;
   };
   c->ws = c->us = nullptr;
+  c->w64 = c->y64 = nullptr;
   c->wmax = c->smax = nullptr;
   c->wsplit = c->ssplit = nullptr;
   c->w32 = c->ws32 = c->us32 = nullptr;
@@ -178,11 +182,15 @@ void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* bas
   } else {
     c->ws = (double*)take(r * q * 8);
     c->us = (double*)take(r * q * 8);
+    if (dtype == HMAT_DTYPE_F32) {
+      c->w64 = (double*)take(std::max<int64_t>(h.n_points, 1) * q * 8);
+      c->y64 = (double*)take(std::max<int64_t>(h.n_points, 1) * q * 8);
+    }
   }
 }
 
-hmat_status ctx_reserve(const Handle& h, EvalContext* c, int64_t q, int mode) {
-  const int64_t need = ctx_bytes(h, q, mode);
+hmat_status ctx_reserve(const Handle& h, EvalContext* c, int64_t q, int mode, int dtype) {
+  const int64_t need = ctx_bytes(h, q, mode, dtype);
   if (need > c->block_bytes) {
     uint8_t* p = nullptr;
     cudaError_t e = cudaMalloc((void**)&p, (size_t)need);
@@ -195,11 +203,11 @@ hmat_status ctx_reserve(const Handle& h, EvalContext* c, int64_t q, int mode) {
     c->block = p;
     c->block_bytes = need;
   }
-  ctx_bind(h, c, q, mode, c->block);
+  ctx_bind(h, c, q, mode, c->block, dtype);
   return HMAT_OK;
 }
 
-ChainMember chain_member(const Handle& h, const EvalContext* c, double* Y, int64_t q) {
+ChainMember chain_member(const Handle& h, const EvalContext* c, void* Y, bool y_f32, int64_t q) {
   ChainMember m{};
   m.tiles = h.tiles;
   m.tasks = h.tasks;
@@ -221,6 +229,7 @@ ChainMember chain_member(const Handle& h, const EvalContext* c, double* Y, int64
   m.n_nodes = (int32_t)h.n_nodes;
   m.first_leaf = (int32_t)(h.n_leaves - 1);
   m.xv = q % 4 == 0 ? 1 : 0;
+  m.y_f32 = y_f32 ? 1 : 0;
   return m;
 }
 
@@ -241,7 +250,9 @@ int chain_grid_cap(const Handle& h, int64_t q) {
   return t ? t->chain_grid : 0;
 }
 
-hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int64_t q, int mode, cudaStream_t s) {
+hmat_status eval_impl(Handle* h, EvalContext* c, const void* W, void* Y, int64_t q, int mode, int dtype,
+                      cudaStream_t s) {
+  const bool f32 = dtype == HMAT_DTYPE_F32;
   Handle::ProfRecord rec{};
   hmat_status st = HMAT_OK;
   cudaError_t e = cudaSuccess;
@@ -250,7 +261,10 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
     int64_t n_ct;
     mixed_tiles(*h, q, &n_t, &n_ct);
     if (!prof_begin(h, HMAT_PHASE_SPLIT, s, &rec)) return HMAT_ECUDA;
-    e = launch_split_f64(h->tc_near, W, h->n_points * q, h->perm, q, n_t, (int)n_ct, c->wmax, c->wsplit, c->w32, s);
+    e = f32 ? launch_split_f32(h->tc_near, (const float*)W, h->n_points * q, h->perm, q, n_t, (int)n_ct, c->wmax,
+                               c->wsplit, c->w32, s)
+            : launch_split_f64(h->tc_near, (const double*)W, h->n_points * q, h->perm, q, n_t, (int)n_ct, c->wmax,
+                               c->wsplit, c->w32, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;
     // the far chain on the side stream (beside the near field), or on s when profiling
@@ -260,7 +274,7 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
     if (!serial &&
         (cudaEventRecord(c->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(c->aux, c->ev_fork, 0) != cudaSuccess))
       return HMAT_ECUDA;
-    ChainMember cm = chain_member(*h, c, Y, q);
+    ChainMember cm = chain_member(*h, c, Y, f32, q);
     auto chain = [&](int part, int32_t kind, cudaStream_t strm) -> hmat_status {
       if (h->chain.count[part] == 0) return HMAT_OK;
       if (!prof_begin(h, kind, strm, &rec)) return HMAT_ECUDA;
@@ -273,8 +287,8 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
     if ((st = chain(0, HMAT_PHASE_FAR_UP, far)) != HMAT_OK) return st;
     if (h->tc_coupling && h->tc_far.n_work > 0) {
       if (!prof_begin(h, HMAT_PHASE_SPLIT, far, &rec)) return HMAT_ECUDA;
-      e = launch_split_f32(h->tc_far, c->ws32, std::max<int64_t>(h->sum_rank, 1) * q, q, n_t, (int)n_ct, c->smax,
-                           c->ssplit, far);
+      e = launch_split_f32(h->tc_far, c->ws32, std::max<int64_t>(h->sum_rank, 1) * q, nullptr, q, n_t, (int)n_ct,
+                           c->smax, c->ssplit, nullptr, far);
       if (e != cudaSuccess) return cuda_status(e);
       if (!prof_end(h, rec, far)) return HMAT_ECUDA;
       if (!prof_begin(h, HMAT_PHASE_COUPLING, far, &rec)) return HMAT_ECUDA;
@@ -286,18 +300,22 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
     if ((st = chain(1, HMAT_PHASE_FAR_DOWN, far)) != HMAT_OK) return st;
     if (!serial && cudaEventRecord(c->ev_join, c->aux) != cudaSuccess) return HMAT_ECUDA;
     if (!prof_begin(h, HMAT_PHASE_NEAR, s, &rec)) return HMAT_ECUDA;
-    e = launch_tc_near(h->tc_near, c->wsplit, c->wmax, h->perm, Y, q, n_t, (int)n_ct, h->status, s);
+    e = launch_tc_near(h->tc_near, c->wsplit, c->wmax, h->perm, Y, f32, q, n_t, (int)n_ct, h->status, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;
     if (!serial && cudaStreamWaitEvent(s, c->ev_join, 0) != cudaSuccess) return HMAT_ECUDA;
     // downward leaf step: adds into Y after the near field has written it
     return chain(2, HMAT_PHASE_DOWN_LEAF, s);
   }
+  // FP64 mode: FP32 W is widened into the workspace and Y rounded from it at the end
+  const double* W64 = f32 ? c->w64 : (const double*)W;
+  double* Y64 = f32 ? c->y64 : (double*)Y;
+  if (f32 && (e = launch_widen((const float*)W, c->w64, h->n_points * q, s)) != cudaSuccess) return cuda_status(e);
   const TuneEntry* tuned = find_tuned(*h, q, HMAT_MODE_FP64);
   for (size_t i = 0; i < h->phases.size(); ++i) {
     const Phase& ph = h->phases[i];
-    const double* X = ph.x == MAT_USER ? W : (ph.x == MAT_SKEL_W ? c->ws : c->us);
-    double* Yd = ph.y == MAT_USER ? Y : (ph.y == MAT_SKEL_W ? c->ws : c->us);
+    const double* X = ph.x == MAT_USER ? W64 : (ph.x == MAT_SKEL_W ? c->ws : c->us);
+    double* Yd = ph.y == MAT_USER ? Y64 : (ph.y == MAT_SKEL_W ? c->ws : c->us);
     const int64_t* xm = phase_x_map(*h, ph);
     const int64_t* ym = ph.y == MAT_USER ? h->perm : nullptr;
     const int shape = tuned && i < tuned->shape.size() ? tuned->shape[i] : -1;
@@ -306,6 +324,7 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;
   }
+  if (f32) return cuda_status(launch_narrow(c->y64, (float*)Y, h->n_points * q, s));
   return HMAT_OK;
 }
 
@@ -319,30 +338,41 @@ extern "C" hmat_status hmat_reserve(hmat_t h, int64_t q_max) {
   if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
   if (dev != h->device) return HMAT_EINVAL;
   if (q_max == 0) return HMAT_OK;
-  const int mode = h->has_mixed && ctx_bytes(*h, q_max, HMAT_MODE_MIXED) > ctx_bytes(*h, q_max, HMAT_MODE_FP64)
+  const int mode = h->has_mixed && (!h->has_fp64 || ctx_bytes(*h, q_max, HMAT_MODE_MIXED) >
+                                                          ctx_bytes(*h, q_max, HMAT_MODE_FP64))
                        ? HMAT_MODE_MIXED
                        : HMAT_MODE_FP64;
   return ctx_reserve(*h, h->ctx, q_max, mode);
 }
 
-extern "C" hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
-  hmat_status st = check_call(h, W, Y, q, mode);
+extern "C" hmat_status hmat_eval_typed(hmat_t h, const void* W, void* Y, int64_t q, int mode, int dtype,
+                                       void* stream) {
+  hmat_status st = check_call(h, W, Y, q, mode, dtype);
   if (st != HMAT_OK || q == 0 || h->n_points == 0) return st;
-  if ((st = ctx_reserve(*h, h->ctx, q, mode)) != HMAT_OK) return st;
-  return eval_impl(h, h->ctx, W, Y, q, mode, (cudaStream_t)stream);
+  if ((st = ctx_reserve(*h, h->ctx, q, mode, dtype)) != HMAT_OK) return st;
+  return eval_impl(h, h->ctx, W, Y, q, mode, dtype, (cudaStream_t)stream);
 }
 
-extern "C" hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
+extern "C" hmat_status hmat_eval(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
+  return hmat_eval_typed(h, W, Y, q, mode, HMAT_DTYPE_F64, stream);
+}
+
+extern "C" hmat_status hmat_eval_host_typed(hmat_t h, const void* W, void* Y, int64_t q, int mode, int dtype,
+                                            void* stream) {
   if (!h || q < 0) return HMAT_EINVAL;
+  if (dtype != HMAT_DTYPE_F64 && dtype != HMAT_DTYPE_F32) return HMAT_EINVAL;
   if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
+  if ((mode == HMAT_MODE_MIXED && !h->has_mixed) || (mode == HMAT_MODE_FP64 && !h->has_fp64))
+    return HMAT_EUNSUPPORTED;
   if (q == 0 || h->n_points == 0) return HMAT_OK;
   if (!W || !Y) return HMAT_EINVAL;
   EvalContext* c = h->ctx;
-  const int64_t values = h->n_points * q;
-  if (values > c->host_cap) {
-    double *w = nullptr, *y = nullptr;
-    cudaError_t e = cudaMalloc((void**)&w, (size_t)values * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&y, (size_t)values * sizeof(double));
+  const int64_t es = dtype_bytes(dtype);
+  const int64_t bytes = h->n_points * q * es;
+  if (bytes > c->host_cap) {
+    void *w = nullptr, *y = nullptr;
+    cudaError_t e = cudaMalloc(&w, (size_t)bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&y, (size_t)bytes);
     if (e != cudaSuccess) {
       cudaFree(w);
       cudaGetLastError();
@@ -353,7 +383,7 @@ extern "C" hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int6
     cudaFree(c->host_y);
     c->host_w = w;
     c->host_y = y;
-    c->host_cap = values;
+    c->host_cap = bytes;
   }
   cudaStream_t s = (cudaStream_t)stream;
   if (mode == HMAT_MODE_MIXED && q >= 2 * kHostSplitMinQ) {
@@ -368,47 +398,50 @@ extern "C" hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int6
     }
     const int64_t n = h->n_points;
     const int64_t qa = std::min<int64_t>(q - 16, (q / 2 + 15) / 16 * 16), qb = q - qa;
-    double* wa = c->host_w;
-    double* wb = c->host_w + n * qa;
-    double* ya = c->host_y;
-    double* yb = c->host_y + n * qa;
+    char* wa = (char*)c->host_w;
+    char* wb = wa + n * qa * es;
+    char* ya = (char*)c->host_y;
+    char* yb = ya + n * qa * es;
     cudaEvent_t* ev = c->ev_copy;
-    const size_t pitch = (size_t)q * sizeof(double);
+    const size_t pitch = (size_t)(q * es);
+    const char* Wc = (const char*)W;
+    char* Yc = (char*)Y;
     cudaError_t e = cudaEventRecord(ev[0], s);  // earlier work on s that used these buffers
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy, ev[0], 0);
     if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(wa, qa * sizeof(double), W, pitch, qa * sizeof(double), n, cudaMemcpyHostToDevice, c->copy);
+      e = cudaMemcpy2DAsync(wa, qa * es, Wc, pitch, qa * es, n, cudaMemcpyHostToDevice, c->copy);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->copy);
     if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(wb, qb * sizeof(double), W + qa, pitch, qb * sizeof(double), n, cudaMemcpyHostToDevice,
-                            c->copy);
+      e = cudaMemcpy2DAsync(wb, qb * es, Wc + qa * es, pitch, qb * es, n, cudaMemcpyHostToDevice, c->copy);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->copy);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
     if (e != cudaSuccess) return cuda_status(e);
-    hmat_status st = hmat_eval(h, wa, ya, qa, mode, stream);
+    hmat_status st = hmat_eval_typed(h, wa, ya, qa, mode, dtype, stream);
     if (st != HMAT_OK) return st;
     if ((e = cudaEventRecord(ev[3], s)) != cudaSuccess || (e = cudaStreamWaitEvent(s, ev[2], 0)) != cudaSuccess)
       return cuda_status(e);
-    if ((st = hmat_eval(h, wb, yb, qb, mode, stream)) != HMAT_OK) return st;
+    if ((st = hmat_eval_typed(h, wb, yb, qb, mode, dtype, stream)) != HMAT_OK) return st;
     e = cudaEventRecord(ev[4], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy, ev[3], 0);
     if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(Y, pitch, ya, qa * sizeof(double), qa * sizeof(double), n, cudaMemcpyDeviceToHost, c->copy);
+      e = cudaMemcpy2DAsync(Yc, pitch, ya, qa * es, qa * es, n, cudaMemcpyDeviceToHost, c->copy);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy, ev[4], 0);
     if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(Y + qa, pitch, yb, qb * sizeof(double), qb * sizeof(double), n, cudaMemcpyDeviceToHost,
-                            c->copy);
+      e = cudaMemcpy2DAsync(Yc + qa * es, pitch, yb, qb * es, qb * es, n, cudaMemcpyDeviceToHost, c->copy);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy);
     return cuda_status(e);
   }
-  const size_t bytes = (size_t)values * sizeof(double);
-  cudaError_t e = cudaMemcpyAsync(c->host_w, W, bytes, cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(c->host_w, W, (size_t)bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
-  hmat_status st = hmat_eval(h, c->host_w, c->host_y, q, mode, stream);
+  hmat_status st = hmat_eval_typed(h, c->host_w, c->host_y, q, mode, dtype, stream);
   if (st != HMAT_OK) return st;
-  e = cudaMemcpyAsync(Y, c->host_y, bytes, cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(Y, c->host_y, (size_t)bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return cuda_status(e);
+}
+
+extern "C" hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int64_t q, int mode, void* stream) {
+  return hmat_eval_host_typed(h, W, Y, q, mode, HMAT_DTYPE_F64, stream);
 }
 
 extern "C" hmat_status hmat_selftest_chain_timeout(hmat_t h, int64_t q, int64_t limit_ns, void* stream) {
@@ -424,7 +457,7 @@ extern "C" hmat_status hmat_selftest_chain_timeout(hmat_t h, int64_t q, int64_t 
   cudaError_t e = cudaMemsetAsync(h->ctx->chain_ctr, 0, (size_t)h->chain.n_ctr * 4, s);
   if (e != cudaSuccess) return cuda_status(e);
   // the workspaces are not filled: the launch waits before it reads or writes any of them
-  const ChainMember m = chain_member(*h, h->ctx, nullptr, q);
+  const ChainMember m = chain_member(*h, h->ctx, nullptr, false, q);
   return cuda_status(launch_chain(m, chain_launch(*h, h->ctx, 0, 1, (uint64_t)limit_ns), 0, s));
 }
 

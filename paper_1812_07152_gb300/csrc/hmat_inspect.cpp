@@ -571,8 +571,9 @@ hmat_status row_ids_gpu(const hmat_plan& pl, const hmat_compress_params& c, cons
 extern "C" hmat_status hmat_plan_build(hmat_plan_t pl, const hmat_compress_params* c, int flags, hmat_t* out) {
   if (!out) return HMAT_EINVAL;
   *out = nullptr;
-  if (flags & ~(HMAT_LOAD_MIXED | HMAT_BUILD_ID_GPU | HMAT_BUILD_NEAR_OTF)) return HMAT_EUNSUPPORTED;
-  if ((flags & HMAT_BUILD_NEAR_OTF) && (flags & HMAT_LOAD_MIXED)) return HMAT_EUNSUPPORTED;
+  if (flags & ~(HMAT_LOAD_MIXED | HMAT_LOAD_MIXED_ONLY | HMAT_BUILD_ID_GPU | HMAT_BUILD_NEAR_OTF))
+    return HMAT_EUNSUPPORTED;
+  if ((flags & HMAT_BUILD_NEAR_OTF) && (flags & (HMAT_LOAD_MIXED | HMAT_LOAD_MIXED_ONLY))) return HMAT_EUNSUPPORTED;
   if (!pl || !valid_compress(c)) return HMAT_EINVAL;
   const Tree& t = pl->t;
   const int64_t n = pl->n;
@@ -681,14 +682,15 @@ extern "C" hmat_status hmat_plan_build(hmat_plan_t pl, const hmat_compress_param
   desc.near = nullptr;
   desc.perm = t.perm.data();
   DeviceBlockSource src{Xt.data(), d, skel_points.data(), c->kernel, c->kernel_param};
-  return load_impl(&desc, &src, flags & (HMAT_LOAD_MIXED | HMAT_BUILD_NEAR_OTF), out);
+  return load_impl(&desc, &src, flags & (HMAT_LOAD_MIXED | HMAT_LOAD_MIXED_ONLY | HMAT_BUILD_NEAR_OTF), out);
 }
 
 extern "C" hmat_status hmat_build(const hmat_build_params* p, int flags, hmat_t* out) {
   if (!out) return HMAT_EINVAL;
   *out = nullptr;
-  if (flags & ~(HMAT_LOAD_MIXED | HMAT_BUILD_ID_GPU | HMAT_BUILD_NEAR_OTF)) return HMAT_EUNSUPPORTED;
-  if ((flags & HMAT_BUILD_NEAR_OTF) && (flags & HMAT_LOAD_MIXED)) return HMAT_EUNSUPPORTED;
+  if (flags & ~(HMAT_LOAD_MIXED | HMAT_LOAD_MIXED_ONLY | HMAT_BUILD_ID_GPU | HMAT_BUILD_NEAR_OTF))
+    return HMAT_EUNSUPPORTED;
+  if ((flags & HMAT_BUILD_NEAR_OTF) && (flags & (HMAT_LOAD_MIXED | HMAT_LOAD_MIXED_ONLY))) return HMAT_EUNSUPPORTED;
   if (!p) return HMAT_EINVAL;
   const hmat_compress_params c{p->kernel, p->kernel_param, p->tol, p->max_rank, p->exact_columns, p->sample_seed};
   if (!valid_compress(&c)) return HMAT_EINVAL;

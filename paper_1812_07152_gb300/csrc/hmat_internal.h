@@ -166,7 +166,7 @@ struct ChainMember {
   const float* w32;           // W in tree order, FP32 (upward leaf input)
   float* ws32;                // skeleton weights w
   float* us32;                // skeleton potentials u
-  double* Y;                  // caller's output (CK_LEAF adds into it through perm)
+  void* Y;                    // caller's output (CK_LEAF adds into it through perm): FP64, or FP32 when y_f32
   const int64_t* perm;
   const int64_t* far_rows;
   const ChainItem* items;
@@ -179,7 +179,7 @@ struct ChainMember {
   int32_t n_nodes;
   int32_t first_leaf;
   int32_t xv;                 // q % 4 == 0: X rows copied 16 bytes at a time
-  int32_t pad;
+  int32_t y_f32;              // Y holds FP32 values
 };
 
 // One persistent launch: tickets item_begin .. item_begin + n_items - 1 of member m,
@@ -233,9 +233,11 @@ struct EvalContext {
   float* ws32 = nullptr;         // mixed: FP32 skeleton workspaces
   float* us32 = nullptr;
   int32_t* chain_ctr = nullptr;  // mixed: tickets and completion counters of the far chain
-  double* host_w = nullptr;      // device copies of W / Y for hmat_eval_host
-  double* host_y = nullptr;
-  int64_t host_cap = 0;          // values
+  double* w64 = nullptr;         // FP64 mode with FP32 W and Y: W widened, Y before rounding (n x q each)
+  double* y64 = nullptr;
+  void* host_w = nullptr;        // device copies of W / Y for hmat_eval_host
+  void* host_y = nullptr;
+  int64_t host_cap = 0;          // bytes of each
   cudaStream_t copy = nullptr;   // hmat_eval_host: host <-> device copies beside the evaluation
   cudaEvent_t ev_copy[5] = {};
   cudaStream_t aux = nullptr;    // mixed: the far chain runs here, beside the near field
@@ -279,8 +281,9 @@ struct Handle {
   GemmTile* tiles = nullptr;
   int* status = nullptr;         // device status word (hmat_status of the first error)
 
-  // mixed precision (HMAT_LOAD_MIXED)
+  // mixed precision (HMAT_LOAD_MIXED); without the FP64 blocks (HMAT_LOAD_MIXED_ONLY)
   bool has_mixed = false;
+  bool has_fp64 = true;
   TcProduct tc_near;             // near field D_ij on the tensor cores
   TcProduct tc_far;              // coupling B_ab on the tensor cores (when tc_coupling)
   bool tc_coupling = false;      // mixed coupling engine: tensor cores, else FP32 CUDA cores
@@ -390,11 +393,12 @@ cudaError_t launch_relayout_f32(const double* arena, const F32Job* jobs, int64_t
 cudaError_t launch_split_f64(const TcProduct& p, const double* X, int64_t n_values, const int64_t* perm, int64_t q,
                              int n_t, int n_ct, unsigned long long* xmax, uint8_t* out, float* x32,
                              cudaStream_t stream);
-cudaError_t launch_split_f32(const TcProduct& p, const float* X, int64_t n_values, int64_t q, int n_t, int n_ct,
-                             unsigned long long* xmax, uint8_t* out, cudaStream_t stream);
-// Y (FP64, rows through perm) = near field; or U (FP32, node rows) = coupling.
+cudaError_t launch_split_f32(const TcProduct& p, const float* X, int64_t n_values, const int64_t* perm, int64_t q,
+                             int n_t, int n_ct, unsigned long long* xmax, uint8_t* out, float* x32,
+                             cudaStream_t stream);
+// Y (FP64, or FP32 when y_f32; rows through perm) = near field; or U (FP32, node rows) = coupling.
 cudaError_t launch_tc_near(const TcProduct& p, const uint8_t* bsplit, const unsigned long long* bmax,
-                           const int64_t* perm, double* Y, int64_t q, int n_t, int n_ct, int* status,
+                           const int64_t* perm, void* Y, bool y_f32, int64_t q, int n_t, int n_ct, int* status,
                            cudaStream_t stream);
 cudaError_t launch_tc_far(const TcProduct& p, const uint8_t* bsplit, const unsigned long long* bmax, float* U,
                           int64_t q, int n_t, int n_ct, int* status, cudaStream_t stream);
@@ -405,18 +409,25 @@ cudaError_t launch_wait_selftest(int* status, uint64_t limit_ns, cudaStream_t st
 // (hmat_noalloc.cu); looked up by every load, never by the evaluation itself.
 cudaError_t noalloc_scratch_address(double** out);
 
-// Evaluation contexts (hmat_eval.cpp).
+// Evaluation contexts (hmat_eval.cpp). dtype: HMAT_DTYPE_F64 or HMAT_DTYPE_F32 (W and Y).
 hmat_status ctx_create(const Handle& h, EvalContext** out);
 void ctx_destroy(EvalContext* c);
-int64_t ctx_bytes(const Handle& h, int64_t q, int mode);          // workspace bytes of one evaluation
-void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* base);  // carve the workspaces
-hmat_status ctx_reserve(const Handle& h, EvalContext* c, int64_t q, int mode);      // grow the own block
-// Enqueue Y = K~ W on `s` with the workspaces of `c` (bound for q and mode by the caller).
-hmat_status eval_impl(Handle* h, EvalContext* c, const double* W, double* Y, int64_t q, int mode, cudaStream_t s);
+int64_t ctx_bytes(const Handle& h, int64_t q, int mode, int dtype = HMAT_DTYPE_F64);  // workspace bytes
+void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* base,
+              int dtype = HMAT_DTYPE_F64);                                             // carve the workspaces
+hmat_status ctx_reserve(const Handle& h, EvalContext* c, int64_t q, int mode,
+                        int dtype = HMAT_DTYPE_F64);                                   // grow the own block
+// Enqueue Y = K~ W on `s` with the workspaces of `c` (bound for q, mode and dtype by the caller).
+hmat_status eval_impl(Handle* h, EvalContext* c, const void* W, void* Y, int64_t q, int mode, int dtype,
+                      cudaStream_t s);
+inline int64_t dtype_bytes(int dtype) { return dtype == HMAT_DTYPE_F32 ? 4 : 8; }
+// FP32 <-> FP64 copies of n values (hmat_mixed.cu): widening exact, narrowing to nearest even.
+cudaError_t launch_widen(const float* src, double* dst, int64_t n, cudaStream_t stream);
+cudaError_t launch_narrow(const double* src, float* dst, int64_t n, cudaStream_t stream);
 // The far chain of one mixed evaluation with the workspaces of c (bound for q): the
 // member description, launch `part` (0, 1, 2 = ChainPlan ranges A, B, C) and the grid cap
 // chosen by the autotuner.
-ChainMember chain_member(const Handle& h, const EvalContext* c, double* Y, int64_t q);
+ChainMember chain_member(const Handle& h, const EvalContext* c, void* Y, bool y_f32, int64_t q);
 ChainLaunch chain_launch(const Handle& h, const EvalContext* c, int part, int32_t extra, uint64_t limit_ns);
 int chain_grid_cap(const Handle& h, int64_t q);
 hmat_status cuda_status(cudaError_t e);

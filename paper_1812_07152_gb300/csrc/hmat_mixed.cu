@@ -324,9 +324,9 @@ __global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t
 
 // One (source k-chunk, column tile): 64 rows of X x n_t columns -> B-operand tiles:
 // n_t rows (columns of X) x 64 values (rows of X), hi then lo. The near field's X is
-// W (FP64, caller order, rows through perm); there the same values also go unscaled
-// into x32, the FP32 tree-order copy the far field reads. The coupling's X is the
-// FP32 skeleton weights in node order. A thread owns one column and 8 consecutive
+// W (FP64 or FP32, caller order, rows through perm); there the same values, rounded to
+// FP32, also go unscaled into x32, the FP32 tree-order copy the far field reads. The
+// coupling's X is the FP32 skeleton weights in node order. A thread owns one column and 8 consecutive
 // rows: one 16-byte chunk of each tile. FP64 arithmetic is 1/64 rate on this GPU, so
 // the split itself is done in FP32 after one conversion on the integer units (24 bits
 // kept, 22 needed),
@@ -370,13 +370,13 @@ __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__
       const int64_t src = src_row[k];
       if (src >= 0 && gq < q) {
         const T v = X[src * q + gq];
-        if constexpr (sizeof(T) == 8) {
-          const float f = narrow_f64<true>((double)v);
-          xs = f32_scale ? f * sf : narrow_f64_hw(mul_f64_hw((double)v, sd));
-          if (x32) x32[(row0 + k) * q + gq] = f;
-        } else {
-          xs = (float)v * sf;
-        }
+        float f;
+        if constexpr (sizeof(T) == 8)
+          f = narrow_f64<true>((double)v);
+        else
+          f = v;
+        xs = f32_scale ? f * sf : narrow_f64_hw(mul_f64_hw((double)v, sd));
+        if (x32) x32[(row0 + k) * q + gq] = f;
       }
       hv[t] = __float2half_rn(xs);
       lv[t] = __float2half_rn(xs - __half2float(hv[t]));
@@ -403,11 +403,12 @@ struct TcArgs {
   const uint8_t* bsplit;            // right-hand operand tiles (k_split)
   const unsigned long long* bmax;   // max |X| of the right-hand side (FP64 bits)
   const int64_t* perm;              // near field: tree order -> caller order of Y's rows
-  void* Y;                          // near field: double (caller order); coupling: float (node rows)
+  void* Y;                          // near field: double or float (caller order); coupling: float (node rows)
   int64_t q;
   int n_t;
   int n_ct;
   int* status;
+  int y_f32;                        // near field: Y holds FP32 values
 };
 
 // Y_t = sum over the list of target t of A_ts X_s, for one (target, m-tile, column
@@ -667,8 +668,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
             static_cast<float*>(a.Y)[out_row * a.q + gc] =
                 f32_out ? __fmul_rn(__fadd_rn(hi[col], t), scf) : far_out_hw(hi[col], t, sc);
           } else {
-            static_cast<double*>(a.Y)[out_row * a.q + gc] =
-                scale_pow2(widen_f32(hi[col]) + widen_f32(t), e_sc, sc);
+            const double y = scale_pow2(widen_f32(hi[col]) + widen_f32(t), e_sc, sc);
+            if (a.y_f32)
+              static_cast<float*>(a.Y)[out_row * a.q + gc] = narrow_f64(y);
+            else
+              static_cast<double*>(a.Y)[out_row * a.q + gc] = y;
           }
         }
       }
@@ -757,7 +761,7 @@ cudaError_t launch_split(const TcProduct& p, const T* X, int64_t n_values, const
 
 template <bool kFar>
 cudaError_t launch_tc(const TcProduct& p, const uint8_t* bsplit, const unsigned long long* bmax, const int64_t* perm,
-                      void* Y, int64_t q, int n_t, int n_ct, int* status, cudaStream_t stream) {
+                      void* Y, bool y_f32, int64_t q, int n_t, int n_ct, int* status, cudaStream_t stream) {
   if (p.n_work == 0) return cudaSuccess;
   if (n_t <= 0 || n_t > kMaxNt || n_t % 16 != 0) return cudaErrorInvalidValue;
   const int64_t grid = p.n_work * n_ct;
@@ -765,7 +769,7 @@ cudaError_t launch_tc(const TcProduct& p, const uint8_t* bsplit, const unsigned 
   const int smem = kStages * kStageBytes + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_tc<kFar>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  TcArgs args{p.dev, bsplit, bmax, perm, Y, q, n_t, n_ct, status};
+  TcArgs args{p.dev, bsplit, bmax, perm, Y, q, n_t, n_ct, status, y_f32 ? 1 : 0};
   k_tc<kFar><<<(unsigned)grid, kTcThreads, smem, stream>>>(args);
   return cudaGetLastError();
 }
@@ -778,20 +782,47 @@ cudaError_t launch_split_f64(const TcProduct& p, const double* X, int64_t n_valu
   return launch_split<double>(p, X, n_values, perm, q, n_t, n_ct, xmax, out, x32, stream);
 }
 
-cudaError_t launch_split_f32(const TcProduct& p, const float* X, int64_t n_values, int64_t q, int n_t, int n_ct,
-                             unsigned long long* xmax, uint8_t* out, cudaStream_t stream) {
-  return launch_split<float>(p, X, n_values, nullptr, q, n_t, n_ct, xmax, out, nullptr, stream);
+cudaError_t launch_split_f32(const TcProduct& p, const float* X, int64_t n_values, const int64_t* perm, int64_t q,
+                             int n_t, int n_ct, unsigned long long* xmax, uint8_t* out, float* x32,
+                             cudaStream_t stream) {
+  return launch_split<float>(p, X, n_values, perm, q, n_t, n_ct, xmax, out, x32, stream);
 }
 
 cudaError_t launch_tc_near(const TcProduct& p, const uint8_t* bsplit, const unsigned long long* bmax,
-                           const int64_t* perm, double* Y, int64_t q, int n_t, int n_ct, int* status,
+                           const int64_t* perm, void* Y, bool y_f32, int64_t q, int n_t, int n_ct, int* status,
                            cudaStream_t stream) {
-  return launch_tc<false>(p, bsplit, bmax, perm, Y, q, n_t, n_ct, status, stream);
+  return launch_tc<false>(p, bsplit, bmax, perm, Y, y_f32, q, n_t, n_ct, status, stream);
 }
 
 cudaError_t launch_tc_far(const TcProduct& p, const uint8_t* bsplit, const unsigned long long* bmax, float* U,
                           int64_t q, int n_t, int n_ct, int* status, cudaStream_t stream) {
-  return launch_tc<true>(p, bsplit, bmax, nullptr, U, q, n_t, n_ct, status, stream);
+  return launch_tc<true>(p, bsplit, bmax, nullptr, U, false, q, n_t, n_ct, status, stream);
+}
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_widen(const float* __restrict__ src, double* __restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = widen_f32<true>(src[i]);
+}
+
+__global__ void __launch_bounds__(256) k_narrow(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = narrow_f64<true>(src[i]);
+}
+
+}  // namespace
+
+cudaError_t launch_widen(const float* src, double* dst, int64_t n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  k_widen<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, stream>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_narrow(const double* src, float* dst, int64_t n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  k_narrow<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, stream>>>(src, dst, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_wait_selftest(int* status, uint64_t limit_ns, cudaStream_t stream) {

@@ -34,6 +34,7 @@ using namespace hmat;
 
 extern "C" hmat_status hmat_eval_noalloc(hmat_t h, const double* W, double* Y, int64_t q, void* stream) {
   if (!h || q < 0) return HMAT_EINVAL;
+  if (!h->has_fp64) return HMAT_EUNSUPPORTED;
   if (q == 0 || h->n_points == 0) return HMAT_OK;
   if (!W || !Y || W == Y) return HMAT_EINVAL;
   const char* w0 = (const char*)W;

@@ -22,8 +22,9 @@ using Clock = std::chrono::steady_clock;
 struct Request {
   int64_t id = 0;
   int matrix = 0;
-  const double* W = nullptr;
-  double* Y = nullptr;
+  int dtype = HMAT_DTYPE_F64;
+  const void* W = nullptr;
+  void* Y = nullptr;
   int64_t ldw = 0, ldy = 0;
   int64_t q = 0;
   Clock::time_point submitted;
@@ -60,24 +61,33 @@ struct hmat_server {
   std::thread dispatcher;
 
   int64_t in_flight_bytes = 0, peak_bytes = 0;
-  int64_t evaluations = 0, batched_requests = 0;
+  int64_t evaluations = 0, batched_requests = 0, rejected = 0;
   std::vector<double> latencies_ms;
+  std::vector<std::vector<double>> matrix_latencies_ms;  // per matrix
 
   // bytes of one evaluation of `matrix` with q columns: workspaces + device W and Y
-  int64_t need(int matrix, int64_t q) const {
+  int64_t need(int matrix, int64_t q, int dtype) const {
     const Handle& h = *handles[matrix];
-    return align256(ctx_bytes(h, q, params.mode)) + 2 * align256(h.n_points * q * (int64_t)sizeof(double));
+    return align256(ctx_bytes(h, q, params.mode, dtype)) + 2 * align256(h.n_points * q * dtype_bytes(dtype));
   }
 
   void run();
-  hmat_status launch(Slot& sl, int matrix, const std::vector<int64_t>& ids, int64_t q_total);
+  void record(const Request& r, Clock::time_point now);
+  hmat_status launch(Slot& sl, int matrix, int dtype, const std::vector<int64_t>& ids, int64_t q_total);
   void retire(Slot& sl, hmat_status st);
 };
 
-hmat_status hmat_server::launch(Slot& sl, int matrix, const std::vector<int64_t>& ids, int64_t q_total) {
+void hmat_server::record(const Request& r, Clock::time_point now) {
+  const double ms = std::chrono::duration<double, std::milli>(now - r.submitted).count();
+  latencies_ms.push_back(ms);
+  matrix_latencies_ms[r.matrix].push_back(ms);
+}
+
+hmat_status hmat_server::launch(Slot& sl, int matrix, int dtype, const std::vector<int64_t>& ids, int64_t q_total) {
   Handle* h = handles[matrix];
   const int64_t n = h->n_points;
-  const int64_t bytes = need(matrix, q_total);
+  const int64_t es = dtype_bytes(dtype);
+  const int64_t bytes = need(matrix, q_total, dtype);
   cudaStream_t s = sl.stream;
   if (!sl.ctx[matrix]) {
     hmat_status st = ctx_create(*h, &sl.ctx[matrix]);
@@ -87,29 +97,29 @@ hmat_status hmat_server::launch(Slot& sl, int matrix, const std::vector<int64_t>
   uint8_t* block = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync((void**)&block, (size_t)std::max<int64_t>(bytes, 256), pool, s);
   if (e != cudaSuccess) return cuda_status(e);
-  double* dW = (double*)block;
-  double* dY = (double*)(block + align256(n * q_total * 8));
-  uint8_t* ws = block + 2 * align256(n * q_total * 8);
+  uint8_t* dW = block;
+  uint8_t* dY = block + align256(n * q_total * es);
+  uint8_t* ws = block + 2 * align256(n * q_total * es);
   // W columns of the merged requests side by side (strided copies), evaluate, split Y back
   int64_t col = 0;
   for (int64_t id : ids) {
     const Request& r = requests[id];
-    e = cudaMemcpy2DAsync(dW + col, (size_t)q_total * 8, r.W, (size_t)r.ldw * 8, (size_t)r.q * 8, (size_t)n,
-                          cudaMemcpyDefault, s);
+    e = cudaMemcpy2DAsync(dW + col * es, (size_t)(q_total * es), r.W, (size_t)(r.ldw * es), (size_t)(r.q * es),
+                          (size_t)n, cudaMemcpyDefault, s);
     if (e != cudaSuccess) break;
     col += r.q;
   }
   hmat_status st = cuda_status(e);
   if (st == HMAT_OK) {
-    ctx_bind(*h, c, q_total, params.mode, ws);
-    st = eval_impl(h, c, dW, dY, q_total, params.mode, s);
+    ctx_bind(*h, c, q_total, params.mode, ws, dtype);
+    st = eval_impl(h, c, dW, dY, q_total, params.mode, dtype, s);
   }
   col = 0;
   for (int64_t id : ids) {
     if (st != HMAT_OK) break;
     const Request& r = requests[id];
-    e = cudaMemcpy2DAsync(r.Y, (size_t)r.ldy * 8, dY + col, (size_t)q_total * 8, (size_t)r.q * 8, (size_t)n,
-                          cudaMemcpyDefault, s);
+    e = cudaMemcpy2DAsync(r.Y, (size_t)(r.ldy * es), dY + col * es, (size_t)(q_total * es), (size_t)(r.q * es),
+                          (size_t)n, cudaMemcpyDefault, s);
     st = cuda_status(e);
     col += r.q;
   }
@@ -132,7 +142,7 @@ void hmat_server::retire(Slot& sl, hmat_status st) {
     Request& r = requests[id];
     r.done = true;
     r.status = st;
-    latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r.submitted).count());
+    record(r, now);
   }
   in_flight_bytes -= sl.bytes;
   sl.members.clear();
@@ -179,21 +189,21 @@ void hmat_server::run() {
       int64_t q_total = head.q;
       for (size_t k = 1; k < pending.size(); ++k) {
         const Request& r = requests[pending[k]];
-        if (r.matrix != head.matrix || q_total + r.q > params.max_q) continue;
-        if (in_flight_bytes + need(head.matrix, q_total + r.q) > params.memory_budget) continue;
+        if (r.matrix != head.matrix || r.dtype != head.dtype || q_total + r.q > params.max_q) continue;
+        if (in_flight_bytes + need(head.matrix, q_total + r.q, head.dtype) > params.memory_budget) continue;
         ids.push_back(r.id);
         q_total += r.q;
       }
-      if (in_flight_bytes + need(head.matrix, q_total) > params.memory_budget) break;  // wait for memory
+      if (in_flight_bytes + need(head.matrix, q_total, head.dtype) > params.memory_budget) break;  // wait for memory
       for (int64_t id : ids) pending.erase(std::find(pending.begin(), pending.end(), id));
-      const hmat_status st = launch(*free_slot, head.matrix, ids, q_total);
+      const hmat_status st = launch(*free_slot, head.matrix, head.dtype, ids, q_total);
       if (st != HMAT_OK) {
         const auto now = Clock::now();
         for (int64_t id : ids) {
           Request& r = requests[id];
           r.done = true;
           r.status = st;
-          latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r.submitted).count());
+          record(r, now);
         }
         cv_done.notify_all();
       } else {
@@ -216,7 +226,7 @@ extern "C" hmat_status hmat_server_create(const hmat_t* handles, int count, cons
   if (!out) return HMAT_EINVAL;
   *out = nullptr;
   if (!handles || count <= 0 || count > 64 || !p || p->slots < 1 || p->slots > 64 || p->memory_budget <= 0 ||
-      p->max_q < 1)
+      p->max_q < 1 || p->max_pending < 0)
     return HMAT_EINVAL;
   if (p->mode != HMAT_MODE_FP64 && p->mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
   int dev = -1;
@@ -224,12 +234,14 @@ extern "C" hmat_status hmat_server_create(const hmat_t* handles, int count, cons
   for (int i = 0; i < count; ++i) {
     if (!handles[i] || handles[i]->device != dev) return HMAT_EINVAL;
     if (p->mode == HMAT_MODE_MIXED && !handles[i]->has_mixed) return HMAT_EUNSUPPORTED;
+    if (p->mode == HMAT_MODE_FP64 && !handles[i]->has_fp64) return HMAT_EUNSUPPORTED;
   }
   hmat_server* sv = new (std::nothrow) hmat_server();
   if (!sv) return HMAT_ENOMEM;
   sv->device = dev;
   sv->params = *p;
   sv->handles.assign(handles, handles + count);
+  sv->matrix_latencies_ms.resize(count);
   cudaMemPoolProps props{};
   props.allocType = cudaMemAllocationTypePinned;
   props.location.type = cudaMemLocationTypeDevice;
@@ -267,17 +279,23 @@ bool copyable(const void* p) {
 
 }  // namespace
 
-extern "C" hmat_status hmat_server_submit(hmat_server_t sv, int matrix, const double* W, int64_t ldw, double* Y,
-                                          int64_t ldy, int64_t q, int64_t* id) {
+extern "C" hmat_status hmat_server_submit_typed(hmat_server_t sv, int matrix, const void* W, int64_t ldw, void* Y,
+                                                int64_t ldy, int64_t q, int dtype, int64_t* id) {
   if (!sv || !id || matrix < 0 || matrix >= (int)sv->handles.size() || q < 1 || !W || !Y || ldw < q || ldy < q)
     return HMAT_EINVAL;
+  if (dtype != HMAT_DTYPE_F64 && dtype != HMAT_DTYPE_F32) return HMAT_EINVAL;
   if (q > sv->params.max_q || !copyable(W) || !copyable(Y)) return HMAT_EINVAL;
-  if (sv->need(matrix, q) > sv->params.memory_budget) return HMAT_ENOMEM;
+  if (sv->need(matrix, q, dtype) > sv->params.memory_budget) return HMAT_ENOMEM;
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->stop) return HMAT_EINVAL;
+  if (sv->params.max_pending > 0 && (int64_t)sv->pending.size() >= sv->params.max_pending) {
+    sv->rejected += 1;  // load shedding: the queue is full
+    return HMAT_EBUSY;
+  }
   Request r;
   r.id = sv->next_id++;
   r.matrix = matrix;
+  r.dtype = dtype;
   r.W = W;
   r.Y = Y;
   r.ldw = ldw;
@@ -289,6 +307,11 @@ extern "C" hmat_status hmat_server_submit(hmat_server_t sv, int matrix, const do
   *id = r.id;
   sv->cv_submit.notify_one();
   return HMAT_OK;
+}
+
+extern "C" hmat_status hmat_server_submit(hmat_server_t sv, int matrix, const double* W, int64_t ldw, double* Y,
+                                          int64_t ldy, int64_t q, int64_t* id) {
+  return hmat_server_submit_typed(sv, matrix, W, ldw, Y, ldy, q, HMAT_DTYPE_F64, id);
 }
 
 extern "C" hmat_status hmat_server_wait(hmat_server_t sv, int64_t id, int timeout_ms) {
@@ -304,20 +327,35 @@ extern "C" hmat_status hmat_server_wait(hmat_server_t sv, int64_t id, int timeou
   return st;
 }
 
+namespace {
+
+double percentile(const std::vector<double>& sorted, double p) {
+  if (sorted.empty()) return 0.0;
+  const size_t k = std::min(sorted.size() - 1, (size_t)(p * (double)(sorted.size() - 1) + 0.5));
+  return sorted[k];
+}
+
+}  // namespace
+
 extern "C" hmat_status hmat_server_stats(hmat_server_t sv, double* out, int n) {
   if (!sv || !out || n < 0) return HMAT_EINVAL;
   std::lock_guard<std::mutex> lk(sv->mu);
   std::vector<double> lat = sv->latencies_ms;
   std::sort(lat.begin(), lat.end());
-  auto pct = [&](double p) {
-    if (lat.empty()) return 0.0;
-    const size_t k = std::min(lat.size() - 1, (size_t)(p * (double)(lat.size() - 1) + 0.5));
-    return lat[k];
-  };
-  const double vals[6] = {(double)lat.size(), pct(0.50), pct(0.99),
+  const double vals[7] = {(double)lat.size(), percentile(lat, 0.50), percentile(lat, 0.99),
                           sv->evaluations ? (double)sv->batched_requests / (double)sv->evaluations : 0.0,
-                          (double)sv->evaluations, (double)sv->peak_bytes};
-  for (int i = 0; i < n && i < 6; ++i) out[i] = vals[i];
+                          (double)sv->evaluations, (double)sv->peak_bytes, (double)sv->rejected};
+  for (int i = 0; i < n && i < 7; ++i) out[i] = vals[i];
+  return HMAT_OK;
+}
+
+extern "C" hmat_status hmat_server_matrix_stats(hmat_server_t sv, int matrix, double* out, int n) {
+  if (!sv || !out || n < 0 || matrix < 0 || matrix >= (int)sv->handles.size()) return HMAT_EINVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  std::vector<double> lat = sv->matrix_latencies_ms[matrix];
+  std::sort(lat.begin(), lat.end());
+  const double vals[3] = {(double)lat.size(), percentile(lat, 0.50), percentile(lat, 0.99)};
+  for (int i = 0; i < n && i < 3; ++i) out[i] = vals[i];
   return HMAT_OK;
 }
 

@@ -74,6 +74,7 @@ extern "C" hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream
   if (!h || q <= 0) return HMAT_EINVAL;
   if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
   if (mode == HMAT_MODE_MIXED && !h->has_mixed) return HMAT_EUNSUPPORTED;
+  if (mode == HMAT_MODE_FP64 && !h->has_fp64) return HMAT_EUNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
   if (dev != h->device) return HMAT_EINVAL;
@@ -187,7 +188,7 @@ extern "C" hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream
         return cuda_status(e);
       }
       const double t = timer.best([&] {
-        return launch_tc_near(h->tc_near, c->wsplit, c->wmax, h->perm, Y, q, n_t, n_ct, h->status, s);
+        return launch_tc_near(h->tc_near, c->wsplit, c->wmax, h->perm, Y, false, q, n_t, n_ct, h->status, s);
       });
       if (t < 0) {
         cleanup();
@@ -222,7 +223,7 @@ extern "C" hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream
       int g_best = 0;
       for (int g : {0, 2 * sms, sms, sms / 2, sms / 4}) {
         live->chain_grid = g;
-        const double t = timer.best([&] { return eval_impl(h, c, W, Y, q, mode, s) == HMAT_OK ? cudaSuccess
+        const double t = timer.best([&] { return eval_impl(h, c, W, Y, q, mode, HMAT_DTYPE_F64, s) == HMAT_OK ? cudaSuccess
                                                                                               : cudaErrorUnknown; });
         if (t < 0) break;
         if (g == 0) c_def = t;

@@ -22,10 +22,14 @@ HMAT_ECUDA = -3
 HMAT_ETIMEOUT = -4
 HMAT_EUNSUPPORTED = -5
 HMAT_EDEVICE = -6
+HMAT_EBUSY = -7
 
 HMAT_MODE_FP64 = 0
 HMAT_MODE_MIXED = 1
 HMAT_LOAD_MIXED = 1
+HMAT_LOAD_MIXED_ONLY = 8
+HMAT_DTYPE_F64 = 0
+HMAT_DTYPE_F32 = 1
 
 PHASES = ("near", "up_leaf", "up_transfer", "coupling", "down_transfer", "down_leaf", "split", "far_up", "far_down")
 
@@ -107,7 +111,7 @@ class HmatCompressParams(ctypes.Structure):
 
 class HmatServerParams(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("memory_budget", ctypes.c_int64), ("max_q", ctypes.c_int64),
-                ("mode", ctypes.c_int)]
+                ("mode", ctypes.c_int), ("max_pending", ctypes.c_int64)]
 
 
 class HmatTuneReport(ctypes.Structure):
@@ -140,6 +144,16 @@ def library() -> ctypes.CDLL:
         lib.hmat_reserve.argtypes = [ctypes.c_void_p, ctypes.c_int64]
         lib.hmat_eval_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_int, ctypes.c_void_p]
+        lib.hmat_eval_typed.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        lib.hmat_eval_host_typed.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        lib.hmat_batch_eval_typed.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                              ctypes.POINTER(ctypes.c_void_p), _c_i64p, ctypes.c_int, ctypes.c_void_p]
+        lib.hmat_server_submit_typed.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _c_i64p]
+        lib.hmat_server_matrix_stats.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.c_int]
         lib.hmat_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.hmat_phase_times.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), _c_i64p, ctypes.c_int]
         lib.hmat_measure_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
@@ -175,6 +189,8 @@ def library() -> ctypes.CDLL:
                      "hmat_measure_fp64_peak", "hmat_batch_create", "hmat_batch_eval", "hmat_batch_free",
                      "hmat_server_create", "hmat_server_submit", "hmat_server_wait", "hmat_server_stats",
                      "hmat_server_free", "hmat_autotune", "hmat_selftest_timeout", "hmat_selftest_chain_timeout", "hmat_tune_apply",
+                     "hmat_eval_typed", "hmat_eval_host_typed", "hmat_batch_eval_typed", "hmat_server_submit_typed",
+                     "hmat_server_matrix_stats",
                      "hmat_plan_create", "hmat_plan_build",
                      "hmat_plan_free", "hmat_selftest_conversions"):
             getattr(lib, name).restype = ctypes.c_int
@@ -306,6 +322,23 @@ def hmat_eval(handle: int, W, Y, q: int, mode: int = HMAT_MODE_FP64, stream=None
     _check(library().hmat_eval(handle, _ptr(W), _ptr(Y), int(q), int(mode), _stream(stream)), "hmat_eval")
 
 
+def _dtype_of(x) -> int:
+    name = str(getattr(x, "dtype", ""))
+    if name.endswith("float32"):
+        return HMAT_DTYPE_F32
+    if name.endswith("float64"):
+        return HMAT_DTYPE_F64
+    raise ValueError(f"W and Y must be float32 or float64, not {name}")
+
+
+def hmat_eval_typed(handle: int, W, Y, q: int, mode: int = HMAT_MODE_FP64, dtype: Optional[int] = None,
+                    stream=None) -> None:
+    """Enqueue Y = K~ W with W and Y of element type dtype (default: W's, torch float32 or float64)."""
+    dt = _dtype_of(W) if dtype is None else int(dtype)
+    _check(library().hmat_eval_typed(handle, _ptr(W), _ptr(Y), int(q), int(mode), dt, _stream(stream)),
+           "hmat_eval_typed")
+
+
 def hmat_eval_host(handle: int, W: np.ndarray, Y: np.ndarray, mode: int = HMAT_MODE_FP64, stream=None) -> None:
     """Y = K~ W with host arrays (n x q FP64, C-contiguous; pinned memory copies fastest).
     W and Y may be numpy arrays or CPU torch tensors; synchronises the stream."""
@@ -316,6 +349,20 @@ def hmat_eval_host(handle: int, W: np.ndarray, Y: np.ndarray, mode: int = HMAT_M
             raise ValueError("W and Y must be C-contiguous float64 arrays")
         wp, yp, q = W.ctypes.data, Y.ctypes.data, int(W.shape[1])
     _check(library().hmat_eval_host(handle, wp, yp, q, int(mode), _stream(stream)), "hmat_eval_host")
+
+
+def hmat_eval_host_typed(handle: int, W, Y, mode: int = HMAT_MODE_FP64, stream=None) -> None:
+    """hmat_eval_host for host W and Y of float32 or float64 (numpy arrays or CPU torch tensors, C-contiguous)."""
+    dt = _dtype_of(W)
+    if _dtype_of(Y) != dt:
+        raise ValueError("W and Y must have the same dtype")
+    if hasattr(W, "data_ptr"):
+        wp, yp, q = int(W.data_ptr()), int(Y.data_ptr()), int(W.shape[1])
+    else:
+        if not (W.flags.c_contiguous and Y.flags.c_contiguous):
+            raise ValueError("W and Y must be C-contiguous")
+        wp, yp, q = W.ctypes.data, Y.ctypes.data, int(W.shape[1])
+    _check(library().hmat_eval_host_typed(handle, wp, yp, q, int(mode), dt, _stream(stream)), "hmat_eval_host_typed")
 
 
 def hmat_profile(handle: int, enable=True) -> None:
@@ -417,14 +464,24 @@ def hmat_batch_eval(batch: int, Ws, Ys, stream=None) -> None:
     _check(library().hmat_batch_eval(batch, w, y, q, _stream(stream)), "hmat_batch_eval")
 
 
+def hmat_batch_eval_typed(batch: int, Ws, Ys, stream=None) -> None:
+    """hmat_batch_eval for members' W and Y of one element type (float32 or float64 torch CUDA tensors)."""
+    n = len(Ws)
+    dt = _dtype_of(Ws[0])
+    w = (ctypes.c_void_p * n)(*[_ptr(x) for x in Ws])
+    y = (ctypes.c_void_p * n)(*[_ptr(x) for x in Ys])
+    q = (ctypes.c_int64 * n)(*[int(x.shape[1]) for x in Ws])
+    _check(library().hmat_batch_eval_typed(batch, w, y, q, dt, _stream(stream)), "hmat_batch_eval_typed")
+
+
 def hmat_batch_free(batch: int) -> None:
     _check(library().hmat_batch_free(batch), "hmat_batch_free")
 
 
 def hmat_server_create(handles: Sequence[int], slots: int, memory_budget: int, max_q: int,
-                       mode: int = HMAT_MODE_FP64) -> int:
+                       mode: int = HMAT_MODE_FP64, max_pending: int = 0) -> int:
     arr = (ctypes.c_void_p * len(handles))(*handles)
-    p = HmatServerParams(int(slots), int(memory_budget), int(max_q), int(mode))
+    p = HmatServerParams(int(slots), int(memory_budget), int(max_q), int(mode), int(max_pending))
     sv = ctypes.c_void_p()
     _check(library().hmat_server_create(arr, len(handles), ctypes.byref(p), ctypes.byref(sv)), "hmat_server_create")
     return int(sv.value)
@@ -432,12 +489,17 @@ def hmat_server_create(handles: Sequence[int], slots: int, memory_budget: int, m
 
 def hmat_server_submit(server: int, matrix: int, W, Y) -> int:
     """Queue Y = K~_matrix W; W and Y are pinned CPU (or CUDA) tensors of n x q whose rows are contiguous
-    (column slices of a wider tensor are fine). Returns the request id."""
+    (column slices of a wider tensor are fine), float64 or float32 (both the same). Returns the request id;
+    raises HmatError with status HMAT_EBUSY when the server's queue is full."""
     if W.stride(1) != 1 or Y.stride(1) != 1 or tuple(W.shape) != tuple(Y.shape):
         raise ValueError("W and Y must be n x q with contiguous rows")
+    dt = _dtype_of(W)
+    if _dtype_of(Y) != dt:
+        raise ValueError("W and Y must have the same dtype")
     rid = ctypes.c_int64()
-    _check(library().hmat_server_submit(server, int(matrix), _ptr(W), int(W.stride(0)), _ptr(Y), int(Y.stride(0)),
-                                        int(W.shape[1]), ctypes.byref(rid)), "hmat_server_submit")
+    _check(library().hmat_server_submit_typed(server, int(matrix), _ptr(W), int(W.stride(0)), _ptr(Y),
+                                              int(Y.stride(0)), int(W.shape[1]), dt, ctypes.byref(rid)),
+           "hmat_server_submit")
     return int(rid.value)
 
 
@@ -447,10 +509,16 @@ def hmat_server_wait(server: int, request: int, timeout_ms: int = -1) -> int:
 
 
 def hmat_server_stats(server: int) -> dict:
-    out = (ctypes.c_double * 6)()
-    _check(library().hmat_server_stats(server, out, 6), "hmat_server_stats")
-    keys = ("completed", "p50_ms", "p99_ms", "requests_per_evaluation", "evaluations", "peak_bytes")
+    out = (ctypes.c_double * 7)()
+    _check(library().hmat_server_stats(server, out, 7), "hmat_server_stats")
+    keys = ("completed", "p50_ms", "p99_ms", "requests_per_evaluation", "evaluations", "peak_bytes", "rejected")
     return dict(zip(keys, [float(v) for v in out]))
+
+
+def hmat_server_matrix_stats(server: int, matrix: int) -> dict:
+    out = (ctypes.c_double * 3)()
+    _check(library().hmat_server_matrix_stats(server, int(matrix), out, 3), "hmat_server_matrix_stats")
+    return dict(zip(("completed", "p50_ms", "p99_ms"), [float(v) for v in out]))
 
 
 def hmat_server_free(server: int) -> None:

@@ -112,3 +112,37 @@ def test_memory_budget_bounds_admission(mats):
         hp.hmat_server_free(sv)
     for W, Y, _ in reqs:
         assert torch.equal(Y, _alone(h, W, hp.HMAT_MODE_FP64))
+
+
+def test_bounded_queue_sheds_load_and_per_matrix_stats(mats):
+    """With max_pending, a burst beyond what one slot drains is refused with HMAT_EBUSY
+    (nothing queued); every accepted request completes, the refusals are counted, and
+    the per-matrix completions add up to the total."""
+    handles = [h for _, h in mats]
+    sv = hp.hmat_server_create(handles, slots=1, memory_budget=8 << 30, max_q=64, mode=hp.HMAT_MODE_FP64,
+                               max_pending=2)
+    accepted, refused = [], 0
+    try:
+        bufs = []
+        for k in range(200):
+            m = k % len(mats)
+            W = torch.from_numpy(rhs(mats[m][0].n, 64, 1300 + k)).pin_memory()
+            Y = torch.empty_like(W).pin_memory()
+            bufs.append((W, Y))
+            try:
+                accepted.append(hp.hmat_server_submit(sv, m, W, Y))
+            except hp.HmatError as e:
+                assert e.status == hp.HMAT_EBUSY
+                refused += 1
+        for rid in accepted:
+            assert hp.hmat_server_wait(sv, rid, 60000) == hp.HMAT_OK
+        st = hp.hmat_server_stats(sv)
+        assert refused > 0 and st["rejected"] == refused
+        assert st["completed"] == len(accepted)
+        per = [hp.hmat_server_matrix_stats(sv, m) for m in range(len(mats))]
+        assert sum(p["completed"] for p in per) == len(accepted)
+        for p in per:
+            if p["completed"]:
+                assert p["p99_ms"] >= p["p50_ms"] > 0
+    finally:
+        hp.hmat_server_free(sv)
