@@ -648,10 +648,14 @@ def run_hss(args, dist) -> dict:
             torch.cuda.synchronize()
             return dist.max(e0.elapsed_time(e1) / steps)
 
+        ms_default = timed(lambda: hp.hmat_eval(h, W, Y, q, hp.HMAT_MODE_FP64, stream))
+        tune = hp.hmat_autotune(h, q, hp.HMAT_MODE_FP64, stream)
         hp.hmat_profile(h, True)
-        hp.hmat_eval(h, W, Y, q, hp.HMAT_MODE_FP64, stream)
-        launches = sum(c for _, c in hp.hmat_phase_times(h).values())
+        for _ in range(20):
+            hp.hmat_eval(h, W, Y, q, hp.HMAT_MODE_FP64, stream)
+        ph = hp.hmat_phase_times(h)
         hp.hmat_profile(h, False)
+        launches = sum(c for _, c in ph.values()) // 20
         ms_eval = timed(lambda: hp.hmat_eval(h, W, Y, q, hp.HMAT_MODE_FP64, stream))
         b = hp.hmat_batch_create([h], hp.HMAT_MODE_FP64)
         try:
@@ -664,6 +668,9 @@ def run_hss(args, dist) -> dict:
         return {"workload": w.name, "n": w.n, "q": q, "mode": "fp64", "levels": info["levels"],
                 "sum_rank": info["sum_rank"], "steps": steps, "launches_per_eval": launches,
                 "us_per_eval": round(ms_eval * 1e3, 2), "us_per_eval_graph": round(ms_graph * 1e3, 2),
+                "us_per_eval_untuned": round(ms_default * 1e3, 2),
+                "phases_us_per_eval": {k: round(v[0] / 20 * 1e3, 2) for k, v in ph.items() if v[1]},
+                "autotune": tune,
                 "value": round(dist.world * q / (ms_eval / 1e3), 1), "unit": "cols/s",
                 "gflops": round(flops / (ms_eval / 1e3) / 1e9, 2)}
     finally:

@@ -326,11 +326,13 @@ hmat_status hmat_eval_host_typed(hmat_t h, const void* W, void* Y, int64_t q, in
  * level), HMAT_PHASE_COUPLING (u = sum B w), HMAT_PHASE_DOWN_TRANSFER
  * ([u_l; u_r] += P u, one launch per level), HMAT_PHASE_DOWN_LEAF (Y += P u),
  * HMAT_PHASE_SPLIT (mixed mode only: scale and split W into FP16 hi/lo tiles),
- * HMAT_PHASE_FAR_UP (mixed mode: one persistent launch of the upward pass over
- * every level; when the coupling runs in FP32 it also holds the coupling and the
+ * HMAT_PHASE_FAR_UP (one persistent launch over every tree level: in the FP64 mode
+ * the whole far field, from the upward pass to the downward leaf step; in the mixed
+ * mode the upward pass, and, when the coupling runs in FP32, the coupling and the
  * downward transfers), HMAT_PHASE_FAR_DOWN (mixed mode: one persistent launch of the
  * downward transfers after the tensor-core coupling). In the mixed mode the downward
- * leaf step is one persistent launch too (HMAT_PHASE_DOWN_LEAF).
+ * leaf step is one persistent launch too (HMAT_PHASE_DOWN_LEAF). The FP64 mode's
+ * other phase kinds are hmat_eval_noalloc's, which keeps one launch per level.
  */
 #define HMAT_PHASE_NEAR 0
 #define HMAT_PHASE_UP_LEAF 1
@@ -339,7 +341,7 @@ hmat_status hmat_eval_host_typed(hmat_t h, const void* W, void* Y, int64_t q, in
 #define HMAT_PHASE_DOWN_TRANSFER 4
 #define HMAT_PHASE_DOWN_LEAF 5
 #define HMAT_PHASE_SPLIT 6          /* mixed mode: max |W| and the FP16 hi/lo split of W */
-#define HMAT_PHASE_FAR_UP 7         /* mixed mode: persistent far-chain launch, upward pass (+ FP32 coupling) */
+#define HMAT_PHASE_FAR_UP 7         /* persistent far-chain launch (FP64: the whole far field) */
 #define HMAT_PHASE_FAR_DOWN 8       /* mixed mode: persistent far-chain launch, downward transfers */
 #define HMAT_PHASE_COUNT 9
 hmat_status hmat_profile(hmat_t h, int enable);
@@ -399,11 +401,12 @@ hmat_status hmat_eval_noalloc(hmat_t h, const double* W, double* Y, int64_t q, v
 /*
  * hmat_autotune - choose the tile shapes of h's evaluations with q columns in
  * `mode` by timing candidates on the device (CUDA events on `stream`); later
- * hmat_eval, hmat_eval_host, hmat_eval_noalloc, batch and server evaluations of h
- * with that q and mode use them. FP64 mode: per launch of the evaluation (one per
- * phase of Section 2.1's evaluation and row-tile size), the column tile of the
- * grouped GEMM (1 to 64 columns) among those that pad less than half a tile; a long
- * launch is timed on its longest tiles. Mixed mode: the column width of the
+ * hmat_eval, hmat_eval_host, batch and server evaluations of h with that q and mode
+ * use them. FP64 mode: per near-field launch (one per row-tile size), the column
+ * tile of the grouped GEMM (1 to 64 columns) among those that pad less than half a
+ * tile (a long launch is timed on its longest tiles), then the column tile of the
+ * persistent far chain, timed on whole chain launches (narrower tiles too when the
+ * chain is short: they spread thin levels over more SMs). Mixed mode: the column width of the
  * tensor-core near-field CTAs (fewer, wider tiles copy each near block fewer
  * times; more, narrower ones fill more SMs on a matrix with few leaves). Every
  * candidate sums each output in the same order, so results are bitwise those of
@@ -545,18 +548,17 @@ hmat_status hmat_status_poll(hmat_t h, void* stream);
 hmat_status hmat_selftest_timeout(hmat_t h, int64_t limit_ns, void* stream);
 
 /*
- * hmat_selftest_chain_timeout - failure-detection self-test of the mixed mode's
- * persistent far chain (no counterpart in the paper). Enqueues on `stream` the
- * chain's first launch for q columns (on the handle's own workspace, which it
- * reserves like hmat_eval) with every dependency requirement raised by one, so
- * that no wait can be met: each wait gives up after limit_ns nanoseconds
- * (0 < limit_ns <= 10 s, else HMAT_EINVAL), latches HMAT_ETIMEOUT in h's status
- * word and stops the launch, which reads and writes no workspace before its
- * waits. The next hmat_status_poll returns HMAT_ETIMEOUT; the context stays
- * usable. HMAT_EUNSUPPORTED without HMAT_LOAD_MIXED, HMAT_EINVAL when the HMatrix
- * has no far field.
+ * hmat_selftest_chain_timeout - failure-detection self-test of the persistent far
+ * chain of `mode` (no counterpart in the paper). Enqueues on `stream` the chain's
+ * first launch for q columns (on the handle's own workspace, which it reserves like
+ * hmat_eval) with every dependency requirement raised by one, so that no wait can be
+ * met: each wait gives up after limit_ns nanoseconds (0 < limit_ns <= 10 s, else
+ * HMAT_EINVAL), latches HMAT_ETIMEOUT in h's status word and stops the launch, which
+ * reads and writes no workspace before its waits. The next hmat_status_poll returns
+ * HMAT_ETIMEOUT; the context stays usable. HMAT_EUNSUPPORTED when the handle has no
+ * copy for `mode`, HMAT_EINVAL when the HMatrix has no far field.
  */
-hmat_status hmat_selftest_chain_timeout(hmat_t h, int64_t q, int64_t limit_ns, void* stream);
+hmat_status hmat_selftest_chain_timeout(hmat_t h, int64_t q, int mode, int64_t limit_ns, void* stream);
 
 /* hmat_info - sizes of the loaded HMatrix: out[0] = n_points, out[1] = levels,
  * out[2] = near entries, out[3] = far entries, out[4] = near values (stored, or

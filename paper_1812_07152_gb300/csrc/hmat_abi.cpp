@@ -211,6 +211,9 @@ void free_device(Handle* h) {
   cudaFree(h->chain.items);
   cudaFree(h->chain.expect);
   h->chain = ChainPlan{};
+  cudaFree(h->chain64.items);
+  cudaFree(h->chain64.expect);
+  h->chain64 = ChainPlan{};
   h->arena32 = nullptr; h->entries32 = nullptr; h->has_mixed = false;
   cudaFree(h->arena);
   cudaFree(h->pts_tree);
@@ -460,6 +463,52 @@ hmat_status build_mixed(Handle* h, const hmat_desc* d, const Validated& v, const
   return HMAT_OK;
 }
 
+// Counts per node of the items a dependent item waits for (the expect layout of ChainSync).
+std::vector<int32_t> chain_expect(const std::vector<ChainItem>& items, int64_t n, int L) {
+  std::vector<int32_t> expect(3 * n + L + 1, 0);
+  for (const ChainItem& it : items) {
+    if (it.kind == CK_UP) {
+      expect[it.node] += 1;
+      expect[3 * n + it.level] += 1;
+    } else if (it.kind == CK_CPL) {
+      expect[n + it.node] += 1;
+    } else if (it.kind == CK_DN) {
+      expect[2 * n + it.node] += 1;
+    }
+  }
+  return expect;
+}
+
+// The FP64 far field as one chain launch: the upward pass, each level's coupling after
+// the next level up, the downward transfers, the downward leaf step.
+hmat_status build_chain64(Handle* h, const Validated& v, const std::vector<ChainItem> (&by_kind)[4]) {
+  const int L = h->levels;
+  std::vector<ChainItem> items;
+  auto level_range = [&](int ck, int l) {
+    for (const ChainItem& it : by_kind[ck])
+      if (it.level == l) items.push_back(it);
+  };
+  level_range(CK_UP, L);
+  for (int l = L - 1; l >= 1; --l) {
+    level_range(CK_UP, l);
+    level_range(CK_CPL, l + 1);
+  }
+  if (L >= 1) level_range(CK_CPL, 1);
+  for (int l = 1; l < L; ++l) level_range(CK_DN, l);
+  level_range(CK_LEAF, L);
+  if (items.size() > (size_t)INT32_MAX) return HMAT_EUNSUPPORTED;
+  ChainPlan& cp = h->chain64;
+  cp.begin[0] = 0;
+  cp.count[0] = (int32_t)items.size();
+  cp.waits[0] = kWaitUp | kWaitLevel | kWaitCpl | kWaitDn;
+  const std::vector<int32_t> expect = chain_expect(items, v.n_nodes, L);
+  cp.n_ctr = kChainCtrHead + (int64_t)expect.size();
+  cudaError_t e = chain64_prepare();
+  if (e == cudaSuccess) e = upload(&cp.items, items, &h->device_bytes);
+  if (e == cudaSuccess) e = upload(&cp.expect, expect, &h->device_bytes);
+  return cuda_status(e);
+}
+
 // The far field of the mixed mode as chain items (hmat_chain.cu): every tile of the
 // FP32 phases, ordered so that every item's dependencies come before it, and the
 // number of items per node and kind that a dependent item waits for.
@@ -513,17 +562,7 @@ hmat_status build_chain(Handle* h, const Validated& v, const std::vector<GemmTil
   cp.count[2] = (int32_t)items.size() - cp.begin[2];
   cp.waits[2] = 0;
   if (items.size() > (size_t)INT32_MAX) return HMAT_EUNSUPPORTED;
-  std::vector<int32_t> expect(3 * n + L + 1, 0);
-  for (const ChainItem& it : items) {
-    if (it.kind == CK_UP) {
-      expect[it.node] += 1;
-      expect[3 * n + it.level] += 1;
-    } else if (it.kind == CK_CPL) {
-      expect[n + it.node] += 1;
-    } else if (it.kind == CK_DN) {
-      expect[2 * n + it.node] += 1;
-    }
-  }
+  const std::vector<int32_t> expect = chain_expect(items, n, L);
   cp.n_ctr = kChainCtrHead + (int64_t)expect.size();
   cudaError_t e = chain_prepare(nullptr, nullptr);
   if (e == cudaSuccess) e = upload(&cp.items, items, &h->device_bytes);
@@ -686,10 +725,12 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     ph.n_tiles = (int64_t)tiles.size() - ph.tile_begin;
     if (ph.n_tiles > 0) h->phases32.push_back(ph);
   };
-  std::vector<int32_t> task_node;  // the tree node of each task (the chain's counters)
-  auto new_task = [&](int64_t out_row, int64_t m, int accumulate, int64_t node) -> int32_t {
+  std::vector<int32_t> task_node;  // the tree node of each task (the chains' counters)
+  std::vector<PhaseKind> task_kind;
+  auto new_task = [&](int64_t out_row, int64_t m, int accumulate, int64_t node, PhaseKind kind) -> int32_t {
     tasks.push_back(GemmTask{out_row, (int32_t)m, (int32_t)entries.size(), (int32_t)entries.size(), accumulate});
     task_node.push_back((int32_t)node);
+    task_kind.push_back(kind);
     return (int32_t)tasks.size() - 1;
   };
   auto add_entry = [&](int32_t t, int64_t a_off, int64_t x_row, int64_t k, int64_t lda, int trans) {
@@ -703,7 +744,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     for (int64_t i = 0; i < v.n_leaves; ++i) {
       const int64_t a = fl + i;
       if (h->size[a] == 0) continue;
-      const int32_t t = new_task(h->begin[a], h->size[a], 0, a);
+      const int32_t t = new_task(h->begin[a], h->size[a], 0, a, PH_NEAR);
       for (int64_t e = d->near_ptr[i]; e < d->near_ptr[i + 1]; ++e) {
         const int64_t b = fl + d->near_idx[e];
         add_entry(t, near_off[e], h->begin[b], h->size[b], h->size[b], 0);
@@ -716,7 +757,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     std::vector<int32_t> ids;
     for (int64_t a = fl; a < v.n_nodes; ++a) {
       if (h->rank[a] == 0) continue;
-      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0, a);
+      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0, a, PH_UP_LEAF);
       add_entry(t, basis_off[a], h->begin[a], h->size[a], h->rank[a], 1);
       ids.push_back(t);
     }
@@ -726,7 +767,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     std::vector<int32_t> ids;
     for (int64_t a = ((int64_t)1 << level) - 1; a < ((int64_t)2 << level) - 1; ++a) {
       if (h->rank[a] == 0) continue;
-      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0, a);
+      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0, a, PH_UP_TRANS);
       add_entry(t, basis_off[a], h->skel_off[2 * a + 1], rows_of(a), h->rank[a], 1);
       ids.push_back(t);
     }
@@ -736,7 +777,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     std::vector<int32_t> ids;
     for (int64_t a = 1; a < v.n_nodes; ++a) {
       if (h->rank[a] == 0) continue;
-      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0, a);
+      const int32_t t = new_task(h->skel_off[a], h->rank[a], 0, a, PH_COUPLING);
       if (far_task_off[a] >= 0) add_entry(t, far_task_off[a], far_rows_off[a], far_k[a], far_k[a], 0);
       ids.push_back(t);
     }
@@ -746,7 +787,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     std::vector<int32_t> ids;
     for (int64_t a = ((int64_t)1 << level) - 1; a < ((int64_t)2 << level) - 1; ++a) {
       if (h->rank[a] == 0 || rows_of(a) == 0) continue;
-      const int32_t t = new_task(h->skel_off[2 * a + 1], rows_of(a), 1, a);
+      const int32_t t = new_task(h->skel_off[2 * a + 1], rows_of(a), 1, a, PH_DOWN_TRANS);
       add_entry(t, basis_off[a], h->skel_off[a], h->rank[a], h->rank[a], 0);
       ids.push_back(t);
     }
@@ -756,11 +797,41 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     std::vector<int32_t> ids;
     for (int64_t a = fl; a < v.n_nodes; ++a) {
       if (h->rank[a] == 0 || h->size[a] == 0) continue;
-      const int32_t t = new_task(h->begin[a], h->size[a], 1, a);
+      const int32_t t = new_task(h->begin[a], h->size[a], 1, a, PH_DOWN_LEAF);
       add_entry(t, basis_off[a], h->skel_off[a], h->rank[a], h->rank[a], 0);
       ids.push_back(t);
     }
     add_phase(PH_DOWN_LEAF, d->levels, MAT_SKEL_U, MAT_USER, ids, XMAP_NONE);
+  }
+
+  // ---- the FP64 far chain: 16-row tiles of every far-field task (appended to the tile
+  // array), longest first within a (step, level)
+  std::vector<ChainItem> items64[4];  // per ChainKind, in (level, cost) order within
+  {
+    const int L = d->levels;
+    std::vector<std::vector<std::pair<int64_t, int32_t>>> by(4 * (L + 1));
+    for (size_t t = 0; t < tasks.size(); ++t) {
+      const PhaseKind k = task_kind[t];
+      if (k == PH_NEAR) continue;
+      const int ck = (k == PH_UP_LEAF || k == PH_UP_TRANS) ? CK_UP
+                     : k == PH_COUPLING ? CK_CPL : (k == PH_DOWN_TRANS ? CK_DN : CK_LEAF);
+      int64_t kk = 0;
+      for (int32_t e = tasks[t].e_begin; e < tasks[t].e_end; ++e) kk += entries[e].k;
+      by[ck * (L + 1) + level_of(task_node[t])].push_back({std::max<int64_t>(kk, 1), (int32_t)t});
+    }
+    for (int ck = 0; ck < 4; ++ck)
+      for (int l = 0; l <= L; ++l) {
+        auto& b = by[ck * (L + 1) + l];
+        std::stable_sort(b.begin(), b.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+        for (const auto& p : b) {
+          const int32_t t = p.second;
+          for (int32_t m0 = 0; m0 < tasks[t].m; m0 += 16) {
+            items64[ck].push_back(ChainItem{(int32_t)tiles.size(), task_node[t], (uint8_t)ck, 0, (uint8_t)l,
+                                            (uint8_t)(ck == CK_CPL ? 1 : 0)});
+            tiles.push_back(GemmTile{t, m0});
+          }
+        }
+      }
   }
 
   // ---- device allocations and upload
@@ -865,6 +936,13 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
     if (ms != HMAT_OK) {
       free_device(h.get());
       return ms;
+    }
+  }
+  {
+    hmat_status cs = build_chain64(h.get(), v, items64);
+    if (cs != HMAT_OK) {
+      free_device(h.get());
+      return cs;
     }
   }
   if ((e = noalloc_scratch_address(&h->noalloc_scratch)) != cudaSuccess) return fail(e);

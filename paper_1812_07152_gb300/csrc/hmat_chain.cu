@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "hmat_chain.cuh"
 #include "hmat_gemm_f32.cuh"
 
 namespace hmat {
@@ -42,83 +43,6 @@ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int kChainSmem = cmax(cmax(cmax(chain_smem<16, 32>(), chain_smem<16, 64>()),
                                      cmax(chain_smem<32, 32>(), chain_smem<32, 64>())),
                                 cmax(chain_smem<64, 32>(), chain_smem<64, 64>()));
-
-__device__ __forceinline__ uint64_t chain_timer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ int ld_acquire(const int32_t* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Thread 0 only: wait until *cnt >= need (need <= 0: nothing to wait for). False when the
-// launch aborted or the wait ran out (which latches HMAT_ETIMEOUT and aborts the launch).
-__device__ bool chain_wait(const int32_t* cnt, int need, const ChainLaunch& l, int* status, uint64_t* t0) {
-  if (need <= 0) return true;
-  for (uint32_t i = 0;; ++i) {
-    if (ld_acquire(cnt) >= need) return true;
-    if ((i & 7) == 7) {
-      if (*(volatile int32_t*)l.abort_flag) return false;
-      const uint64_t t = chain_timer();
-      if (*t0 == 0) {
-        *t0 = t;
-      } else if (t - *t0 > l.limit_ns) {
-        atomicCAS(status, 0, (int)HMAT_ETIMEOUT);
-        atomicExch(l.abort_flag, 1);
-        return false;
-      }
-    }
-    __nanosleep(128);
-  }
-}
-
-// The dependencies of one item (thread 0).
-__device__ bool chain_deps(const ChainMember& m, const ChainItem& it, const ChainLaunch& l) {
-  const int n = m.n_nodes;
-  const int32_t* e_up = m.expect;
-  const int32_t* e_cpl = m.expect + n;
-  const int32_t* e_dn = m.expect + 2 * n;
-  const int32_t* e_lvl = m.expect + 3 * n;
-  const int32_t* c_up = m.ctr;
-  const int32_t* c_cpl = m.ctr + n;
-  const int32_t* c_dn = m.ctr + 2 * n;
-  const int32_t* c_lvl = m.ctr + 3 * n;
-  const int nct = m.n_ct;
-  uint64_t t0 = 0;
-  auto need = [&](const int32_t* e, int node) { return e[node] > 0 ? e[node] * nct + l.extra : 0; };
-  // self-test: the root never has a basis, so its upward counter stays 0 and this wait runs out
-  if (l.extra > 0 && !chain_wait(c_up, l.extra, l, m.status, &t0)) return false;
-  const int a = it.node;
-  switch (it.kind) {
-    case CK_UP:
-      if ((l.waits & kWaitUp) && a < m.first_leaf)
-        for (int c = 2 * a + 1; c <= 2 * a + 2; ++c)
-          if (!chain_wait(c_up + c, need(e_up, c), l, m.status, &t0)) return false;
-      return true;
-    case CK_CPL:
-      if (l.waits & kWaitLevel)
-        return chain_wait(c_lvl + it.level, need(e_lvl, it.level), l, m.status, &t0);
-      return true;
-    case CK_DN:
-    case CK_LEAF:
-      if (l.waits & kWaitCpl) {
-        if (!chain_wait(c_cpl + a, need(e_cpl, a), l, m.status, &t0)) return false;
-        if (it.kind == CK_DN)
-          for (int c = 2 * a + 1; c <= 2 * a + 2; ++c)
-            if (!chain_wait(c_cpl + c, need(e_cpl, c), l, m.status, &t0)) return false;
-      }
-      if ((l.waits & kWaitDn) && a >= 1) {
-        const int p = (a - 1) / 2;
-        if (!chain_wait(c_dn + p, need(e_dn, p), l, m.status, &t0)) return false;
-      }
-      return true;
-  }
-  return true;
-}
 
 // out of line: inlined, the twelve tile shapes of a launch share one register allocation
 // (210 registers, one CTA per SM); as calls each keeps its own and the kernel needs the
@@ -170,7 +94,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__
         t = atomicAdd(l.ticket, 1);
         // the acquire loads of the waits order this CTA's operand reads (after the barrier
         // below) after the producers' writes
-        if (t < total) go = chain_deps(m, m.items[l.item_begin + t / m.n_ct], l) ? 1 : 0;
+        if (t < total) go = chain_deps(m.sync, m.items[l.item_begin + t / m.n_ct], l) ? 1 : 0;
       }
       s_t = t;
       s_go = go;
@@ -195,19 +119,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__
         break;
     }
     __syncthreads();  // the tile's outputs are written and its shared memory is free again
-    if (threadIdx.x == 0 && it.kind != CK_LEAF) {  // nothing waits for a leaf item
-      __threadfence();
-      const int n = m.n_nodes;
-      switch (it.kind) {
-        case CK_UP:
-          atomicAdd(m.ctr + it.node, 1);
-          atomicAdd(m.ctr + 3 * n + it.level, 1);
-          break;
-        case CK_CPL: atomicAdd(m.ctr + n + it.node, 1); break;
-        case CK_DN: atomicAdd(m.ctr + 2 * n + it.node, 1); break;
-        default: break;
-      }
-    }
+    if (threadIdx.x == 0) chain_done(m.sync, it);
   }
 }
 

@@ -152,7 +152,7 @@ int64_t ctx_bytes(const Handle& h, int64_t q, int mode, int dtype) {
            align_up(h.chain.n_ctr * 4);
   }
   const int64_t io = dtype == HMAT_DTYPE_F32 ? 2 * align_up(std::max<int64_t>(h.n_points, 1) * q * 8) : 0;
-  return 2 * align_up(r * q * 8) + io;
+  return 2 * align_up(r * q * 8) + io + align_up(h.chain64.n_ctr * 4);
 }
 
 void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* base, int dtype) {
@@ -182,6 +182,7 @@ void ctx_bind(const Handle& h, EvalContext* c, int64_t q, int mode, uint8_t* bas
   } else {
     c->ws = (double*)take(r * q * 8);
     c->us = (double*)take(r * q * 8);
+    c->chain_ctr = (int32_t*)take(h.chain64.n_ctr * 4);
     if (dtype == HMAT_DTYPE_F32) {
       c->w64 = (double*)take(std::max<int64_t>(h.n_points, 1) * q * 8);
       c->y64 = (double*)take(std::max<int64_t>(h.n_points, 1) * q * 8);
@@ -220,14 +221,12 @@ ChainMember chain_member(const Handle& h, const EvalContext* c, void* Y, bool y_
   m.perm = h.perm;
   m.far_rows = h.far_rows;
   m.items = h.chain.items;
-  m.expect = h.chain.expect;
-  m.ctr = c->chain_ctr + kChainCtrHead;
-  m.status = h.status;
   m.q = q;
   m.bn = chain_bn(q);
   m.n_ct = (int32_t)((q + m.bn - 1) / m.bn);
-  m.n_nodes = (int32_t)h.n_nodes;
   m.first_leaf = (int32_t)(h.n_leaves - 1);
+  m.sync = ChainSync{h.chain.expect, c->chain_ctr + kChainCtrHead, h.status, (int32_t)h.n_nodes, m.first_leaf,
+                     m.n_ct, 0};
   m.xv = q % 4 == 0 ? 1 : 0;
   m.y_f32 = y_f32 ? 1 : 0;
   return m;
@@ -240,6 +239,43 @@ ChainLaunch chain_launch(const Handle& h, const EvalContext* c, int part, int32_
   l.ticket = c->chain_ctr + part;
   l.abort_flag = c->chain_ctr + 3;
   l.waits = h.chain.waits[part];
+  l.extra = extra;
+  l.limit_ns = limit_ns;
+  return l;
+}
+
+ChainMember64 chain_member64(const Handle& h, const EvalContext* c, const double* W, double* Y, int64_t q) {
+  ChainMember64 m{};
+  m.tiles = h.tiles;
+  m.tasks = h.tasks;
+  m.entries = h.entries;
+  m.arena = h.arena;
+  m.W = W;
+  m.ws = c->ws;
+  m.us = c->us;
+  m.Y = Y;
+  m.perm = h.perm;
+  m.far_rows = h.far_rows;
+  m.items = h.chain64.items;
+  m.q = q;
+  m.first_leaf = (int32_t)(h.n_leaves - 1);
+  // the column tiles are those of the shape the launch uses; the counters count them
+  const TuneEntry* t = find_tuned(h, q, HMAT_MODE_FP64);
+  const int shape = t && t->chain_shape >= 0 ? t->chain_shape : fp64_default_shape(q);
+  const int bn = fp64_shape_columns(shape);
+  m.n_ct = (int32_t)((q + bn - 1) / bn);
+  m.sync = ChainSync{h.chain64.expect, c->chain_ctr + kChainCtrHead, h.status, (int32_t)h.n_nodes, m.first_leaf,
+                     m.n_ct, 0};
+  return m;
+}
+
+ChainLaunch chain_launch64(const Handle& h, const EvalContext* c, int32_t extra, uint64_t limit_ns) {
+  ChainLaunch l{};
+  l.item_begin = h.chain64.begin[0];
+  l.n_items = h.chain64.count[0];
+  l.ticket = c->chain_ctr;
+  l.abort_flag = c->chain_ctr + 3;
+  l.waits = h.chain64.waits[0];
   l.extra = extra;
   l.limit_ns = limit_ns;
   return l;
@@ -312,8 +348,10 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const void* W, void* Y, int64_t
   double* Y64 = f32 ? c->y64 : (double*)Y;
   if (f32 && (e = launch_widen((const float*)W, c->w64, h->n_points * q, s)) != cudaSuccess) return cuda_status(e);
   const TuneEntry* tuned = find_tuned(*h, q, HMAT_MODE_FP64);
+  // the near field, one launch per row-tile size; then the far field as one persistent launch
   for (size_t i = 0; i < h->phases.size(); ++i) {
     const Phase& ph = h->phases[i];
+    if (ph.kind != PH_NEAR) continue;
     const double* X = ph.x == MAT_USER ? W64 : (ph.x == MAT_SKEL_W ? c->ws : c->us);
     double* Yd = ph.y == MAT_USER ? Y64 : (ph.y == MAT_SKEL_W ? c->ws : c->us);
     const int64_t* xm = phase_x_map(*h, ph);
@@ -321,6 +359,15 @@ hmat_status eval_impl(Handle* h, EvalContext* c, const void* W, void* Y, int64_t
     const int shape = tuned && i < tuned->shape.size() ? tuned->shape[i] : -1;
     if (!prof_begin(h, (int32_t)ph.kind, s, &rec)) return HMAT_ECUDA;
     e = launch_fp64_phase(*h, ph, X, xm, Yd, ym, q, shape, -1, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!prof_end(h, rec, s)) return HMAT_ECUDA;
+  }
+  if (h->chain64.count[0] > 0) {
+    if ((e = cudaMemsetAsync(c->chain_ctr, 0, (size_t)h->chain64.n_ctr * 4, s)) != cudaSuccess) return cuda_status(e);
+    const ChainMember64 cm = chain_member64(*h, c, W64, Y64, q);
+    const int shape = tuned && tuned->chain_shape >= 0 ? tuned->chain_shape : fp64_default_shape(q);
+    if (!prof_begin(h, HMAT_PHASE_FAR_UP, s, &rec)) return HMAT_ECUDA;
+    e = launch_chain64(cm, chain_launch64(*h, c, 0, kChainWaitNs), shape, tuned ? tuned->chain_grid : 0, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (!prof_end(h, rec, s)) return HMAT_ECUDA;
   }
@@ -444,21 +491,27 @@ extern "C" hmat_status hmat_eval_host(hmat_t h, const double* W, double* Y, int6
   return hmat_eval_host_typed(h, W, Y, q, mode, HMAT_DTYPE_F64, stream);
 }
 
-extern "C" hmat_status hmat_selftest_chain_timeout(hmat_t h, int64_t q, int64_t limit_ns, void* stream) {
+extern "C" hmat_status hmat_selftest_chain_timeout(hmat_t h, int64_t q, int mode, int64_t limit_ns, void* stream) {
   if (!h || q <= 0 || limit_ns <= 0 || limit_ns > 10000000000LL) return HMAT_EINVAL;
-  if (!h->has_mixed) return HMAT_EUNSUPPORTED;
+  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
+  if ((mode == HMAT_MODE_MIXED && !h->has_mixed) || (mode == HMAT_MODE_FP64 && !h->has_fp64))
+    return HMAT_EUNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
   if (dev != h->device) return HMAT_EINVAL;
-  if (h->chain.count[0] == 0) return HMAT_EINVAL;  // no far field: nothing to wait on
-  hmat_status st = ctx_reserve(*h, h->ctx, q, HMAT_MODE_MIXED);
+  const ChainPlan& plan = mode == HMAT_MODE_MIXED ? h->chain : h->chain64;
+  if (plan.count[0] == 0) return HMAT_EINVAL;  // no far field: nothing to wait on
+  hmat_status st = ctx_reserve(*h, h->ctx, q, mode);
   if (st != HMAT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaMemsetAsync(h->ctx->chain_ctr, 0, (size_t)h->chain.n_ctr * 4, s);
+  cudaError_t e = cudaMemsetAsync(h->ctx->chain_ctr, 0, (size_t)plan.n_ctr * 4, s);
   if (e != cudaSuccess) return cuda_status(e);
   // the workspaces are not filled: the launch waits before it reads or writes any of them
-  const ChainMember m = chain_member(*h, h->ctx, nullptr, false, q);
-  return cuda_status(launch_chain(m, chain_launch(*h, h->ctx, 0, 1, (uint64_t)limit_ns), 0, s));
+  if (mode == HMAT_MODE_MIXED)
+    return cuda_status(launch_chain(chain_member(*h, h->ctx, nullptr, false, q),
+                                    chain_launch(*h, h->ctx, 0, 1, (uint64_t)limit_ns), 0, s));
+  return cuda_status(launch_chain64(chain_member64(*h, h->ctx, nullptr, nullptr, q),
+                                    chain_launch64(*h, h->ctx, 1, (uint64_t)limit_ns), fp64_default_shape(q), 0, s));
 }
 
 extern "C" hmat_status hmat_profile(hmat_t h, int enable) {

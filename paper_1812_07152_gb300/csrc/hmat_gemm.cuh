@@ -51,20 +51,19 @@ struct Cfg {
 
 __device__ __forceinline__ int64_t map_row(const int64_t* __restrict__ m, int64_t r) { return m ? m[r] : r; }
 
-// The grid is one-dimensional: CTA b works on tile b / n_col_tiles and column tile
-// b % n_col_tiles, so the column tiles of one output block run side by side and
-// read each block of A from HBM once (the others hit L2).
+// One CTA tile: output rows m0 .. m0 + BM - 1 of the tile's task, columns q0 .. q0 + BN - 1;
+// the CTA has exactly Cfg::kThreads threads.
 //
 // TA: stored block type, TX / TY: input / output matrix types, TC: the type of the
 // products and sums. Entry offsets index the FP64 arena; a_shift maps them into an
 // arena that holds only the values from a_shift on. kOtf: the blocks are not read but
 // evaluated from the points (`otf`), entry by entry, as the build evaluates them.
 template <typename TA, typename TX, typename TY, typename TC, int BM, int BN, int CTM, int CTN, bool kOtf>
-__global__ void __launch_bounds__(Cfg<BM, BN, CTM, CTN>::kThreads)
-k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
-               const GemmEntry* __restrict__ entries, const TA* __restrict__ arena, int64_t a_shift,
-               const TX* X, const int64_t* __restrict__ x_map,
-               TY* Y, const int64_t* __restrict__ y_map, int64_t q, int n_col_tiles, OtfArgs otf) {
+__device__ __forceinline__ void gemm_tile(const GemmTile tile, const GemmTask* __restrict__ tasks,
+                                          const GemmEntry* __restrict__ entries, const TA* __restrict__ arena,
+                                          int64_t a_shift, const TX* X, const int64_t* __restrict__ x_map, TY* Y,
+                                          const int64_t* __restrict__ y_map, int64_t q, int64_t q0,
+                                          const OtfArgs& otf) {
   using C = Cfg<BM, BN, CTM, CTN>;
   constexpr int NT = C::kThreads;
   constexpr int TM = CTM, TN = CTN;
@@ -72,10 +71,8 @@ k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ 
   __shared__ TC As[2][BK][BM + 1];
   __shared__ TC Xs[2][BK][BN];
 
-  const GemmTile tile = tiles[blockIdx.x / n_col_tiles];
   const GemmTask task = tasks[tile.task];
   const int m0 = tile.m0;
-  const int64_t q0 = (int64_t)(blockIdx.x % n_col_tiles) * BN;
   const int tid = threadIdx.x;
   const int ty = tid / CX, tx = tid % CX;
 
@@ -173,6 +170,20 @@ k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ 
       if (c < q) dst[c] = task.accumulate ? (TY)(dst[c] + (TY)acc[i][j]) : (TY)acc[i][j];
     }
   }
+}
+
+// The grid is one-dimensional: CTA b works on tile b / n_col_tiles and column tile
+// b % n_col_tiles, so the column tiles of one output block run side by side and
+// read each block of A from HBM once (the others hit L2).
+template <typename TA, typename TX, typename TY, typename TC, int BM, int BN, int CTM, int CTN, bool kOtf>
+__global__ void __launch_bounds__(Cfg<BM, BN, CTM, CTN>::kThreads)
+k_grouped_gemm(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
+               const GemmEntry* __restrict__ entries, const TA* __restrict__ arena, int64_t a_shift,
+               const TX* X, const int64_t* __restrict__ x_map,
+               TY* Y, const int64_t* __restrict__ y_map, int64_t q, int n_col_tiles, OtfArgs otf) {
+  gemm_tile<TA, TX, TY, TC, BM, BN, CTM, CTN, kOtf>(tiles[blockIdx.x / n_col_tiles], tasks, entries, arena, a_shift,
+                                                     X, x_map, Y, y_map, q,
+                                                     (int64_t)(blockIdx.x % n_col_tiles) * BN, otf);
 }
 
 template <typename TA, typename TX, typename TY, typename TC, int BM, int BN, int CTM, int CTN, bool kOtf>

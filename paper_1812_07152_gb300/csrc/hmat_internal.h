@@ -157,6 +157,17 @@ struct ChainItem {
 // Which dependencies a launch waits for (the others are ordered by the stream).
 constexpr uint32_t kWaitUp = 1, kWaitLevel = 2, kWaitCpl = 4, kWaitDn = 8;
 
+// The dependency state of one evaluation's chain (per member of a launch).
+struct ChainSync {
+  const int32_t* expect;      // items per node of CK_UP, CK_CPL, CK_DN, then CK_UP items per level
+  int32_t* ctr;               // completed items (x column tiles), same layout as expect
+  int* status;                // the handle's status word
+  int32_t n_nodes;
+  int32_t first_leaf;
+  int32_t n_ct;               // column tiles of each item
+  int32_t pad;
+};
+
 // Everything an item needs of one evaluation of one HMatrix.
 struct ChainMember {
   const GemmTile* tiles;
@@ -170,16 +181,35 @@ struct ChainMember {
   const int64_t* perm;
   const int64_t* far_rows;
   const ChainItem* items;
-  const int32_t* expect;      // items per node of CK_UP, CK_CPL, CK_DN, then CK_UP items per level
-  int32_t* ctr;               // completed items (x column tiles), same layout as expect
-  int* status;                // the handle's status word
+  ChainSync sync;
   int64_t q;
   int32_t n_ct;               // column tiles of bn columns
   int32_t bn;                 // 32 or 64
-  int32_t n_nodes;
   int32_t first_leaf;
   int32_t xv;                 // q % 4 == 0: X rows copied 16 bytes at a time
   int32_t y_f32;              // Y holds FP32 values
+  int32_t pad;
+};
+
+// The FP64 far chain (hmat_chain64.cu): one launch over the upward pass, the coupling,
+// the downward transfers and the downward leaf step of the FP64 mode, after the near
+// field (which the stream orders before it). Items are 16-row tiles of the tasks.
+struct ChainMember64 {
+  const GemmTile* tiles;
+  const GemmTask* tasks;
+  const GemmEntry* entries;   // FP64 entries
+  const double* arena;
+  const double* W;            // caller's right-hand side (rows through perm)
+  double* ws;
+  double* us;
+  double* Y;                  // caller's output (rows through perm)
+  const int64_t* perm;
+  const int64_t* far_rows;
+  const ChainItem* items;
+  ChainSync sync;
+  int64_t q;
+  int32_t n_ct;
+  int32_t first_leaf;
 };
 
 // One persistent launch: tickets item_begin .. item_begin + n_items - 1 of member m,
@@ -208,6 +238,10 @@ struct ChainPlan {
 constexpr int kChainCtrHead = 4;
 
 cudaError_t launch_chain(const ChainMember& m, const ChainLaunch& l, int grid_cap, cudaStream_t stream);
+// FP64 chain with column tiles of kColBN[shape] columns; chain64_prepare caches the
+// kernels' occupancy on the current device (at load, outside any graph capture).
+cudaError_t launch_chain64(const ChainMember64& m, const ChainLaunch& l, int shape, int grid_cap, cudaStream_t stream);
+cudaError_t chain64_prepare();
 // Sets the chain kernels' attributes on the current device (once) and returns the CTAs
 // that fit on it at once (16-byte X copies, 4-byte X copies; either may be null);
 // called at load, so that no launch (or graph capture) does it.
@@ -232,7 +266,7 @@ struct EvalContext {
   float* w32 = nullptr;          // mixed: FP32 copy of W in tree order
   float* ws32 = nullptr;         // mixed: FP32 skeleton workspaces
   float* us32 = nullptr;
-  int32_t* chain_ctr = nullptr;  // mixed: tickets and completion counters of the far chain
+  int32_t* chain_ctr = nullptr;  // tickets and completion counters of the far chain (either mode)
   double* w64 = nullptr;         // FP64 mode with FP32 W and Y: W widened, Y before rounding (n x q each)
   double* y64 = nullptr;
   void* host_w = nullptr;        // device copies of W / Y for hmat_eval_host
@@ -251,7 +285,8 @@ struct TuneEntry {
   int mode = 0;
   std::vector<int8_t> shape;   // FP64: column shape (index into kColBN) per entry of Handle::phases
   int n_t = 0;                 // mixed: columns per tensor-core CTA
-  int chain_grid = 0;          // mixed: CTAs of the persistent far chain (0: every resident CTA)
+  int chain_grid = 0;          // CTAs of the persistent far chain (0: every resident CTA)
+  int chain_shape = -1;        // FP64: column shape of the far chain (index into kColBN; -1: default)
   double default_ms = 0, tuned_ms = 0;
 };
 
@@ -293,6 +328,7 @@ struct Handle {
                                  // of 4 (rows m..lda-1 zero), a_off a multiple of 4
   GemmEntry* entries32 = nullptr;  // the entries with a_off/lda into arena32 (trans = 1)
   ChainPlan chain;                 // the far field of the mixed mode as persistent launches
+  ChainPlan chain64;               // the far field of the FP64 mode as one persistent launch (range A)
 
   // near blocks evaluated on the fly (HMAT_BUILD_NEAR_OTF): the arena holds no near
   // blocks; the near phase computes K(x_i, x_j) from the tree-ordered points
@@ -429,6 +465,9 @@ cudaError_t launch_narrow(const double* src, float* dst, int64_t n, cudaStream_t
 // chosen by the autotuner.
 ChainMember chain_member(const Handle& h, const EvalContext* c, void* Y, bool y_f32, int64_t q);
 ChainLaunch chain_launch(const Handle& h, const EvalContext* c, int part, int32_t extra, uint64_t limit_ns);
+// The same for the FP64 mode's single far-chain launch (the column shape from the tuned entry).
+ChainMember64 chain_member64(const Handle& h, const EvalContext* c, const double* W, double* Y, int64_t q);
+ChainLaunch chain_launch64(const Handle& h, const EvalContext* c, int32_t extra, uint64_t limit_ns);
 int chain_grid_cap(const Handle& h, int64_t q);
 hmat_status cuda_status(cudaError_t e);
 

@@ -1,9 +1,9 @@
 // hmat_autotune: picks the tile shapes of one HMatrix's evaluation for one q and mode
 // by timing the candidates on the device (CUDA events on the caller's stream).
 //
-// FP64 mode: per launch of the evaluation (one per phase and row-tile size), the
-// column tile of the grouped GEMM among the widths 1..64 that waste less than half
-// of a tile on padding. Mixed mode: the column width of the tensor-core near-field
+// FP64 mode: per near-field launch (one per row-tile size), the column tile of the
+// grouped GEMM among the widths 1..64 that waste less than half of a tile on padding,
+// then the column tile of the far chain timed on whole chain launches. Mixed mode: the column width of the tensor-core near-field
 // CTAs (the number of CTAs that share one D tile), then the number of CTAs of the
 // persistent far chain, timed on whole evaluations. Every candidate sums each output
 // in the same order, so a tuned evaluation gives bitwise the result of an untuned one;
@@ -132,6 +132,7 @@ extern "C" hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream
     const std::vector<int> cand = fp64_candidates(q);
     for (size_t i = 0; i < h->phases.size(); ++i) {
       const Phase& ph = h->phases[i];
+      if (ph.kind != PH_NEAR) continue;  // the far field runs as one chain launch (below)
       const double* X = ph.x == MAT_USER ? W : (ph.x == MAT_SKEL_W ? c->ws : c->us);
       double* Yd = ph.y == MAT_USER ? Y : (ph.y == MAT_SKEL_W ? c->ws : c->us);
       const int64_t* xm = phase_x_map(*h, ph);
@@ -174,6 +175,77 @@ extern "C" hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream
       entry.default_ms += t_def * scale;
       entry.tuned_ms += t_best * scale;
       if (ph.kind == PH_NEAR) near_cols = std::max(near_cols, fp64_shape_columns(best));
+      ++n_tuned;
+    }
+    // the far chain: its column width, timed on whole launches (near field untouched); a
+    // short chain (latency-bound: thin levels, few tiles per level) also tries narrower
+    // tiles, which spread each level over more CTAs
+    if (h->chain64.count[0] > 0) {
+      auto prev = std::find_if(h->tuned.begin(), h->tuned.end(),
+                               [&](const TuneEntry& t) { return t.q == q && t.mode == mode; });
+      const bool had = prev != h->tuned.end();
+      const TuneEntry saved = had ? *prev : TuneEntry{};
+      if (!had) h->tuned.push_back(entry);
+      TuneEntry* live = &*std::find_if(h->tuned.begin(), h->tuned.end(),
+                                       [&](const TuneEntry& t) { return t.q == q && t.mode == mode; });
+      *live = entry;
+      int grid_cap = 0;
+      auto run_chain = [&](int shape) -> cudaError_t {
+        live->chain_shape = shape;
+        cudaError_t ce = cudaMemsetAsync(c->chain_ctr, 0, (size_t)h->chain64.n_ctr * 4, s);
+        if (ce != cudaSuccess) return ce;
+        return launch_chain64(chain_member64(*h, c, W, Y, q), chain_launch64(*h, c, 0, kChainWaitNs), shape,
+                              grid_cap, s);
+      };
+      const int def = fp64_default_shape(q);
+      std::vector<int> cand = fp64_candidates(q);
+      const double t_def = timer.best([&] { return run_chain(def); });
+      if (t_def >= 0 && t_def < 5.0)
+        for (int sh = 0; sh < def; ++sh)
+          if (std::find(cand.begin(), cand.end(), sh) == cand.end()) cand.push_back(sh);
+      double t_best = t_def;
+      int best = def;
+      for (int sh : cand) {
+        if (t_def < 0) break;
+        if (sh == def) continue;
+        const double t = timer.best([&] { return run_chain(sh); });
+        if (t < 0) {
+          t_best = -1;
+          break;
+        }
+        if (t < t_best) {
+          t_best = t;
+          best = sh;
+        }
+      }
+      // then the grid: fewer CTAs than the default (less waiting) or more (more warps per SM)
+      int best_grid = 0;
+      for (int g : {sms, 2 * sms, 4 * sms, 16 * sms, 64 * sms}) {
+        if (t_best < 0) break;
+        grid_cap = g;
+        const double t = timer.best([&] { return run_chain(best); });
+        if (t < 0) {
+          t_best = -1;
+          break;
+        }
+        if (t < t_best) {
+          t_best = t;
+          best_grid = g;
+        }
+      }
+      if (had) {
+        *live = saved;
+      } else {
+        h->tuned.erase(h->tuned.begin() + (live - &h->tuned[0]));
+      }
+      if (t_def < 0 || t_best < 0) {
+        cleanup();
+        return HMAT_ECUDA;
+      }
+      entry.chain_shape = best;
+      entry.chain_grid = best_grid;
+      entry.default_ms += t_def;
+      entry.tuned_ms += t_best;
       ++n_tuned;
     }
   } else {

@@ -176,7 +176,8 @@ def library() -> ctypes.CDLL:
                                       ctypes.POINTER(HmatTuneReport)]
         lib.hmat_selftest_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         lib.hmat_tune_apply.argtypes = [ctypes.c_void_p, ctypes.POINTER(HmatTuneReport)]
-        lib.hmat_selftest_chain_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
+        lib.hmat_selftest_chain_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                                                    ctypes.c_void_p]
         lib.hmat_selftest_conversions.argtypes = [ctypes.c_int64, ctypes.c_uint64, _c_i64p]
         lib.hmat_plan_create.argtypes = [ctypes.POINTER(HmatPlanParams), ctypes.POINTER(ctypes.c_void_p)]
         lib.hmat_plan_build.argtypes = [ctypes.c_void_p, ctypes.POINTER(HmatCompressParams), ctypes.c_int,
@@ -421,10 +422,10 @@ def hmat_selftest_timeout(handle: int, limit_ns: int, stream=None) -> None:
     _check(library().hmat_selftest_timeout(handle, int(limit_ns), _stream(stream)), "hmat_selftest_timeout")
 
 
-def hmat_selftest_chain_timeout(handle: int, q: int, limit_ns: int, stream=None) -> None:
-    """Enqueue the mixed mode's persistent far-chain launch with requirements no item can meet: every wait
-    runs out after limit_ns and latches HMAT_ETIMEOUT in the handle's status word."""
-    _check(library().hmat_selftest_chain_timeout(handle, int(q), int(limit_ns), _stream(stream)),
+def hmat_selftest_chain_timeout(handle: int, q: int, limit_ns: int, mode: int = HMAT_MODE_MIXED, stream=None) -> None:
+    """Enqueue the persistent far-chain launch of `mode` with requirements no item can meet: every wait runs out
+    after limit_ns and latches HMAT_ETIMEOUT in the handle's status word."""
+    _check(library().hmat_selftest_chain_timeout(handle, int(q), int(mode), int(limit_ns), _stream(stream)),
            "hmat_selftest_chain_timeout")
 
 

@@ -7,6 +7,7 @@ tree level, with bounded dependency waits between their CTA tiles).
   dependency came after it in the list), for both coupling engines.
 - The serialised profiling mode gives bitwise the result of the overlapped one, and
   an evaluation takes fewer than ten launches.
+- The FP64 mode's far field is one persistent launch too, bitwise the per-level launches.
 - A chain launch whose waits cannot be met gives up after the host-chosen limit,
   reports HMAT_ETIMEOUT through the status word, and the context stays usable.
 """
@@ -124,3 +125,59 @@ def test_tune_apply_rejects_bad_choices():
     finally:
         hp.hmat_free(h)
         hp.hmat_free(h64)
+
+
+@pytest.mark.parametrize("base,n,q,ov", [("h2_gmm8d_n65536", 4096, 37, ()), ("hss_uniform3d_n2048", 2048, 16, ()),
+                                         ("h2_imq3d_n262144", 5000, 3, (("leaf_size", 40),)),
+                                         ("hss_uniform3d_n2048", 1500, 24, (("tol", 0.0), ("max_rank", 10 ** 6)))])
+def test_fp64_chain_equals_per_level_launches_bitwise(base, n, q, ov):
+    """The FP64 far field as one persistent launch of 16-row tiles sums every output in the
+    order of the per-level launches that hmat_eval_noalloc keeps, so the two agree bit for bit,
+    for every column width the tuner may pick."""
+    import ctypes
+    w, H, _ = oracle_case(base, n, q, **dict(ov))
+    W = rhs(w.n, q, 31 + q)
+    Yref = hm.evaluate(H, W)
+    h = hp.hmat_load(**desc_from_oracle(H))
+    try:
+        fn = hp.library().hmat_eval_noalloc
+        fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        fn.restype = ctypes.c_int
+        Wd = torch.from_numpy(W).cuda()
+        Yl = torch.full_like(Wd, float("nan"))
+        assert fn(h, Wd.data_ptr(), Yl.data_ptr(), q, torch.cuda.current_stream().cuda_stream) == hp.HMAT_OK
+        Yc = torch.full_like(Wd, float("nan"))
+        hp.hmat_eval(h, Wd, Yc, q, hp.HMAT_MODE_FP64)
+        assert hp.hmat_status_poll(h) == hp.HMAT_OK
+        assert torch.equal(Yc, Yl)
+        assert np.linalg.norm(Yc.cpu().numpy() - Yref) <= 1e-12 * np.linalg.norm(Yref)
+        rep = hp.hmat_autotune(h, q, hp.HMAT_MODE_FP64)
+        Yt = torch.full_like(Wd, float("nan"))
+        hp.hmat_eval(h, Wd, Yt, q, hp.HMAT_MODE_FP64)
+        assert hp.hmat_status_poll(h) == hp.HMAT_OK
+        assert torch.equal(Yt, Yl), rep
+    finally:
+        hp.hmat_free(h)
+
+
+def test_fp64_chain_wait_runs_out_and_context_survives():
+    w, H, _ = oracle_case("hss_uniform3d_n2048", 2048, 16)
+    h = hp.hmat_load(**desc_from_oracle(H))
+    try:
+        W = rhs(w.n, 16, 12)
+        Wd = torch.from_numpy(W).cuda()
+        Y0 = torch.empty_like(Wd)
+        hp.hmat_eval(h, Wd, Y0, 16, hp.HMAT_MODE_FP64)
+        assert hp.hmat_status_poll(h) == hp.HMAT_OK
+        hp.hmat_selftest_chain_timeout(h, 16, 2_000_000, mode=hp.HMAT_MODE_FP64)
+        assert hp.hmat_status_poll(h) == hp.HMAT_ETIMEOUT
+        assert hp.hmat_status_poll(h) == hp.HMAT_OK
+        Y1 = torch.empty_like(Wd)
+        hp.hmat_eval(h, Wd, Y1, 16, hp.HMAT_MODE_FP64)
+        assert hp.hmat_status_poll(h) == hp.HMAT_OK
+        assert torch.equal(Y0, Y1)
+        with pytest.raises(hp.HmatError) as ei:
+            hp.hmat_selftest_chain_timeout(h, 16, 2_000_000, mode=hp.HMAT_MODE_MIXED)
+        assert ei.value.status == hp.HMAT_EUNSUPPORTED
+    finally:
+        hp.hmat_free(h)
