@@ -6,9 +6,12 @@ bench.py times.
   leaves (the longest and shortest near lists among them) are formed by the oracle's
   leaf-subset evaluator and compared with the GPU's FP64 result (relative error <=
   1e-12 on those rows) and its mixed result (<= 1e-6), after autotuning as the bench does.
-* N = 262144 inverse-multiquadric recipe (q = 512): too large for the oracle, so the
-  GPU's own HMatrix (hmat_build) is held to properties that hold at any size: K~ is
-  symmetric (W1^T K~ W2 = W2^T K~ W1) and the product is linear, in FP64 to 1e-12.
+* N = 262144 inverse-multiquadric recipe (uniform 3-D, 1/sqrt(r^2 + 0.01), leaf 256,
+  tol 1e-7, q = 512: the precision-mode recipe): the same comparison with the oracle's
+  own HMatrix at full size (about 11 GB of near blocks and 4 GB of coupling blocks on
+  the host), both modes after autotuning; and the GPU's own HMatrix (hmat_build) held to
+  properties that hold at any size: K~ is symmetric (W1^T K~ W2 = W2^T K~ W1) and the
+  product is linear, in FP64 to 1e-12.
 """
 import numpy as np
 import pytest
@@ -27,8 +30,7 @@ def _rows(H, leaves):
     return np.concatenate([t.perm[t.index_set(a)] for a in leaves])
 
 
-def test_mixture_recipe_full_size_sampled_rows():
-    w = WORKLOADS["h2_gmm8d_n65536"]
+def _sampled_rows_against_oracle(w, label):
     H, _ = hm.compress_workload(w)
     t = H.tree
     lengths = {}
@@ -50,10 +52,18 @@ def test_mixture_recipe_full_size_sampled_rows():
             assert hp.hmat_status_poll(h) == hp.HMAT_OK
             Y = Yd.cpu().numpy()[rows]
             err = np.linalg.norm(Y - Yref[rows]) / np.linalg.norm(Yref[rows])
-            print(f"full-size mixture recipe, mode {mode}: relative error on {len(rows)} sampled rows {err:.3e}")
+            print(f"full-size {label} recipe, mode {mode}: relative error on {len(rows)} sampled rows {err:.3e}")
             assert err <= tol, (mode, err)
     finally:
         hp.hmat_free(h)
+
+
+def test_mixture_recipe_full_size_sampled_rows():
+    _sampled_rows_against_oracle(WORKLOADS["h2_gmm8d_n65536"], "mixture")
+
+
+def test_imq_recipe_full_size_sampled_rows():
+    _sampled_rows_against_oracle(WORKLOADS["h2_imq3d_n262144"], "inverse-multiquadric")
 
 
 def test_imq_recipe_full_size_symmetry_and_linearity():
