@@ -718,11 +718,14 @@ def run_batch(args, dist) -> dict:
         t_tune = time.perf_counter() - t0
         hp.hmat_batch_free(b)
         b = hp.hmat_batch_create(handles, mode)
+        batch_tune = hp.hmat_batch_autotune(b, Ws, Ys, stream)   # the chain grid, on whole replays
         ms_graph = dist.max(timed(lambda: hp.hmat_batch_eval(b, Ws, Ys, stream)))
+        info = hp.hmat_batch_info(b)
         ms_loop = dist.max(timed(lambda: [hp.hmat_eval(h, W, Y, W.shape[1], mode, stream)
                                           for h, W, Y in zip(handles, Ws, Ys)]))
         hp.hmat_batch_free(b)
         out[name] = {"value": round(dist.world * cols / (ms_graph / 1e3), 1), "ms_per_step": round(ms_graph, 4),
+                     "kernels_per_replay": info["kernels"], "batch_autotune": batch_tune,
                      "untuned_value": round(dist.world * cols / (ms_default / 1e3), 1),
                      "untuned_ms": round(ms_default, 4), "autotune_s": round(t_tune, 2),
                      "one_call_per_matrix_value": round(dist.world * cols / (ms_loop / 1e3), 1),

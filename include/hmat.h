@@ -446,20 +446,38 @@ hmat_status hmat_autotune(hmat_t h, int64_t q, int mode, void* stream, hmat_tune
 hmat_status hmat_tune_apply(hmat_t h, const hmat_tune_report* choice);
 
 /*
- * Batches: many HMatrices (uneven sizes, ranks and q) evaluated together. A batch
- * owns one evaluation context (workspaces) and one CUDA stream per member; the
- * first hmat_batch_eval with a given set of W, Y pointers and q values captures
- * every member's evaluation as a parallel branch of one CUDA graph, later calls
- * with the same arguments replay that graph with a single launch (a call with
- * other arguments captures a new graph). The same handle may appear more than
- * once. Handles must outlive the batch and must not be evaluated elsewhere while
- * one of the batch's graphs runs.
+ * Batches: many HMatrices (uneven sizes, ranks and q) evaluated together. The first
+ * hmat_batch_eval with a given set of W, Y pointers and q values captures one CUDA
+ * graph in which every step of the evaluation is one launch over all members (a
+ * flattened work list with a member table): in the mixed mode the W splits, the
+ * persistent far chains, the tensor-core couplings, the tensor-core near fields and
+ * the downward leaf steps of all members, about ten kernels in all; in the FP64 mode
+ * each member's near-field launches on parallel graph branches, then the far fields
+ * of all members in one persistent chain launch per column tile width. Later calls
+ * with the same arguments replay that graph with a single launch (a call with other
+ * arguments captures a new graph). Each member's result is bitwise what it gets
+ * alone, with the handle's tuned tile shapes. The same handle may appear more than
+ * once. Handles must outlive the batch and must not be evaluated elsewhere while one
+ * of the batch's graphs runs. The batch owns one device block for every member's
+ * workspaces and the launch tables.
  *
  * hmat_batch_create - `count` handles (all on the current device), `mode` is
  * HMAT_MODE_FP64 or HMAT_MODE_MIXED (every handle loaded with HMAT_LOAD_MIXED).
  * hmat_batch_eval - Y[i] = K~_i W[i] (device pointers, n_i x q[i], caller order)
  * for every member, enqueued on `stream`; the first call for a new argument set
  * allocates workspaces (cudaMalloc, which synchronises the device).
+ * hmat_batch_info - out[0] members, out[1] kernel launches in the graph of the last
+ * argument set (0 before the first call), out[2] device bytes held by the batch, out[3]
+ * the CTAs of its chain launches (0: every resident CTA), out[4] 1 when the batch runs
+ * the branched schedule.
+ * hmat_batch_autotune - time whole replays of the batch for these arguments with the
+ * chain launches capped at several CTA counts (the chains run beside the tensor-core
+ * near field, which needs whole SMs), and with the branched schedule (every member's
+ * own evaluation as a branch of the graph: more, smaller launches that overlap one
+ * another), and keep the fastest for later calls; the members' own tile shapes are
+ * those of hmat_autotune. Results are bitwise the same for every choice. ms_default /
+ * ms_tuned (may be NULL) receive the replay time of the flattened schedule with every
+ * resident CTA and of the choice. Synchronous.
  */
 typedef struct hmat_batch* hmat_batch_t;
 hmat_status hmat_batch_create(const hmat_t* handles, int count, int mode, hmat_batch_t* out);
@@ -469,6 +487,13 @@ hmat_status hmat_batch_eval(hmat_batch_t b, const double* const* W, double* cons
  * `dtype` (a call with another dtype than the captured graph's captures a new one). */
 hmat_status hmat_batch_eval_typed(hmat_batch_t b, const void* const* W, void* const* Y, const int64_t* q, int dtype,
                                   void* stream);
+hmat_status hmat_batch_info(hmat_batch_t b, int64_t* out, int n);
+hmat_status hmat_batch_autotune(hmat_batch_t b, const void* const* W, void* const* Y, const int64_t* q, int dtype,
+                                void* stream, double* ms_default, double* ms_tuned);
+/* hmat_batch_schedule - pin the schedule without timing: branched 0 (flattened, the
+ * default) or 1, and the chain launches' CTAs (0: every resident CTA); the next call
+ * recaptures. HMAT_EINVAL for other values. */
+hmat_status hmat_batch_schedule(hmat_batch_t b, int branched, int chain_grid);
 hmat_status hmat_batch_free(hmat_batch_t b);
 
 /*

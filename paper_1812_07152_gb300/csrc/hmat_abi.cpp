@@ -503,6 +503,7 @@ hmat_status build_chain64(Handle* h, const Validated& v, const std::vector<Chain
   cp.waits[0] = kWaitUp | kWaitLevel | kWaitCpl | kWaitDn;
   const std::vector<int32_t> expect = chain_expect(items, v.n_nodes, L);
   cp.n_ctr = kChainCtrHead + (int64_t)expect.size();
+  cp.host = items;
   cudaError_t e = chain64_prepare();
   if (e == cudaSuccess) e = upload(&cp.items, items, &h->device_bytes);
   if (e == cudaSuccess) e = upload(&cp.expect, expect, &h->device_bytes);
@@ -564,6 +565,7 @@ hmat_status build_chain(Handle* h, const Validated& v, const std::vector<GemmTil
   if (items.size() > (size_t)INT32_MAX) return HMAT_EUNSUPPORTED;
   const std::vector<int32_t> expect = chain_expect(items, n, L);
   cp.n_ctr = kChainCtrHead + (int64_t)expect.size();
+  cp.host = items;
   cudaError_t e = chain_prepare(nullptr, nullptr);
   if (e == cudaSuccess) e = upload(&cp.items, items, &h->device_bytes);
   if (e == cudaSuccess) e = upload(&cp.expect, expect, &h->device_bytes);

@@ -73,49 +73,123 @@ __device__ __forceinline__ void chain_tile_bn(const ChainMember& m, const ChainI
     chain_tile_cls<TY, 64, XV>(m, it, q0, X, x_map, Y, y_map, smf);
 }
 
-// XV: the launch copies X rows 16 bytes at a time (q a multiple of 4); a kernel of its
-// own, since those shapes need far fewer registers than the 4-byte copies
-template <bool XV>
-__global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__ ChainMember m,
-                                                         const __grid_constant__ ChainLaunch l) {
+// kXV = 1: one member whose items copy X rows 16 bytes at a time (q a multiple of 4),
+// 0: 4 bytes at a time, 2: many members (batches), the width per member; kernels of
+// their own, since the 16-byte shapes need far fewer registers than the 4-byte ones.
+template <int kXV>
+__global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__ ChainMember m1,
+                                                         const __grid_constant__ ChainLaunch l,
+                                                         const __grid_constant__ ChainMulti<ChainMember> mm) {
   extern __shared__ __align__(16) float smf[];
-  __shared__ int s_t;
+  __shared__ ChainMember sm;  // the member of the current item
+  __shared__ ChainItem s_it;
+  __shared__ int64_t s_q0;
   __shared__ int s_go;
-  const int total = l.n_items * m.n_ct;
+  constexpr bool multi = kXV == 2;  // multi-member launches run the per-member form
+  const int64_t total = multi ? mm.total : (int64_t)l.n_items * m1.n_ct;
   // a launch with no dependencies (the downward leaf step) is a plain grid over its items
-  const bool free_run = l.waits == 0 && l.extra == 0;
+  const bool free_run = multi ? mm.free_run != 0 : (l.waits == 0 && l.extra == 0);
+  int cur = -1;  // warp 0: member held in sm
   for (int k = 0;; ++k) {
-    if (threadIdx.x == 0 && free_run) {
-      s_t = blockIdx.x + k * gridDim.x;
-      s_go = s_t < total;
-    } else if (threadIdx.x == 0) {
-      int go = 0, t = 0;
-      if (!*(volatile int32_t*)l.abort_flag) {
-        t = atomicAdd(l.ticket, 1);
+    if (threadIdx.x < 32) {  // warp 0: the ticket (lane 0), the member copy (all lanes)
+      int go = 0, mi = 0;
+      int64_t t = 0;
+      if (threadIdx.x == 0) {
+        if (free_run) {
+          t = blockIdx.x + (int64_t)k * gridDim.x;
+          go = t < total;
+        } else if (!*(volatile int32_t*)l.abort_flag) {
+          t = atomicAdd(l.ticket, 1);
+          go = t < total;
+        }
+        if constexpr (multi) {
+          if (go) {
+            if (mm.list) {
+              mi = mm.list[t].member;
+            } else {
+              int lo = 0, hi = mm.n_members - 1;
+              while (lo < hi) {
+                const int mid = (lo + hi) / 2;
+                if (mm.parts[mid].ticket_end > t) hi = mid;
+                else lo = mid + 1;
+              }
+              mi = lo;
+            }
+          }
+        }
+      }
+      if constexpr (multi) {
+        go = __shfl_sync(0xffffffffu, go, 0);
+        mi = __shfl_sync(0xffffffffu, mi, 0);
+        if (go && mi != cur) {  // one 32-bit word per lane
+          const uint32_t* src = reinterpret_cast<const uint32_t*>(mm.members + mi);
+          uint32_t* dst = reinterpret_cast<uint32_t*>(&sm);
+          for (int w = threadIdx.x; w < (int)(sizeof(ChainMember) / 4); w += 32) dst[w] = src[w];
+          cur = mi;
+        }
+        __syncwarp();
+      }
+      if (threadIdx.x == 0 && go) {
+        int64_t local = t;
+        uint32_t waits = l.waits;
+        int32_t ib = l.item_begin;
+        const ChainMember& mt = multi ? sm : m1;
+        if (multi && mm.list) {
+          const ChainTicket ck = mm.list[t];
+          waits = ck.waits;
+          s_it = mt.items[ck.item];
+          s_q0 = (int64_t)ck.ct * mt.bn;
+        } else {
+          if constexpr (multi) {
+            local = t - (mi > 0 ? mm.parts[mi - 1].ticket_end : 0);
+            waits = mm.parts[mi].waits;
+            ib = mm.parts[mi].item_begin;
+          }
+          s_it = mt.items[ib + local / mt.n_ct];
+          s_q0 = (local % mt.n_ct) * mt.bn;
+        }
         // the acquire loads of the waits order this CTA's operand reads (after the barrier
         // below) after the producers' writes
-        if (t < total) go = chain_deps(m.sync, m.items[l.item_begin + t / m.n_ct], l) ? 1 : 0;
+        if (!free_run) {
+          ChainLaunch lw = l;
+          lw.waits = waits;
+          go = chain_deps(mt.sync, s_it, lw) ? 1 : 0;
+        }
       }
-      s_t = t;
-      s_go = go;
+      if (threadIdx.x == 0) s_go = go;
     }
     __syncthreads();
     if (!s_go) break;
-    const int t = s_t;
-    const ChainItem it = m.items[l.item_begin + t / m.n_ct];
-    const int64_t q0 = (int64_t)(t % m.n_ct) * m.bn;
+    const ChainItem it = s_it;
+    const int64_t q0 = s_q0;
+    const ChainMember& m = multi ? sm : m1;
+    const bool xv = kXV == 2 ? m.xv != 0 : kXV == 1;
     switch (it.kind) {
-      case CK_UP:
+      case CK_UP: {
         // leaves read the FP32 tree-order copy of W, inner nodes their children's w
-        chain_tile_bn<float, XV>(m, it, q0, it.node >= m.first_leaf ? m.w32 : m.ws32, nullptr, m.ws32, nullptr, smf);
+        const float* X = it.node >= m.first_leaf ? m.w32 : m.ws32;
+        if (xv) chain_tile_bn<float, true>(m, it, q0, X, nullptr, m.ws32, nullptr, smf);
+        else chain_tile_bn<float, false>(m, it, q0, X, nullptr, m.ws32, nullptr, smf);
         break;
-      case CK_CPL: chain_tile_bn<float, XV>(m, it, q0, m.ws32, m.far_rows, m.us32, nullptr, smf); break;
-      case CK_DN: chain_tile_bn<float, XV>(m, it, q0, m.us32, nullptr, m.us32, nullptr, smf); break;
+      }
+      case CK_CPL:
+        if (xv) chain_tile_bn<float, true>(m, it, q0, m.ws32, m.far_rows, m.us32, nullptr, smf);
+        else chain_tile_bn<float, false>(m, it, q0, m.ws32, m.far_rows, m.us32, nullptr, smf);
+        break;
+      case CK_DN:
+        if (xv) chain_tile_bn<float, true>(m, it, q0, m.us32, nullptr, m.us32, nullptr, smf);
+        else chain_tile_bn<float, false>(m, it, q0, m.us32, nullptr, m.us32, nullptr, smf);
+        break;
       default:
-        if (m.y_f32)
-          chain_tile_bn<float, XV>(m, it, q0, m.us32, nullptr, static_cast<float*>(m.Y), m.perm, smf);
-        else
-          chain_tile_bn<double, XV>(m, it, q0, m.us32, nullptr, static_cast<double*>(m.Y), m.perm, smf);
+        if (m.y_f32) {
+          float* Y = static_cast<float*>(m.Y);
+          if (xv) chain_tile_bn<float, true>(m, it, q0, m.us32, nullptr, Y, m.perm, smf);
+          else chain_tile_bn<float, false>(m, it, q0, m.us32, nullptr, Y, m.perm, smf);
+        } else {
+          double* Y = static_cast<double*>(m.Y);
+          if (xv) chain_tile_bn<double, true>(m, it, q0, m.us32, nullptr, Y, m.perm, smf);
+          else chain_tile_bn<double, false>(m, it, q0, m.us32, nullptr, Y, m.perm, smf);
+        }
         break;
     }
     __syncthreads();  // the tile's outputs are written and its shared memory is free again
@@ -128,8 +202,17 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__
 namespace {
 
 std::mutex g_chain_mu;
-int g_chain_occ[2][64] = {};  // resident chain CTAs per SM, per kernel and device (0: not prepared)
+int g_chain_occ[3][64] = {};  // resident chain CTAs per SM, per kernel (kXV) and device (0: not prepared)
 int g_chain_sms[64] = {};
+
+template <int kXV>
+cudaError_t chain_occ(int dev) {
+  cudaError_t e = cudaFuncSetAttribute(k_chain<kXV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kChainSmem);
+  int o = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_chain<kXV>, kChainThreads, kChainSmem);
+  if (e == cudaSuccess) g_chain_occ[kXV][dev] = o > 0 ? o : 1;
+  return e;
+}
 
 }  // namespace
 
@@ -142,15 +225,10 @@ cudaError_t chain_prepare(int* grid_v, int* grid_s) {
   if (g_chain_occ[0][dev] == 0) {
     int s = 0;
     e = cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = chain_occ<0>(dev);
+    if (e == cudaSuccess) e = chain_occ<1>(dev);
+    if (e == cudaSuccess) e = chain_occ<2>(dev);
     if (e != cudaSuccess) return e;
-    for (int v = 0; v < 2; ++v) {
-      auto kern = v ? k_chain<true> : k_chain<false>;
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kChainSmem);
-      int o = 0;
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kChainThreads, kChainSmem);
-      if (e != cudaSuccess) return e;
-      g_chain_occ[v][dev] = o > 0 ? o : 1;
-    }
     g_chain_sms[dev] = s;
   }
   if (grid_v) *grid_v = g_chain_sms[dev] * g_chain_occ[1][dev];
@@ -168,10 +246,31 @@ cudaError_t launch_chain(const ChainMember& m, const ChainLaunch& l, int grid_ca
   int64_t grid = m.xv ? full_v : full_s;
   if (grid_cap > 0) grid = std::min<int64_t>(grid, grid_cap);
   grid = std::min<int64_t>(grid, (int64_t)l.n_items * m.n_ct);
+  const ChainMulti<ChainMember> none{nullptr, nullptr, 0, 0, 0, nullptr};
   if (m.xv)
-    k_chain<true><<<(unsigned)grid, kChainThreads, kChainSmem, stream>>>(m, l);
+    k_chain<1><<<(unsigned)grid, kChainThreads, kChainSmem, stream>>>(m, l, none);
   else
-    k_chain<false><<<(unsigned)grid, kChainThreads, kChainSmem, stream>>>(m, l);
+    k_chain<0><<<(unsigned)grid, kChainThreads, kChainSmem, stream>>>(m, l, none);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain_multi(const ChainMulti<ChainMember>& mm, const ChainLaunch& l, int grid_cap,
+                               cudaStream_t stream) {
+  if (mm.total <= 0 || mm.n_members <= 0) return cudaSuccess;
+  if (mm.total > INT32_MAX) return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = chain_prepare(nullptr, nullptr)) != cudaSuccess) return e;
+  int64_t grid;
+  {
+    std::lock_guard<std::mutex> lock(g_chain_mu);
+    grid = (int64_t)g_chain_sms[dev] * g_chain_occ[2][dev];
+  }
+  if (grid_cap > 0) grid = std::min<int64_t>(grid, grid_cap);
+  grid = std::min<int64_t>(grid, mm.total);
+  const ChainMember none{};
+  k_chain<2><<<(unsigned)grid, kChainThreads, kChainSmem, stream>>>(none, l, mm);
   return cudaGetLastError();
 }
 

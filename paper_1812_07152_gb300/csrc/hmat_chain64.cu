@@ -22,27 +22,74 @@ template <int BN, int CTM, int CTN>
 using Cfg64 = gemm::Cfg<16, BN, CTM, CTN>;
 
 template <int BN, int CTM, int CTN>
-__global__ void __launch_bounds__(Cfg64<BN, CTM, CTN>::kThreads) k_chain64(const __grid_constant__ ChainMember64 m,
-                                                                          const __grid_constant__ ChainLaunch l) {
-  __shared__ int s_t;
+__global__ void __launch_bounds__(Cfg64<BN, CTM, CTN>::kThreads)
+k_chain64(const __grid_constant__ ChainMember64 m1, const __grid_constant__ ChainLaunch l,
+          const __grid_constant__ ChainMulti<ChainMember64> mm) {
+  __shared__ ChainMember64 sm;  // the member of the current item
+  __shared__ ChainItem s_it;
+  __shared__ int64_t s_q0;
   __shared__ int s_go;
-  const int total = l.n_items * m.n_ct;
+  const bool multi = mm.members != nullptr;
+  const int64_t total = multi ? mm.total : (int64_t)l.n_items * m1.n_ct;
   const gemm::OtfArgs no_otf{nullptr, 0, KernelSpec{}};
+  int cur = -1;  // thread 0: member held in sm
   for (;;) {
     if (threadIdx.x == 0) {
-      int go = 0, t = 0;
+      int go = 0;
+      int64_t t = 0;
       if (!*(volatile int32_t*)l.abort_flag) {
         t = atomicAdd(l.ticket, 1);
-        if (t < total) go = chain_deps(m.sync, m.items[l.item_begin + t / m.n_ct], l) ? 1 : 0;
+        go = t < total;
       }
-      s_t = t;
+      if (go) {
+        int mi = 0;
+        int64_t local = t;
+        uint32_t waits = l.waits;
+        int32_t ib = l.item_begin;
+        int32_t item = -1, ct = 0;
+        if (multi && mm.list) {
+          const ChainTicket ck = mm.list[t];
+          mi = ck.member;
+          waits = ck.waits;
+          item = ck.item;
+          ct = ck.ct;
+        } else if (multi) {
+          int lo = 0, hi = mm.n_members - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (mm.parts[mid].ticket_end > t) hi = mid;
+            else lo = mid + 1;
+          }
+          mi = lo;
+          local = t - (mi > 0 ? mm.parts[mi - 1].ticket_end : 0);
+          waits = mm.parts[mi].waits;
+          ib = mm.parts[mi].item_begin;
+        }
+        if (multi && mi != cur) {  // one 32-bit word at a time: few registers live in the copy
+          const uint32_t* src = reinterpret_cast<const uint32_t*>(mm.members + mi);
+          uint32_t* dst = reinterpret_cast<uint32_t*>(&sm);
+          for (int w = 0; w < (int)(sizeof(ChainMember64) / 4); ++w) dst[w] = src[w];
+          cur = mi;
+        }
+        const ChainMember64& mt = multi ? sm : m1;
+        if (item >= 0) {
+          s_it = mt.items[item];
+          s_q0 = (int64_t)ct * BN;
+        } else {
+          s_it = mt.items[ib + local / mt.n_ct];
+          s_q0 = (local % mt.n_ct) * BN;
+        }
+        ChainLaunch lw = l;
+        lw.waits = waits;
+        go = chain_deps(mt.sync, s_it, lw) ? 1 : 0;
+      }
       s_go = go;
     }
     __syncthreads();
     if (!s_go) break;
-    const int t = s_t;
-    const ChainItem it = m.items[l.item_begin + t / m.n_ct];
-    const int64_t q0 = (int64_t)(t % m.n_ct) * BN;
+    const ChainItem it = s_it;
+    const int64_t q0 = s_q0;
+    const ChainMember64& m = multi ? sm : m1;
     const GemmTile tile = m.tiles[it.tile];
     const double* X;
     const int64_t* x_map = nullptr;
@@ -112,7 +159,8 @@ cudaError_t prepare_all(int dev) {
 }
 
 template <int BN, int CTM, int CTN>
-cudaError_t launch_shape(const ChainMember64& m, const ChainLaunch& l, int shape, int grid_cap, cudaStream_t s) {
+cudaError_t launch_shape(const ChainMember64& m, const ChainLaunch& l, const ChainMulti<ChainMember64>& mm, int shape,
+                         int grid_cap, cudaStream_t s) {
   constexpr int NT = Cfg64<BN, CTM, CTN>::kThreads;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -131,8 +179,8 @@ cudaError_t launch_shape(const ChainMember64& m, const ChainLaunch& l, int shape
     full = g_full[dev][shape];
   }
   int64_t grid = grid_cap > 0 ? std::min<int64_t>(full, grid_cap) : def;
-  grid = std::min<int64_t>(grid, (int64_t)l.n_items * m.n_ct);
-  k_chain64<BN, CTM, CTN><<<(unsigned)grid, NT, 0, s>>>(m, l);
+  grid = std::min<int64_t>(grid, mm.members ? mm.total : (int64_t)l.n_items * m.n_ct);
+  k_chain64<BN, CTM, CTN><<<(unsigned)grid, NT, 0, s>>>(m, l, mm);
   return cudaGetLastError();
 }
 
@@ -146,21 +194,37 @@ cudaError_t chain64_prepare() {
   return prepare_all(dev);
 }
 
+namespace {
+
+cudaError_t launch_any(const ChainMember64& m, const ChainLaunch& l, const ChainMulti<ChainMember64>& mm, int shape,
+                       int grid_cap, cudaStream_t stream) {
+  // the per-thread register tiles of hmat_gemm.cuh's column shapes
+  switch (shape) {
+    case 0: return launch_shape<1, 1, 1>(m, l, mm, shape, grid_cap, stream);
+    case 1: return launch_shape<2, 1, 1>(m, l, mm, shape, grid_cap, stream);
+    case 2: return launch_shape<4, 2, 1>(m, l, mm, shape, grid_cap, stream);
+    case 3: return launch_shape<8, 2, 2>(m, l, mm, shape, grid_cap, stream);
+    case 4: return launch_shape<16, 4, 4>(m, l, mm, shape, grid_cap, stream);
+    case 5: return launch_shape<32, 4, 4>(m, l, mm, shape, grid_cap, stream);
+    case 6: return launch_shape<64, 4, 4>(m, l, mm, shape, grid_cap, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
 cudaError_t launch_chain64(const ChainMember64& m, const ChainLaunch& l, int shape, int grid_cap,
                            cudaStream_t stream) {
   if (l.n_items <= 0 || m.q <= 0) return cudaSuccess;
   if ((int64_t)l.n_items * m.n_ct > INT32_MAX) return cudaErrorInvalidValue;
-  // the per-thread register tiles of hmat_gemm.cuh's column shapes
-  switch (shape) {
-    case 0: return launch_shape<1, 1, 1>(m, l, shape, grid_cap, stream);
-    case 1: return launch_shape<2, 1, 1>(m, l, shape, grid_cap, stream);
-    case 2: return launch_shape<4, 2, 1>(m, l, shape, grid_cap, stream);
-    case 3: return launch_shape<8, 2, 2>(m, l, shape, grid_cap, stream);
-    case 4: return launch_shape<16, 4, 4>(m, l, shape, grid_cap, stream);
-    case 5: return launch_shape<32, 4, 4>(m, l, shape, grid_cap, stream);
-    case 6: return launch_shape<64, 4, 4>(m, l, shape, grid_cap, stream);
-    default: return cudaErrorInvalidValue;
-  }
+  return launch_any(m, l, ChainMulti<ChainMember64>{nullptr, nullptr, 0, 0, 0, nullptr}, shape, grid_cap, stream);
+}
+
+cudaError_t launch_chain64_multi(const ChainMulti<ChainMember64>& mm, const ChainLaunch& l, int shape, int grid_cap,
+                                 cudaStream_t stream) {
+  if (mm.total <= 0 || mm.n_members <= 0) return cudaSuccess;
+  if (mm.total > INT32_MAX) return cudaErrorInvalidValue;
+  return launch_any(ChainMember64{}, l, mm, shape, grid_cap, stream);
 }
 
 }  // namespace hmat

@@ -228,6 +228,7 @@ struct ChainLaunch {
 // also the coupling and the downward transfers), B (downward transfers after the
 // tensor-core coupling), C (downward leaf step).
 struct ChainPlan {
+  std::vector<ChainItem> host;    // the items (host copy, for the batches' ticket lists)
   ChainItem* items = nullptr;     // device
   int32_t* expect = nullptr;      // device, 3 * n_nodes + levels + 1
   int32_t begin[3] = {0, 0, 0};
@@ -237,10 +238,47 @@ struct ChainPlan {
 };
 constexpr int kChainCtrHead = 4;
 
+// Many members in one launch (batches): member k's tickets are parts[k-1].ticket_end ..
+// parts[k].ticket_end - 1 of the launch (items item_begin .. item_begin + n_items - 1 of
+// members[k], each times its column tiles), waiting as `waits` says. One ticket counter
+// and one abort flag for the launch (ChainLaunch); members keep their own counters.
+struct ChainPart {
+  int64_t ticket_end;
+  int32_t item_begin;
+  int32_t n_items;
+  uint32_t waits;
+  int32_t pad;
+};
+// A ticket of a multi-member launch whose tickets follow an explicit order (list != null):
+// member index, item index in that member's item array, column tile, the waits.
+struct ChainTicket {
+  int32_t member;
+  int32_t item;
+  int32_t ct;
+  uint32_t waits;
+};
+template <typename M>
+struct ChainMulti {
+  const M* members;           // device; null: the launch has one member, the kernel parameter
+  const ChainPart* parts;     // device; per-member ticket ranges (when list is null)
+  int32_t n_members;
+  int32_t free_run;           // no member waits: a plain grid over the tickets
+  int64_t total;              // tickets of the launch
+  const ChainTicket* list;    // device, or null: the tickets in this order, one entry each
+};
+// A batch orders the tickets of its chain launches across members by stage (an item's
+// stage is below that of every item it waits for, so the order stays deadlock-free):
+// every member's leaf items, then every member's next level, and so on.
+int chain_stage(const ChainItem& it, int levels, int max_levels);
+
 cudaError_t launch_chain(const ChainMember& m, const ChainLaunch& l, int grid_cap, cudaStream_t stream);
+cudaError_t launch_chain_multi(const ChainMulti<ChainMember>& mm, const ChainLaunch& l, int grid_cap,
+                               cudaStream_t stream);
 // FP64 chain with column tiles of kColBN[shape] columns; chain64_prepare caches the
 // kernels' occupancy on the current device (at load, outside any graph capture).
 cudaError_t launch_chain64(const ChainMember64& m, const ChainLaunch& l, int shape, int grid_cap, cudaStream_t stream);
+cudaError_t launch_chain64_multi(const ChainMulti<ChainMember64>& mm, const ChainLaunch& l, int shape, int grid_cap,
+                                 cudaStream_t stream);
 cudaError_t chain64_prepare();
 // Sets the chain kernels' attributes on the current device (once) and returns the CTAs
 // that fit on it at once (16-byte X copies, 4-byte X copies; either may be null);
@@ -432,6 +470,50 @@ cudaError_t launch_split_f64(const TcProduct& p, const double* X, int64_t n_valu
 cudaError_t launch_split_f32(const TcProduct& p, const float* X, int64_t n_values, const int64_t* perm, int64_t q,
                              int n_t, int n_ct, unsigned long long* xmax, uint8_t* out, float* x32,
                              cudaStream_t stream);
+// The arguments of one tensor-core product (near field or coupling) of one evaluation.
+struct TcArgs {
+  TcLists tc;
+  const uint8_t* bsplit;            // right-hand operand tiles (k_split)
+  const unsigned long long* bmax;   // max |X| of the right-hand side (FP64 bits)
+  const int64_t* perm;              // near field: tree order -> caller order of Y's rows
+  void* Y;                          // near field: double or float (caller order); coupling: float (node rows)
+  int64_t q;
+  int n_t;
+  int n_ct;
+  int* status;
+  int y_f32;                        // near field: Y holds FP32 values
+};
+// One right-hand-side split of one evaluation (multi-member launches carry one per member).
+struct SplitJob {
+  TcLists tc;
+  const void* X;                    // FP64 or FP32 by the launch
+  const int64_t* perm;              // rows of X through perm (the near field's W), or null
+  int64_t q;
+  int n_t;
+  int n_ct;
+  const unsigned long long* xmax;
+  uint8_t* out;
+  float* x32;                       // FP32 tree-order copy of X, or null
+};
+// max |X| over n values of one member.
+struct AbsJob {
+  const void* X;
+  int64_t n;
+  unsigned long long* out;
+};
+// Blocks of one max |X| pass over n values.
+inline int64_t absmax_blocks(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b);
+}
+// Multi-member launches (batches); the tables and block prefixes are device arrays.
+cudaError_t launch_absmax_multi(bool f32, const AbsJob* jobs, const int64_t* block_end, int n, int64_t blocks,
+                                cudaStream_t stream);
+cudaError_t launch_split_multi(bool f32, const SplitJob* jobs, const int64_t* block_end, int n, int64_t blocks,
+                               cudaStream_t stream);
+cudaError_t launch_tc_multi(bool far, const TcArgs* args, const int64_t* block_end, int n, int64_t blocks,
+                            cudaStream_t stream);
+
 // Y (FP64, or FP32 when y_f32; rows through perm) = near field; or U (FP32, node rows) = coupling.
 cudaError_t launch_tc_near(const TcProduct& p, const uint8_t* bsplit, const unsigned long long* bmax,
                            const int64_t* perm, void* Y, bool y_f32, int64_t q, int n_t, int n_ct, int* status,

@@ -281,13 +281,14 @@ __device__ __forceinline__ double key_value(uint32_t k) { return (double)__uint_
 
 // max |X| over n values: 16-byte loads, four in flight per thread and iteration (few
 // registers, so that every SM holds enough loads in flight to stream at HBM rate)
+// (block bid of nb blocks working on X)
 template <typename T>
-__global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t n,
-                                                unsigned long long* __restrict__ out) {
+__device__ __forceinline__ void absmax_body(const T* __restrict__ X, int64_t n, unsigned long long* __restrict__ out,
+                                            int64_t bid, int64_t nb) {
   using Key = decltype(abs_key(T{}));
   constexpr int kPer = 16 / (int)sizeof(T);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = nb * blockDim.x;
+  const int64_t tid = bid * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n_vec = ((uintptr_t)X & 15u) == 0 ? n / kPer : 0;
   const uint4* V = reinterpret_cast<const uint4*>(X);
   Key m = 0;
@@ -322,6 +323,34 @@ __global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t
   if (threadIdx.x == 0 && mm > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(mm));
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t n,
+                                                unsigned long long* __restrict__ out) {
+  absmax_body<T>(X, n, out, blockIdx.x, gridDim.x);
+}
+
+// The member of a multi-member launch that block b belongs to: the first j with
+// block_end[j] > b; *first receives the block's index within the member.
+__device__ __forceinline__ int member_of(const int64_t* __restrict__ block_end, int n, int64_t b, int64_t* first) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (block_end[mid] > b) hi = mid;
+    else lo = mid + 1;
+  }
+  *first = lo > 0 ? block_end[lo - 1] : 0;
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_absmax_multi(const AbsJob* __restrict__ jobs,
+                                                      const int64_t* __restrict__ block_end, int n_jobs) {
+  int64_t first;
+  const int j = member_of(block_end, n_jobs, blockIdx.x, &first);
+  const AbsJob job = jobs[j];
+  absmax_body<T>(static_cast<const T*>(job.X), job.n, job.out, blockIdx.x - first, block_end[j] - first);
+}
+
 // One (source k-chunk, column tile): 64 rows of X x n_t columns -> B-operand tiles:
 // n_t rows (columns of X) x 64 values (rows of X), hi then lo. The near field's X is
 // W (FP64 or FP32, caller order, rows through perm); there the same values, rounded to
@@ -334,12 +363,17 @@ __global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t
 // RN32(v) is subnormal, and such values (|v| < 2^-126) scale to below half the smallest
 // FP16 subnormal (both sides give 0) for every k <= 100; larger k take the FP64 path.
 template <typename T>
-__global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__ X, const int64_t* __restrict__ perm,
-                                               int64_t q, int n_t, int n_ct,
-                                               const unsigned long long* __restrict__ xmax,
-                                               uint8_t* __restrict__ out, float* __restrict__ x32) {
-  const int64_t g = blockIdx.x / n_ct;
-  const int ct = blockIdx.x % n_ct;
+__device__ __forceinline__ void split_body(const SplitJob& j, int64_t b) {
+  const TcLists& tc = j.tc;
+  const T* __restrict__ X = static_cast<const T*>(j.X);
+  const int64_t* __restrict__ perm = j.perm;
+  const int64_t q = j.q;
+  const int n_t = j.n_t, n_ct = j.n_ct;
+  const unsigned long long* __restrict__ xmax = j.xmax;
+  uint8_t* __restrict__ out = j.out;
+  float* __restrict__ x32 = j.x32;
+  const int64_t g = b / n_ct;
+  const int ct = b % n_ct;
   const int node = tc.chunk_node[g], c = tc.chunk_c[g];
   const int n_j = tc.size[node];
   const int64_t row0 = tc.begin[node] + (int64_t)c * kTcK;
@@ -391,6 +425,30 @@ __global__ void __launch_bounds__(256) k_split(TcLists tc, const T* __restrict__
   for (int i = threadIdx.x; i < n_t * 16; i += blockDim.x) dst[i] = src[i];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_split(const SplitJob j) {
+  split_body<T>(j, blockIdx.x);
+}
+
+// one 32-bit word per thread: a job or argument block copied into shared memory
+template <typename S>
+__device__ __forceinline__ void copy_words(S* dst, const S* src) {
+  const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
+  for (int w = threadIdx.x; w < (int)(sizeof(S) / 4); w += blockDim.x) d32[w] = s32[w];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_split_multi(const SplitJob* __restrict__ jobs,
+                                                     const int64_t* __restrict__ block_end, int n_jobs) {
+  __shared__ SplitJob sj;
+  int64_t first;
+  const int jx = member_of(block_end, n_jobs, blockIdx.x, &first);
+  copy_words(&sj, jobs + jx);
+  __syncthreads();
+  split_body<T>(sj, blockIdx.x - first);
+}
+
 // ------------------------------------------------------------------ the tensor-core product kernel
 
 // coupling output when 2^-(k_a + k_x) is no normal FP32 number (out of line: see hmat_fp.cuh)
@@ -398,25 +456,24 @@ static __device__ __noinline__ float far_out_hw(float hi, float t, double sc) {
   return __double2float_rn(((double)hi + (double)t) * sc);
 }
 
-struct TcArgs {
-  TcLists tc;
-  const uint8_t* bsplit;            // right-hand operand tiles (k_split)
-  const unsigned long long* bmax;   // max |X| of the right-hand side (FP64 bits)
-  const int64_t* perm;              // near field: tree order -> caller order of Y's rows
-  void* Y;                          // near field: double or float (caller order); coupling: float (node rows)
-  int64_t q;
-  int n_t;
-  int n_ct;
-  int* status;
-  int y_f32;                        // near field: Y holds FP32 values
-};
+
 
 // Y_t = sum over the list of target t of A_ts X_s, for one (target, m-tile, column
 // tile). kFar = false: the near field (A = D, X = W, Y FP64 in caller order);
 // kFar = true: the coupling reduction (A = B, X = skeleton weights w, Y = the FP32
 // skeleton potentials u, written in node order).
-template <bool kFar>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
+// Many products in one launch (batches): block b works for the member j with
+// block_end[j - 1] <= b < block_end[j] (each member's blocks: its work items x column tiles).
+struct TcMulti {
+  const TcArgs* args;        // null: one product, the kernel parameter
+  const int64_t* block_end;
+  int n;
+};
+
+// kMulti: a launch over many products (the batch); single launches read their arguments
+// straight from the kernel parameters
+template <bool kFar, bool kMulti>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ TcArgs a0, const TcMulti mm) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], mfull_bar[2], mempty_bar[2], cfull_bar,
@@ -429,9 +486,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcArgs a) {
   __shared__ int64_t s_aoff[kStagedEntries], s_g0[kStagedEntries];
   __shared__ int s_nb;
 
+  __shared__ TcArgs sa;  // multi-member launches: this block's member
+  int64_t blk = blockIdx.x;
+  if constexpr (kMulti) {
+    int64_t first;
+    const int j = member_of(mm.block_end, mm.n, blk, &first);
+    copy_words(&sa, mm.args + j);
+    blk -= first;
+    __syncthreads();
+  }
+  const TcArgs& a = kMulti ? sa : a0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const TcTile work = a.tc.work[blockIdx.x / a.n_ct];
-  const int ct = blockIdx.x % a.n_ct;
+  const TcTile work = a.tc.work[blk / a.n_ct];
+  const int ct = blk % a.n_ct;
   const int tgt = work.node, mt = work.mt;
   const int64_t e0 = a.tc.ptr[tgt], e1 = a.tc.ptr[tgt + 1];
   const uint32_t b_bytes = 2u * (uint32_t)a.n_t * 128u;
@@ -749,13 +816,12 @@ cudaError_t launch_split(const TcProduct& p, const T* X, int64_t n_values, const
   if (n_t <= 0 || n_t > kMaxNt || n_t % 16 != 0) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(xmax, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = std::min<int64_t>((n_values + 255) / 256, 152 * 8);
-  k_absmax<T><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, stream>>>(X, n_values, xmax);
+  k_absmax<T><<<(unsigned)absmax_blocks(n_values), 256, 0, stream>>>(X, n_values, xmax);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int64_t grid = p.n_chunks * n_ct;
   if (grid == 0) return cudaSuccess;
   if (grid > 2147483647LL) return cudaErrorInvalidValue;
-  k_split<T><<<(unsigned)grid, 256, 0, stream>>>(p.dev, X, perm, q, n_t, n_ct, xmax, out, x32);
+  k_split<T><<<(unsigned)grid, 256, 0, stream>>>(SplitJob{p.dev, X, perm, q, n_t, n_ct, xmax, out, x32});
   return cudaGetLastError();
 }
 
@@ -767,14 +833,48 @@ cudaError_t launch_tc(const TcProduct& p, const uint8_t* bsplit, const unsigned 
   const int64_t grid = p.n_work * n_ct;
   if (grid > 2147483647LL) return cudaErrorInvalidValue;
   const int smem = kStages * kStageBytes + 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_tc<kFar>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_tc<kFar, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   TcArgs args{p.dev, bsplit, bmax, perm, Y, q, n_t, n_ct, status, y_f32 ? 1 : 0};
-  k_tc<kFar><<<(unsigned)grid, kTcThreads, smem, stream>>>(args);
+  k_tc<kFar, false><<<(unsigned)grid, kTcThreads, smem, stream>>>(args, TcMulti{nullptr, nullptr, 0});
   return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t launch_absmax_multi(bool f32, const AbsJob* jobs, const int64_t* block_end, int n, int64_t blocks,
+                                cudaStream_t stream) {
+  if (n <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 2147483647LL) return cudaErrorInvalidValue;
+  if (f32)
+    k_absmax_multi<float><<<(unsigned)blocks, 256, 0, stream>>>(jobs, block_end, n);
+  else
+    k_absmax_multi<double><<<(unsigned)blocks, 256, 0, stream>>>(jobs, block_end, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_multi(bool f32, const SplitJob* jobs, const int64_t* block_end, int n, int64_t blocks,
+                               cudaStream_t stream) {
+  if (n <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 2147483647LL) return cudaErrorInvalidValue;
+  if (f32)
+    k_split_multi<float><<<(unsigned)blocks, 256, 0, stream>>>(jobs, block_end, n);
+  else
+    k_split_multi<double><<<(unsigned)blocks, 256, 0, stream>>>(jobs, block_end, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_multi(bool far, const TcArgs* args, const int64_t* block_end, int n, int64_t blocks,
+                            cudaStream_t stream) {
+  if (n <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 2147483647LL) return cudaErrorInvalidValue;
+  const int smem = kStages * kStageBytes + 1024;
+  auto kern = far ? k_tc<true, true> : k_tc<false, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)blocks, kTcThreads, smem, stream>>>(TcArgs{}, TcMulti{args, block_end, n});
+  return cudaGetLastError();
+}
 
 cudaError_t launch_split_f64(const TcProduct& p, const double* X, int64_t n_values, const int64_t* perm, int64_t q,
                              int n_t, int n_ct, unsigned long long* xmax, uint8_t* out, float* x32,

@@ -162,6 +162,11 @@ def library() -> ctypes.CDLL:
         lib.hmat_batch_eval.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_void_p), _c_i64p, ctypes.c_void_p]
         lib.hmat_batch_free.argtypes = [ctypes.c_void_p]
+        lib.hmat_batch_info.argtypes = [ctypes.c_void_p, _c_i64p, ctypes.c_int]
+        lib.hmat_batch_schedule.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        lib.hmat_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.POINTER(ctypes.c_void_p), _c_i64p, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         lib.hmat_server_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                            ctypes.POINTER(HmatServerParams), ctypes.POINTER(ctypes.c_void_p)]
         lib.hmat_server_submit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
@@ -191,7 +196,7 @@ def library() -> ctypes.CDLL:
                      "hmat_server_create", "hmat_server_submit", "hmat_server_wait", "hmat_server_stats",
                      "hmat_server_free", "hmat_autotune", "hmat_selftest_timeout", "hmat_selftest_chain_timeout", "hmat_tune_apply",
                      "hmat_eval_typed", "hmat_eval_host_typed", "hmat_batch_eval_typed", "hmat_server_submit_typed",
-                     "hmat_server_matrix_stats",
+                     "hmat_server_matrix_stats", "hmat_batch_info", "hmat_batch_autotune", "hmat_batch_schedule",
                      "hmat_plan_create", "hmat_plan_build",
                      "hmat_plan_free", "hmat_selftest_conversions"):
             getattr(lib, name).restype = ctypes.c_int
@@ -473,6 +478,30 @@ def hmat_batch_eval_typed(batch: int, Ws, Ys, stream=None) -> None:
     y = (ctypes.c_void_p * n)(*[_ptr(x) for x in Ys])
     q = (ctypes.c_int64 * n)(*[int(x.shape[1]) for x in Ws])
     _check(library().hmat_batch_eval_typed(batch, w, y, q, dt, _stream(stream)), "hmat_batch_eval_typed")
+
+
+def hmat_batch_info(batch: int) -> dict:
+    out = (ctypes.c_int64 * 5)()
+    _check(library().hmat_batch_info(batch, out, 5), "hmat_batch_info")
+    return {"members": int(out[0]), "kernels": int(out[1]), "device_bytes": int(out[2]), "chain_grid": int(out[3]),
+            "branched": int(out[4])}
+
+
+def hmat_batch_schedule(batch: int, branched: int = 0, chain_grid: int = 0) -> None:
+    _check(library().hmat_batch_schedule(batch, int(branched), int(chain_grid)), "hmat_batch_schedule")
+
+
+def hmat_batch_autotune(batch: int, Ws, Ys, stream=None) -> dict:
+    """Time whole replays of the batch with several chain grids and keep the fastest (bitwise neutral)."""
+    n = len(Ws)
+    dt = _dtype_of(Ws[0])
+    w = (ctypes.c_void_p * n)(*[_ptr(x) for x in Ws])
+    y = (ctypes.c_void_p * n)(*[_ptr(x) for x in Ys])
+    q = (ctypes.c_int64 * n)(*[int(x.shape[1]) for x in Ws])
+    d, t = ctypes.c_double(), ctypes.c_double()
+    _check(library().hmat_batch_autotune(batch, w, y, q, dt, _stream(stream), ctypes.byref(d), ctypes.byref(t)),
+           "hmat_batch_autotune")
+    return {"default_ms": float(d.value), "tuned_ms": float(t.value), **hmat_batch_info(batch)}
 
 
 def hmat_batch_free(batch: int) -> None:

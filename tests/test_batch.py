@@ -1,7 +1,8 @@
 """Batched evaluation (hmat_batch_*): many HMatrices of uneven size, rank and q in
-one CUDA-graph launch. Every member's result must be bitwise the one it gets when
-evaluated alone (the same kernels in the same order, no atomics) and match the FP64
-oracle within the mode's tolerance."""
+one CUDA-graph launch in which every step is one launch over all members. Every
+member's result must be bitwise the one it gets when evaluated alone (the same tiles
+summed in the same order, no atomics) and match the FP64 oracle within the mode's
+tolerance; the mixed-mode graph holds about ten kernels however many members."""
 import numpy as np
 import pytest
 
@@ -18,6 +19,7 @@ MEMBERS = [
     ("h2_imq3d_n262144", 1500, (("leaf_size", 128),)),
     ("h2_imq3d_n262144", 5000, (("leaf_size", 256),)),
     ("h2_gmm8d_n65536", 1100, ()),
+    ("hss_uniform3d_n2048", 1500, (("tol", 0.0), ("max_rank", 10 ** 6))),   # coupling on the tensor cores
 ]
 
 
@@ -36,7 +38,7 @@ def loaded():
 def test_batch_equals_members_alone(loaded, mode, tol):
     # the second member appears twice, with different right-hand sides
     members = loaded + [loaded[1]]
-    qs = [5, 64, 1, 130, 17, 33]
+    qs = [5, 64, 1, 130, 17, 24, 33]
     handles = [h for _, _, h in members]
     Ws = [torch.from_numpy(rhs(w.n, q, 700 + i)).cuda() for i, ((w, _, _), q) in enumerate(zip(members, qs))]
     Ys = [torch.full_like(W, float("nan")) for W in Ws]
@@ -48,6 +50,10 @@ def test_batch_equals_members_alone(loaded, mode, tol):
                     W.mul_(-0.5)
             hp.hmat_batch_eval(b, Ws, Ys)
             torch.cuda.synchronize()
+            info = hp.hmat_batch_info(b)
+            assert info["members"] == len(members)
+            if mode == hp.HMAT_MODE_MIXED:
+                assert 0 < info["kernels"] <= 10, info
             for (w, H, h), W, Y in zip(members, Ws, Ys):
                 alone = torch.empty_like(W)
                 hp.hmat_eval(h, W, alone, W.shape[1], mode)
@@ -56,6 +62,23 @@ def test_batch_equals_members_alone(loaded, mode, tol):
                 Yref = hm.evaluate(H, W.cpu().numpy())
                 err = np.linalg.norm(Y.cpu().numpy() - Yref) / np.linalg.norm(Yref)
                 assert err <= tol, err
+        assert all(hp.hmat_status_poll(h) == hp.HMAT_OK for h in handles)
+        # the other schedules (one branch per member; a capped chain grid) and the tuner's
+        # choice give bitwise the same results
+        ref = [Y.clone() for Y in Ys]
+        for branched, grid in ((1, 0), (0, 7)):
+            hp.hmat_batch_schedule(b, branched, grid)
+            for Y in Ys:
+                Y.fill_(float("nan"))
+            hp.hmat_batch_eval(b, Ws, Ys)
+            torch.cuda.synchronize()
+            assert hp.hmat_batch_info(b)["branched"] == branched
+            assert all(torch.equal(Y, R) for Y, R in zip(Ys, ref)), (branched, grid)
+        rep = hp.hmat_batch_autotune(b, Ws, Ys)
+        assert 0 < rep["tuned_ms"] <= rep["default_ms"]
+        hp.hmat_batch_eval(b, Ws, Ys)
+        torch.cuda.synchronize()
+        assert all(torch.equal(Y, R) for Y, R in zip(Ys, ref))
         assert all(hp.hmat_status_poll(h) == hp.HMAT_OK for h in handles)
     finally:
         hp.hmat_batch_free(b)
