@@ -303,7 +303,13 @@ hmat_status build_tc(Handle* h, const TcSpec& sp, TcProduct* out) {
     for (int64_t e = sp.ptr[i]; e < sp.ptr[i + 1]; ++e) cost += kc[sp.idx[e]];
     for (int32_t m = 0; m < n_mt[i]; ++m) work.push_back({cost, TcTile{(int32_t)i, m}});
   }
-  std::stable_sort(work.begin(), work.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+  // longest lists first by half-octave class of their length (no long list in the last
+  // wave), tree order within a class: targets that run side by side are neighbours and
+  // share most of their sources, whose right-hand-side tiles then come from L2
+  // (measured: N=262144 inverse multiquadric near field 4.83 -> 4.57 ms; strict
+  // longest-first is needed where list lengths spread, the N=65536 mixture's 98..512)
+  auto cls = [](int64_t c) { return c > 0 ? (int)std::floor(2.0 * std::log2((double)c)) : 0; };
+  std::stable_sort(work.begin(), work.end(), [&](const auto& x, const auto& y) { return cls(x.first) > cls(y.first); });
   std::vector<TcTile> work_list;
   for (auto& w : work) work_list.push_back(w.second);
   out->n_work = (int64_t)work_list.size();
