@@ -585,6 +585,33 @@ hmat_status hmat_selftest_timeout(hmat_t h, int64_t limit_ns, void* stream);
  */
 hmat_status hmat_selftest_chain_timeout(hmat_t h, int64_t q, int mode, int64_t limit_ns, void* stream);
 
+/*
+ * hmat_selftest_row_id - runs the GPU row interpolative decomposition of the inspector
+ * (HMAT_BUILD_ID_GPU; Section 3.1, low-rank approximation) on a given matrix instead
+ * of one formed from points, to check it against a reference (no counterpart in the
+ * paper). M: host, n_rows x n_cols row-major, the rows are the candidates. The ID is
+ * the column-pivoted QR of M^T stopped at the first |R_kk| <= tol |R_11| or at max_rank:
+ * *rank = k, piv[0..n_rows-1] the row order after the pivoting (piv[0..k-1] the
+ * skeleton), T (k x (n_rows - k), row-major) = R_11^{-1} R_12, so that row piv[k + c]
+ * of M ~= sum_i T[i][c] M[piv[i]]. Synchronous; n_rows <= 8192 and n_rows x n_cols <=
+ * 2^26 (else HMAT_EINVAL).
+ */
+hmat_status hmat_selftest_row_id(const double* M, int64_t n_rows, int64_t n_cols, double tol, int32_t max_rank,
+                                 int32_t* piv, int32_t* rank, double* T);
+
+/*
+ * hmat_selftest_device_check - failure-detection self-test of the persistent far
+ * chain's index checks (no counterpart in the paper): every item, tile and node index
+ * a chain launch takes from device memory is checked against the size of the array it
+ * indexes before anything is read through it, and an inconsistent one latches
+ * HMAT_EDEVICE in the status word and stops the launch. This enqueues one chain launch
+ * of `mode` for q columns whose only ticket names the item just past the handle's item
+ * array; the check catches it before any read, so the next hmat_status_poll returns
+ * HMAT_EDEVICE and the context stays usable. HMAT_EUNSUPPORTED when the handle has no
+ * copy for `mode`, HMAT_EINVAL when it has no far field.
+ */
+hmat_status hmat_selftest_device_check(hmat_t h, int64_t q, int mode, void* stream);
+
 /* hmat_info - sizes of the loaded HMatrix: out[0] = n_points, out[1] = levels,
  * out[2] = near entries, out[3] = far entries, out[4] = near values (stored, or
  * evaluated on the fly under HMAT_BUILD_NEAR_OTF, see out[10]),

@@ -12,6 +12,6 @@ from .hmat import (  # noqa: F401
     hmat_status_poll, hmat_info, hmat_free, hmat_strerror, library, exported_symbols, hmat_eval_host,
     hmat_profile, hmat_phase_times, hmat_measure_fp64_peak, PHASES, hmat_batch_create, hmat_batch_eval,
     hmat_batch_free, hmat_server_create, hmat_server_submit, hmat_server_wait, hmat_server_stats,
-    hmat_server_free, hmat_autotune, hmat_tune_apply, hmat_selftest_timeout, hmat_selftest_chain_timeout,
+    hmat_server_free, hmat_autotune, hmat_tune_apply, hmat_selftest_timeout, hmat_selftest_chain_timeout, hmat_selftest_row_id, hmat_selftest_device_check,
     hmat_selftest_conversions, hmat_plan_create, hmat_plan_build, hmat_plan_free,
 )

@@ -929,6 +929,7 @@ hmat_status load_impl(const hmat_desc* d, const DeviceBlockSource* src, int flag
   if ((e = upload(&h->tasks, tasks, &h->device_bytes)) != cudaSuccess) return fail(e);
   if ((e = upload(&h->entries, entries, &h->device_bytes)) != cudaSuccess) return fail(e);
   if ((e = upload(&h->tiles, tiles, &h->device_bytes)) != cudaSuccess) return fail(e);
+  h->n_tiles = (int64_t)tiles.size();
   std::vector<int> zero(1, 0);
   if ((e = upload(&h->status, zero, &h->device_bytes)) != cudaSuccess) return fail(e);
   if (flags & HMAT_LOAD_MIXED) {

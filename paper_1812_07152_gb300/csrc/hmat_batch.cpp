@@ -284,6 +284,7 @@ hmat_status capture_mixed(hmat_batch* b, const void* const* W, void* const* Y, c
     l.ticket = tickets + k;
     l.abort_flag = tickets + kTickets - 1;
     l.limit_ns = kChainWaitNs;
+    l.status = live.empty() ? nullptr : b->handles[live[0]]->status;
     return l;
   };
   const int nW = (int)mt.absW.size(), nS = (int)mt.absS.size();
@@ -434,6 +435,7 @@ hmat_status capture_fp64(hmat_batch* b, const void* const* W, void* const* Y, co
     l.ticket = tickets + g;
     l.abort_flag = tickets + kTickets - 1;
     l.limit_ns = kChainWaitNs;
+    l.status = b->handles[kv.second[0]]->status;
     const ChainMulti<ChainMember64> mm{(const ChainMember64*)(tb + ft.off[3 * g]), nullptr,
                                        (int32_t)kv.second.size(), 0, ft.off[3 * g + 2],
                                        (const ChainTicket*)(tb + ft.off[3 * g + 1])};

@@ -119,6 +119,11 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__
         }
       }
       if constexpr (multi) {
+        if (threadIdx.x == 0 && go && (mi < 0 || mi >= mm.n_members)) {  // an inconsistent ticket list
+          atomicCAS(l.status, 0, (int)HMAT_EDEVICE);
+          atomicExch(l.abort_flag, 1);
+          go = 0;
+        }
         go = __shfl_sync(0xffffffffu, go, 0);
         mi = __shfl_sync(0xffffffffu, mi, 0);
         if (go && mi != cur) {  // one 32-bit word per lane
@@ -134,10 +139,11 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__
         uint32_t waits = l.waits;
         int32_t ib = l.item_begin;
         const ChainMember& mt = multi ? sm : m1;
+        int64_t ii;
         if (multi && mm.list) {
           const ChainTicket ck = mm.list[t];
           waits = ck.waits;
-          s_it = mt.items[ck.item];
+          ii = ck.item;
           s_q0 = (int64_t)ck.ct * mt.bn;
         } else {
           if constexpr (multi) {
@@ -145,12 +151,18 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__
             waits = mm.parts[mi].waits;
             ib = mm.parts[mi].item_begin;
           }
-          s_it = mt.items[ib + local / mt.n_ct];
+          ii = ib + local / mt.n_ct;
           s_q0 = (local % mt.n_ct) * mt.bn;
+        }
+        // every index taken from device data is checked before it is used
+        go = chain_item_ok(mt.items, ii, mt.n_items, mt.n_tiles, mt.sync.n_nodes, &s_it) ? 1 : 0;
+        if (!go) {
+          atomicCAS(mt.sync.status, 0, (int)HMAT_EDEVICE);
+          atomicExch(l.abort_flag, 1);
         }
         // the acquire loads of the waits order this CTA's operand reads (after the barrier
         // below) after the producers' writes
-        if (!free_run) {
+        if (go && !free_run) {
           ChainLaunch lw = l;
           lw.waits = waits;
           go = chain_deps(mt.sync, s_it, lw) ? 1 : 0;

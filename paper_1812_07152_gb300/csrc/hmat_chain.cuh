@@ -94,6 +94,18 @@ static __device__ bool chain_deps(const ChainSync& m, const ChainItem& it, const
   return true;
 }
 
+// Thread 0: item ii of a member's list, checked against the sizes it indexes (the item
+// array, the tile array, the tree's nodes) before any of them is read through it; false
+// (nothing read) for an inconsistent index.
+static __device__ __forceinline__ bool chain_item_ok(const ChainItem* items, int64_t ii, int32_t n_items,
+                                                     int32_t n_tiles, int32_t n_nodes, ChainItem* out) {
+  if (ii < 0 || ii >= n_items) return false;
+  const ChainItem it = items[ii];
+  if (it.tile < 0 || it.tile >= n_tiles || it.node < 0 || it.node >= n_nodes || it.kind > CK_LEAF) return false;
+  *out = it;
+  return true;
+}
+
 // Thread 0, after the CTA barrier that ends the item's tile: count it complete.
 static __device__ __forceinline__ void chain_done(const ChainSync& m, const ChainItem& it) {
   if (it.kind == CK_LEAF) return;  // nothing waits for a leaf item

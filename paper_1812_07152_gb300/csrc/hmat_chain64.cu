@@ -65,23 +65,38 @@ k_chain64(const __grid_constant__ ChainMember64 m1, const __grid_constant__ Chai
           waits = mm.parts[mi].waits;
           ib = mm.parts[mi].item_begin;
         }
-        if (multi && mi != cur) {  // one 32-bit word at a time: few registers live in the copy
+        if (multi && (mi < 0 || mi >= mm.n_members)) {  // an inconsistent ticket list
+          atomicCAS(l.status, 0, (int)HMAT_EDEVICE);
+          atomicExch(l.abort_flag, 1);
+          go = 0;
+        }
+        if (go && multi && mi != cur) {  // one 32-bit word at a time: few registers live in the copy
           const uint32_t* src = reinterpret_cast<const uint32_t*>(mm.members + mi);
           uint32_t* dst = reinterpret_cast<uint32_t*>(&sm);
           for (int w = 0; w < (int)(sizeof(ChainMember64) / 4); ++w) dst[w] = src[w];
           cur = mi;
         }
-        const ChainMember64& mt = multi ? sm : m1;
-        if (item >= 0) {
-          s_it = mt.items[item];
-          s_q0 = (int64_t)ct * BN;
-        } else {
-          s_it = mt.items[ib + local / mt.n_ct];
-          s_q0 = (local % mt.n_ct) * BN;
+        if (go) {
+          const ChainMember64& mt = multi ? sm : m1;
+          int64_t ii;
+          if (item >= 0) {
+            ii = item;
+            s_q0 = (int64_t)ct * BN;
+          } else {
+            ii = ib + local / mt.n_ct;
+            s_q0 = (local % mt.n_ct) * BN;
+          }
+          // every index taken from device data is checked before it is used
+          go = chain_item_ok(mt.items, ii, mt.n_items, mt.n_tiles, mt.sync.n_nodes, &s_it) ? 1 : 0;
+          if (!go) {
+            atomicCAS(mt.sync.status, 0, (int)HMAT_EDEVICE);
+            atomicExch(l.abort_flag, 1);
+          } else {
+            ChainLaunch lw = l;
+            lw.waits = waits;
+            go = chain_deps(mt.sync, s_it, lw) ? 1 : 0;
+          }
         }
-        ChainLaunch lw = l;
-        lw.waits = waits;
-        go = chain_deps(mt.sync, s_it, lw) ? 1 : 0;
       }
       s_go = go;
     }

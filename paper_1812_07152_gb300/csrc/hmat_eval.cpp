@@ -231,6 +231,8 @@ ChainMember chain_member(const Handle& h, const EvalContext* c, void* Y, bool y_
                      m.n_ct, 0};
   m.xv = q % 4 == 0 ? 1 : 0;
   m.y_f32 = y_f32 ? 1 : 0;
+  m.n_items = (int32_t)h.chain.host.size();
+  m.n_tiles = (int32_t)h.n_tiles;
   return m;
 }
 
@@ -243,6 +245,7 @@ ChainLaunch chain_launch(const Handle& h, const EvalContext* c, int part, int32_
   l.waits = h.chain.waits[part];
   l.extra = extra;
   l.limit_ns = limit_ns;
+  l.status = h.status;
   return l;
 }
 
@@ -268,6 +271,8 @@ ChainMember64 chain_member64(const Handle& h, const EvalContext* c, const double
   m.n_ct = (int32_t)((q + bn - 1) / bn);
   m.sync = ChainSync{h.chain64.expect, c->chain_ctr + kChainCtrHead, h.status, (int32_t)h.n_nodes, m.first_leaf,
                      m.n_ct, 0};
+  m.n_items = (int32_t)h.chain64.host.size();
+  m.n_tiles = (int32_t)h.n_tiles;
   return m;
 }
 
@@ -280,6 +285,7 @@ ChainLaunch chain_launch64(const Handle& h, const EvalContext* c, int32_t extra,
   l.waits = h.chain64.waits[0];
   l.extra = extra;
   l.limit_ns = limit_ns;
+  l.status = h.status;
   return l;
 }
 
@@ -514,6 +520,41 @@ extern "C" hmat_status hmat_selftest_chain_timeout(hmat_t h, int64_t q, int mode
                                     chain_launch(*h, h->ctx, 0, 1, (uint64_t)limit_ns), 0, s));
   return cuda_status(launch_chain64(chain_member64(*h, h->ctx, nullptr, nullptr, q),
                                     chain_launch64(*h, h->ctx, 1, (uint64_t)limit_ns), fp64_default_shape(q), 0, s));
+}
+
+extern "C" hmat_status hmat_selftest_device_check(hmat_t h, int64_t q, int mode, void* stream) {
+  if (!h || q <= 0) return HMAT_EINVAL;
+  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_MIXED) return HMAT_EUNSUPPORTED;
+  if ((mode == HMAT_MODE_MIXED && !h->has_mixed) || (mode == HMAT_MODE_FP64 && !h->has_fp64))
+    return HMAT_EUNSUPPORTED;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HMAT_ECUDA;
+  if (dev != h->device) return HMAT_EINVAL;
+  const ChainPlan& plan = mode == HMAT_MODE_MIXED ? h->chain : h->chain64;
+  if (plan.host.empty()) return HMAT_EINVAL;  // no far field: no chain to check
+  hmat_status st = ctx_reserve(*h, h->ctx, q, mode);
+  if (st != HMAT_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(h->ctx->chain_ctr, 0, (size_t)plan.n_ctr * 4, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  // one ticket whose item index lies just past the item array: the launch's own index
+  // check must catch it before any read
+  if (mode == HMAT_MODE_MIXED) {
+    ChainLaunch l = chain_launch(*h, h->ctx, 0, 0, kChainWaitNs);
+    l.item_begin = (int32_t)plan.host.size();
+    l.n_items = 1;
+    ChainMember m = chain_member(*h, h->ctx, nullptr, false, q);
+    m.n_ct = 1;
+    m.sync.n_ct = 1;
+    return cuda_status(launch_chain(m, l, 1, s));
+  }
+  ChainLaunch l = chain_launch64(*h, h->ctx, 0, kChainWaitNs);
+  l.item_begin = (int32_t)plan.host.size();
+  l.n_items = 1;
+  ChainMember64 m = chain_member64(*h, h->ctx, nullptr, nullptr, q);
+  m.n_ct = 1;
+  m.sync.n_ct = 1;
+  return cuda_status(launch_chain64(m, l, fp64_default_shape(q), 1, s));
 }
 
 extern "C" hmat_status hmat_profile(hmat_t h, int enable) {

@@ -8,6 +8,8 @@
 // downdating with recomputation on cancellation); only the order of the sums differs.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "hmat_internal.h"
 
 namespace hmat {
@@ -64,12 +66,14 @@ __global__ void __launch_bounds__(kIdThreads) k_row_id(const IdJob* __restrict__
     if (tid == 0) rank_out[blockIdx.x] = 0;
     return;
   }
-  const int64_t* rows = ids + job.rows_off;
-  const int64_t* cols = ids + job.cols_off;
-  // A[j * m + i] = k(x_{cols[i]}, x_{rows[j]})
-  for (int64_t e = tid; e < n * m; e += kIdThreads) {
-    const int64_t j = e / m, i = e % m;
-    A[e] = kernel_value_d(kernel, param, pts + cols[i] * d, pts + rows[j] * d, d);
+  if (pts) {  // else A is given (hmat_selftest_row_id)
+    const int64_t* rows = ids + job.rows_off;
+    const int64_t* cols = ids + job.cols_off;
+    // A[j * m + i] = k(x_{cols[i]}, x_{rows[j]})
+    for (int64_t e = tid; e < n * m; e += kIdThreads) {
+      const int64_t j = e / m, i = e % m;
+      A[e] = kernel_value_d(kernel, param, pts + cols[i] * d, pts + rows[j] * d, d);
+    }
   }
   for (int64_t j = tid; j < n; j += kIdThreads) piv[j] = (int32_t)j;
   __syncthreads();
@@ -197,3 +201,45 @@ cudaError_t launch_row_id(const IdJob* jobs, int64_t n_jobs, int64_t max_rows, c
 }
 
 }  // namespace hmat
+
+using namespace hmat;
+
+extern "C" hmat_status hmat_selftest_row_id(const double* M, int64_t n_rows, int64_t n_cols, double tol,
+                                            int32_t max_rank, int32_t* piv, int32_t* rank, double* T) {
+  if (!M || !piv || !rank || !T || n_rows <= 0 || n_cols <= 0 || max_rank < 1 || !(tol >= 0.0)) return HMAT_EINVAL;
+  if (n_rows > 8192 || n_rows * n_cols > ((int64_t)1 << 26)) return HMAT_EINVAL;
+  const int64_t vals = n_rows * n_cols;
+  double* dA = nullptr;
+  int32_t* dp = nullptr;
+  int32_t* dr = nullptr;
+  IdJob* dj = nullptr;
+  const IdJob job{0, 0, 0, 0, (int32_t)n_rows, (int32_t)n_cols};
+  cudaError_t e = cudaMalloc((void**)&dA, (size_t)vals * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dp, (size_t)n_rows * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dr, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dj, sizeof(IdJob));
+  // column j of the column-major |C| x |R| operand is row j of M
+  if (e == cudaSuccess) e = cudaMemcpy(dA, M, (size_t)vals * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dj, &job, sizeof(IdJob), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = launch_row_id(dj, 1, n_rows, nullptr, 0, nullptr, 0, 0.0, tol, max_rank, dA, dp, dr, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int32_t k = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&k, dr, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(piv, dp, (size_t)n_rows * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  std::vector<double> A;
+  if (e == cudaSuccess) {
+    A.resize((size_t)vals);
+    e = cudaMemcpy(A.data(), dA, (size_t)vals * sizeof(double), cudaMemcpyDeviceToHost);
+  }
+  cudaFree(dA);
+  cudaFree(dp);
+  cudaFree(dr);
+  cudaFree(dj);
+  if (e != cudaSuccess) return cuda_status(e);
+  *rank = k;
+  // T (k x (n_rows - k), row-major): column c sits in rows 0..k-1 of column k + c
+  for (int64_t i = 0; i < k; ++i)
+    for (int64_t c = 0; c < n_rows - k; ++c) T[i * (n_rows - k) + c] = A[(size_t)((k + c) * n_cols + i)];
+  return HMAT_OK;
+}

@@ -188,6 +188,8 @@ struct ChainMember {
   int32_t first_leaf;
   int32_t xv;                 // q % 4 == 0: X rows copied 16 bytes at a time
   int32_t y_f32;              // Y holds FP32 values
+  int32_t n_items;            // size of items (every item index is checked against it)
+  int32_t n_tiles;            // size of tiles
   int32_t pad;
 };
 
@@ -210,6 +212,8 @@ struct ChainMember64 {
   int64_t q;
   int32_t n_ct;
   int32_t first_leaf;
+  int32_t n_items;            // size of items (every item index is checked against it)
+  int32_t n_tiles;            // size of tiles
 };
 
 // One persistent launch: tickets item_begin .. item_begin + n_items - 1 of member m,
@@ -222,6 +226,7 @@ struct ChainLaunch {
   uint32_t waits;             // kWait* mask
   int32_t extra;              // self-test: added to every requirement, so that every wait runs out
   uint64_t limit_ns;          // a wait gives up after this long and latches HMAT_ETIMEOUT
+  int* status;                // status word for an inconsistent ticket list (no member to report to)
 };
 
 // Ranges of a handle's chain items per launch: A (upward pass; with the FP32 coupling
@@ -338,6 +343,7 @@ struct Handle {
   int64_t n_far = 0;
   int64_t near_values = 0, basis_values = 0, coupling_values = 0;
   int64_t sum_rank = 0;
+  int64_t n_tiles = 0;            // entries of the tile array (both modes' launches and chains)
 
   std::vector<int64_t> begin, size, skel_off, perm_host, near_ptr, far_ptr;
   std::vector<int32_t> rank, near_idx, far_idx;

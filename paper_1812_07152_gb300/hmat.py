@@ -181,6 +181,10 @@ def library() -> ctypes.CDLL:
                                       ctypes.POINTER(HmatTuneReport)]
         lib.hmat_selftest_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         lib.hmat_tune_apply.argtypes = [ctypes.c_void_p, ctypes.POINTER(HmatTuneReport)]
+        lib.hmat_selftest_device_check.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+        lib.hmat_selftest_row_id.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_double, ctypes.c_int32, _c_i32p, _c_i32p,
+                                             ctypes.POINTER(ctypes.c_double)]
         lib.hmat_selftest_chain_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
                                                     ctypes.c_void_p]
         lib.hmat_selftest_conversions.argtypes = [ctypes.c_int64, ctypes.c_uint64, _c_i64p]
@@ -194,7 +198,7 @@ def library() -> ctypes.CDLL:
                      "hmat_info", "hmat_free", "hmat_eval_host", "hmat_profile", "hmat_phase_times",
                      "hmat_measure_fp64_peak", "hmat_batch_create", "hmat_batch_eval", "hmat_batch_free",
                      "hmat_server_create", "hmat_server_submit", "hmat_server_wait", "hmat_server_stats",
-                     "hmat_server_free", "hmat_autotune", "hmat_selftest_timeout", "hmat_selftest_chain_timeout", "hmat_tune_apply",
+                     "hmat_server_free", "hmat_autotune", "hmat_selftest_timeout", "hmat_selftest_chain_timeout", "hmat_tune_apply", "hmat_selftest_row_id", "hmat_selftest_device_check",
                      "hmat_eval_typed", "hmat_eval_host_typed", "hmat_batch_eval_typed", "hmat_server_submit_typed",
                      "hmat_server_matrix_stats", "hmat_batch_info", "hmat_batch_autotune", "hmat_batch_schedule",
                      "hmat_plan_create", "hmat_plan_build",
@@ -432,6 +436,27 @@ def hmat_selftest_chain_timeout(handle: int, q: int, limit_ns: int, mode: int = 
     after limit_ns and latches HMAT_ETIMEOUT in the handle's status word."""
     _check(library().hmat_selftest_chain_timeout(handle, int(q), int(mode), int(limit_ns), _stream(stream)),
            "hmat_selftest_chain_timeout")
+
+
+def hmat_selftest_device_check(handle: int, q: int, mode: int = HMAT_MODE_FP64, stream=None) -> None:
+    """Enqueue a far-chain launch whose only ticket names an item past the item array: its index check latches
+    HMAT_EDEVICE in the handle's status word before anything is read."""
+    _check(library().hmat_selftest_device_check(handle, int(q), int(mode), _stream(stream)),
+           "hmat_selftest_device_check")
+
+
+def hmat_selftest_row_id(M: np.ndarray, tol: float, max_rank: int):
+    """The GPU row ID of the inspector on the rows of M (host, float64): (rank, pivot order, T)."""
+    A = np.ascontiguousarray(M, dtype=np.float64)
+    n, m = A.shape
+    piv = np.zeros(n, dtype=np.int32)
+    rank = ctypes.c_int32()
+    T = np.zeros(n * n, dtype=np.float64)
+    _check(library().hmat_selftest_row_id(A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n, m, float(tol),
+                                          int(max_rank), piv.ctypes.data_as(_c_i32p), ctypes.byref(rank),
+                                          T.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "hmat_selftest_row_id")
+    k = int(rank.value)
+    return k, piv, T[: k * (n - k)].reshape(k, n - k)
 
 
 def hmat_selftest_conversions(n: int, seed: int = 0) -> dict:

@@ -47,3 +47,27 @@ def test_selftest_rejects_bad_limits():
             assert ei.value.status == hp.HMAT_EINVAL
     finally:
         hp.hmat_free(h)
+
+
+@pytest.mark.parametrize("mode", [hp.HMAT_MODE_FP64, hp.HMAT_MODE_MIXED])
+def test_chain_index_check_latches_edevice_and_context_survives(mode):
+    """A far-chain launch whose only ticket names an item past the item array: the chain's own
+    index check catches it before any read, latches HMAT_EDEVICE, and the next evaluation on
+    the same context still matches the oracle."""
+    w, H, _ = oracle_case("h2_gmm8d_n65536", 4096, 8)
+    h = hp.hmat_load(**desc_from_oracle(H), flags=hp.HMAT_LOAD_MIXED)
+    try:
+        assert hp.hmat_status_poll(h) == hp.HMAT_OK
+        hp.hmat_selftest_device_check(h, 8, mode)
+        assert hp.hmat_status_poll(h) == hp.HMAT_EDEVICE
+        assert hp.hmat_status_poll(h) == hp.HMAT_OK
+        W = rhs(w.n, 8, 21)
+        Yref = hm.evaluate(H, W)
+        Wd = torch.from_numpy(W).cuda()
+        Yd = torch.empty_like(Wd)
+        hp.hmat_eval(h, Wd, Yd, 8, mode)
+        assert hp.hmat_status_poll(h) == hp.HMAT_OK
+        tol = 1e-12 if mode == hp.HMAT_MODE_FP64 else 1e-6
+        assert np.linalg.norm(Yd.cpu().numpy() - Yref) <= tol * np.linalg.norm(Yref)
+    finally:
+        hp.hmat_free(h)

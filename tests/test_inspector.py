@@ -205,3 +205,33 @@ def test_gpu_row_ids_full_rank_is_exact():
         assert hm.overall_error(_eval(h, W), KW) <= 1e-13
     finally:
         hp.hmat_free(h)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n_rows,n_cols,tol,rank_expected", [(40, 60, 10 ** -7.5, 8), (64, 200, 10 ** -11.5, 12),
+                                                             (30, 30, 0.0, 30)])
+def test_gpu_row_id_returns_the_oracle_skeleton_on_a_separated_spectrum(n_rows, n_cols, tol, rank_expected):
+    """A matrix whose rows have geometrically decaying scales (a factor 10 apart, in a
+    shuffled order) over a generic Gaussian matrix has unambiguous pivots: each step of the
+    column-pivoted QR picks the row of the next scale. The GPU row ID must return exactly
+    the oracle's skeleton (in pivot order) and rank, and its interpolation matrix P within
+    1e-9 of the oracle's."""
+    rng = np.random.default_rng(n_rows)
+    order = rng.permutation(n_rows)
+    scales = 10.0 ** -np.arange(n_rows, dtype=np.float64)
+    M = (scales[np.argsort(order)][:, None]) * rng.standard_normal((n_rows, n_cols))
+    skel, P, diag = hm.row_id(M, tol, 10 ** 6)
+    assert len(skel) == rank_expected
+    # the pivots follow the scales: the oracle's skeleton is the rows in decreasing scale
+    assert list(skel) == list(np.argsort(-scales[np.argsort(order)])[:rank_expected])
+    k, piv, T = hp.hmat_selftest_row_id(M, tol, 10 ** 6)
+    assert k == rank_expected
+    assert list(piv[:k]) == list(skel)
+    Pg = np.zeros((n_rows, k))
+    Pg[piv[:k], :] = np.eye(k)
+    Pg[piv[k:], :] = T.T
+    assert np.abs(Pg - P).max() <= 1e-9 * max(1.0, np.abs(P).max())
+    # the rank cap stops both at the same pivot
+    skel_c, _, _ = hm.row_id(M, tol, 5)
+    kc, piv_c, _ = hp.hmat_selftest_row_id(M, tol, 5)
+    assert kc == len(skel_c) == min(5, rank_expected) and list(piv_c[:kc]) == list(skel_c)
