@@ -469,13 +469,16 @@ hmat_status hmat_tune_apply(hmat_t h, const hmat_tune_report* choice);
  * hmat_batch_info - out[0] members, out[1] kernel launches in the graph of the last
  * argument set (0 before the first call), out[2] device bytes held by the batch, out[3]
  * the CTAs of its chain launches (0: every resident CTA), out[4] 1 when the batch runs
- * the branched schedule.
+ * the branched schedule, out[5] 1 when its mixed members run at their default
+ * tensor-core column widths instead of their own tuned ones.
  * hmat_batch_autotune - time whole replays of the batch for these arguments with the
  * chain launches capped at several CTA counts (the chains run beside the tensor-core
  * near field, which needs whole SMs), and with the branched schedule (every member's
  * own evaluation as a branch of the graph: more, smaller launches that overlap one
- * another), and keep the fastest for later calls; the members' own tile shapes are
- * those of hmat_autotune. Results are bitwise the same for every choice. ms_default /
+ * another), in the mixed mode also with every member at its default tensor-core column
+ * width (a width tuned for a member alone need not suit it in the batch), and keep the
+ * fastest for later calls; the members' other tile shapes are those of hmat_autotune.
+ * Results are bitwise the same for every choice. ms_default /
  * ms_tuned (may be NULL) receive the replay time of the flattened schedule with every
  * resident CTA and of the choice. Synchronous.
  */
@@ -491,9 +494,10 @@ hmat_status hmat_batch_info(hmat_batch_t b, int64_t* out, int n);
 hmat_status hmat_batch_autotune(hmat_batch_t b, const void* const* W, void* const* Y, const int64_t* q, int dtype,
                                 void* stream, double* ms_default, double* ms_tuned);
 /* hmat_batch_schedule - pin the schedule without timing: branched 0 (flattened, the
- * default) or 1, and the chain launches' CTAs (0: every resident CTA); the next call
- * recaptures. HMAT_EINVAL for other values. */
-hmat_status hmat_batch_schedule(hmat_batch_t b, int branched, int chain_grid);
+ * default) or 1, the chain launches' CTAs (0: every resident CTA) and default_widths 0
+ * (the members' tuned tensor-core column widths, the default) or 1 (their default
+ * widths); the next call recaptures. HMAT_EINVAL for other values. */
+hmat_status hmat_batch_schedule(hmat_batch_t b, int branched, int chain_grid, int default_widths);
 hmat_status hmat_batch_free(hmat_batch_t b);
 
 /*

@@ -98,6 +98,8 @@ struct hmat_batch {
   int kernels = 0;                    // kernel launches in the captured graph
   int chain_grid = 0;                 // CTAs of the chain launches (0: every resident CTA; hmat_batch_autotune)
   int branched = 0;                   // 1: every member's evaluation as a graph branch of its own (hmat_batch_autotune)
+  int default_widths = 0;             // 1: mixed members at their default tensor-core column width, not
+                                      // their own tuned one (hmat_batch_autotune)
   std::vector<cudaStream_t> member_stream;  // branched schedule: one stream per member
   std::vector<cudaEvent_t> member_join;
   // the captured graph and the arguments it was captured for
@@ -211,7 +213,12 @@ struct MixedTables {
       EvalContext* c = b->ctx[i];
       int n_t;
       int64_t n_ct;
-      mixed_tiles(*h, q[i], &n_t, &n_ct);
+      if (b->default_widths) {
+        n_t = mixed_nt_candidates(q[i])[0];
+        n_ct = (q[i] + n_t - 1) / n_t;
+      } else {
+        mixed_tiles(*h, q[i], &n_t, &n_ct);
+      }
       const int nct = (int)n_ct;
       const int64_t r = std::max<int64_t>(h->sum_rank, 1);
       absW.push_back(AbsJob{W[i], h->n_points * q[i], c->wmax});
@@ -621,11 +628,20 @@ extern "C" hmat_status hmat_batch_autotune(hmat_batch_t b, const void* const* W,
   hmat_status st = HMAT_OK;
   // the chain launches run beside the near field, which needs whole SMs: fewer chain CTAs
   // leave it more of them; timed on whole replays of the batch's graph
-  int best_branched = 0;
-  // the flattened schedule with several chain grids, then one branch per member
-  for (int g : {0, 2 * sms, sms, sms / 2, sms / 4, -1}) {
+  int best_branched = 0, best_widths = 0;
+  // the flattened schedule with several chain grids, with the members' own tuned column
+  // widths and (mixed) with every member at its default width (a width tuned for a member
+  // alone need not suit it beside the others), then one branch per member
+  struct Cand { int grid, widths; };
+  std::vector<Cand> cands;
+  for (int w = 0; w < (b->mode == HMAT_MODE_MIXED ? 2 : 1); ++w)
+    for (int g : {0, 2 * sms, sms, sms / 2, sms / 4}) cands.push_back({g, w});
+  cands.push_back({-1, 0});
+  for (const Cand& cd : cands) {
+    const int g = cd.grid;
     b->branched = g < 0 ? 1 : 0;
     b->chain_grid = g < 0 ? 0 : g;
+    b->default_widths = cd.widths;
     if (b->exec) {  // recapture with this grid
       cudaStreamSynchronize(b->capture);
       cudaGraphExecDestroy(b->exec);
@@ -643,17 +659,19 @@ extern "C" hmat_status hmat_batch_autotune(hmat_batch_t b, const void* const* W,
       if (st == HMAT_OK && r > 0) t = std::min(t, (double)ms);
     }
     if (st != HMAT_OK) break;
-    if (g == 0) def = t;
+    if (g == 0 && cd.widths == 0) def = t;
     if (t < best) {
       best = t;
       best_grid = g < 0 ? 0 : g;
       best_branched = g < 0 ? 1 : 0;
+      best_widths = cd.widths;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->chain_grid = st == HMAT_OK ? best_grid : 0;
   b->branched = st == HMAT_OK ? best_branched : 0;
+  b->default_widths = st == HMAT_OK ? best_widths : 0;
   if (b->exec) {
     cudaStreamSynchronize(b->capture);
     cudaGraphExecDestroy(b->exec);
@@ -665,9 +683,10 @@ extern "C" hmat_status hmat_batch_autotune(hmat_batch_t b, const void* const* W,
   return HMAT_OK;
 }
 
-extern "C" hmat_status hmat_batch_schedule(hmat_batch_t b, int branched, int chain_grid) {
-  if (!b || branched < 0 || branched > 1 || chain_grid < 0) return HMAT_EINVAL;
-  if (b->branched != branched || b->chain_grid != chain_grid) {
+extern "C" hmat_status hmat_batch_schedule(hmat_batch_t b, int branched, int chain_grid, int default_widths) {
+  if (!b || branched < 0 || branched > 1 || chain_grid < 0 || default_widths < 0 || default_widths > 1)
+    return HMAT_EINVAL;
+  if (b->branched != branched || b->chain_grid != chain_grid || b->default_widths != default_widths) {
     if (b->exec) {  // the next call recaptures
       cudaStreamSynchronize(b->capture);
       cudaGraphExecDestroy(b->exec);
@@ -675,15 +694,16 @@ extern "C" hmat_status hmat_batch_schedule(hmat_batch_t b, int branched, int cha
     }
     b->branched = branched;
     b->chain_grid = chain_grid;
+    b->default_widths = default_widths;
   }
   return HMAT_OK;
 }
 
 extern "C" hmat_status hmat_batch_info(hmat_batch_t b, int64_t* out, int n) {
   if (!b || !out || n < 0) return HMAT_EINVAL;
-  const int64_t vals[5] = {(int64_t)b->handles.size(), b->exec ? b->kernels : 0, b->block_bytes, b->chain_grid,
-                           b->branched};
-  for (int i = 0; i < n && i < 5; ++i) out[i] = vals[i];
+  const int64_t vals[6] = {(int64_t)b->handles.size(), b->exec ? b->kernels : 0, b->block_bytes, b->chain_grid,
+                           b->branched, b->default_widths};
+  for (int i = 0; i < n && i < 6; ++i) out[i] = vals[i];
   return HMAT_OK;
 }
 

@@ -163,7 +163,7 @@ def library() -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_void_p), _c_i64p, ctypes.c_void_p]
         lib.hmat_batch_free.argtypes = [ctypes.c_void_p]
         lib.hmat_batch_info.argtypes = [ctypes.c_void_p, _c_i64p, ctypes.c_int]
-        lib.hmat_batch_schedule.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        lib.hmat_batch_schedule.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.hmat_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                             ctypes.POINTER(ctypes.c_void_p), _c_i64p, ctypes.c_int, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -506,14 +506,15 @@ def hmat_batch_eval_typed(batch: int, Ws, Ys, stream=None) -> None:
 
 
 def hmat_batch_info(batch: int) -> dict:
-    out = (ctypes.c_int64 * 5)()
-    _check(library().hmat_batch_info(batch, out, 5), "hmat_batch_info")
+    out = (ctypes.c_int64 * 6)()
+    _check(library().hmat_batch_info(batch, out, 6), "hmat_batch_info")
     return {"members": int(out[0]), "kernels": int(out[1]), "device_bytes": int(out[2]), "chain_grid": int(out[3]),
-            "branched": int(out[4])}
+            "branched": int(out[4]), "default_widths": int(out[5])}
 
 
-def hmat_batch_schedule(batch: int, branched: int = 0, chain_grid: int = 0) -> None:
-    _check(library().hmat_batch_schedule(batch, int(branched), int(chain_grid)), "hmat_batch_schedule")
+def hmat_batch_schedule(batch: int, branched: int = 0, chain_grid: int = 0, default_widths: int = 0) -> None:
+    _check(library().hmat_batch_schedule(batch, int(branched), int(chain_grid), int(default_widths)),
+           "hmat_batch_schedule")
 
 
 def hmat_batch_autotune(batch: int, Ws, Ys, stream=None) -> dict:

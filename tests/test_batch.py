@@ -66,14 +66,17 @@ def test_batch_equals_members_alone(loaded, mode, tol):
         # the other schedules (one branch per member; a capped chain grid) and the tuner's
         # choice give bitwise the same results
         ref = [Y.clone() for Y in Ys]
-        for branched, grid in ((1, 0), (0, 7)):
-            hp.hmat_batch_schedule(b, branched, grid)
+        if mode == hp.HMAT_MODE_MIXED:  # a member tuned to a non-default width, then batched at either
+            hp.hmat_tune_apply(handles[3], qs[3], near_cols=48)
+        for branched, grid, widths in ((1, 0, 0), (0, 7, 0), (0, 0, 1), (0, 0, 0)):
+            hp.hmat_batch_schedule(b, branched, grid, widths)
             for Y in Ys:
                 Y.fill_(float("nan"))
             hp.hmat_batch_eval(b, Ws, Ys)
             torch.cuda.synchronize()
-            assert hp.hmat_batch_info(b)["branched"] == branched
-            assert all(torch.equal(Y, R) for Y, R in zip(Ys, ref)), (branched, grid)
+            info = hp.hmat_batch_info(b)
+            assert info["branched"] == branched and info["default_widths"] == widths
+            assert all(torch.equal(Y, R) for Y, R in zip(Ys, ref)), (branched, grid, widths)
         rep = hp.hmat_batch_autotune(b, Ws, Ys)
         assert 0 < rep["tuned_ms"] <= rep["default_ms"]
         hp.hmat_batch_eval(b, Ws, Ys)
