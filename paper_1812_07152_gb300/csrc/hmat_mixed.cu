@@ -173,8 +173,21 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   lo = __fadd_rn(lo, err);
 }
 
+// The scale exponent from the bits of a non-negative maximum (as k_absmax stores it), on the
+// integer units: the exponent field of a normal value is ilogb + 1023; zero, subnormal and
+// non-finite maxima take the FP64 path.
+__device__ __forceinline__ int scale_exponent_bits(unsigned long long bits);
+
 __device__ __forceinline__ int scale_exponent(double maxabs) {
   return maxabs > 0.0 ? kScaleTop - ilogb(maxabs) : 0;
+}
+
+static __device__ __noinline__ double pow2_hw(int k) { return ldexp(1.0, k); }
+
+__device__ __forceinline__ int scale_exponent_bits(unsigned long long bits) {
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex != 0 && ex != 0x7FF) return kScaleTop - (ex - 1023);
+  return scale_exponent(__longlong_as_double((long long)bits));
 }
 
 // Byte offset of FP16 value (row r, column k) inside a 128-row x 64-column SW128 tile.
@@ -377,9 +390,11 @@ __device__ __forceinline__ void split_body(const SplitJob& j, int64_t b) {
   const int node = tc.chunk_node[g], c = tc.chunk_c[g];
   const int n_j = tc.size[node];
   const int64_t row0 = tc.begin[node] + (int64_t)c * kTcK;
-  const int k_x = scale_exponent(__longlong_as_double((long long)*xmax));
-  const double sd = ldexp(1.0, k_x);
-  const float sf = (float)sd;
+  // the scale 2^k_x as FP64 and FP32 bit patterns (every thread of the split computes it:
+  // FP64 ilogb, ldexp and conversions would keep the 1/64-rate FP64 pipe a quarter busy)
+  const int k_x = scale_exponent_bits(*xmax);
+  const double sd = k_x >= -1022 && k_x <= 1023 ? __longlong_as_double((long long)(k_x + 1023) << 52) : pow2_hw(k_x);
+  const float sf = k_x >= -126 && k_x <= 127 ? __int_as_float((k_x + 127) << 23) : narrow_f64_hw(sd);
   const bool f32_scale = k_x <= 100;
   const int64_t q0 = (int64_t)ct * n_t;
   uint8_t* hi_t = out + (g * n_ct + ct) * (int64_t)(2 * n_t * 128);
