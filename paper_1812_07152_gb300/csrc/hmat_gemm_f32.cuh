@@ -15,7 +15,8 @@ namespace gemm {
 // than FP64 on GB300, so these launches are bound by memory latency along each
 // task's K loop (coupling lists reach hundreds of partners). Every task of the mixed
 // far field has at most one entry (the coupling blocks of a node are concatenated),
-// so chunk c of a task covers depth c * BK. The entries index the FP32 arena, where
+// so chunk c of a task covers depth c * BK (BK = 32 for 64 x 64 tiles, which halves their
+// barriers and copy rounds per FMA, else 16). The entries index the FP32 arena, where
 // every operand is k-major (A(m, k) at a[k * lda + m]) with lda a multiple of 4,
 // zero-padded rows up to lda and a 16-byte aligned start, so A is copied 16 bytes
 // (four rows m) at a time. The CTA splits the chunks round-robin over up to four
@@ -42,6 +43,7 @@ __device__ __forceinline__ void bar_sync(int id, int nthreads) {
 
 template <int BM, int BN>
 struct CfgF32 {
+  static constexpr int BK = (BM >= 64 && BN >= 64) ? 32 : gemm::BK;
   static constexpr int kSliceThreads = (BM / TM) * (BN / TN);
   static constexpr int kSlices = kSliceThreads >= 256 ? 1 : (256 / kSliceThreads > 4 ? 4 : 256 / kSliceThreads);
   static constexpr int kThreads = kSliceThreads * kSlices;
@@ -68,6 +70,7 @@ __device__ __forceinline__ void gemm_tile_f32(const GemmTile tile, const GemmTas
                                               const int64_t* __restrict__ y_map, int64_t q, int64_t q0,
                                               float* smf) {
   using C = CfgF32<BM, BN>;
+  constexpr int BK = C::BK;
   constexpr int NTS = C::kSliceThreads;
   constexpr int CX = BN / TN;
   constexpr int S = kAsyncStages;
