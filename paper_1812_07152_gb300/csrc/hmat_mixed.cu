@@ -10,8 +10,9 @@
 //    subnormal lo for values down to 2^-16 of the maximum;
 //  * Y_t = sum_s (Ah Xh + Ah Xl + Al Xh), the dropped Al Xl term is 2^-22 relative;
 //  * the tensor core's FP32 accumulator truncates (rounds toward zero, measured on
-//    this GPU), so the dominant Ah Xh product is accumulated in TMEM for two blocks
-//    only and then drained by the epilogue warps into a compensated FP32 (hi, lo)
+//    this GPU), so the dominant Ah Xh product is accumulated in TMEM over a few blocks
+//    only (near field: whole blocks up to 512 summed terms; coupling: two blocks) and then
+//    drained by the epilogue warps into a compensated FP32 (hi, lo)
 //    pair per output (hi in registers, lo in TMEM columns 384..511); the two small
 //    cross terms (2^-11 of the result) accumulate over the whole list in a second
 //    TMEM accumulator.
@@ -41,7 +42,10 @@ constexpr int kMaxNt = 128;                  // columns of W per CTA (MMA N)
 constexpr uint32_t kTmemCols = 512;          // main[0], main[1], cross, compensation terms
 constexpr uint64_t kWaitNs = 2000000000ull;  // give up a wait after 2 s
 constexpr int kScaleTop = 13;                // scaled maxima land in [2^13, 2^14)
-constexpr int kDrainBlocks = 2;              // near blocks accumulated in TMEM between two drains
+constexpr int kDrainChunks = 8;              // near field: a drain follows the block that brings the
+                                             // accumulator to 8 k-chunks (512 summed terms)
+constexpr int kDrainBlocksFar = 2;           // coupling: a drain every 2 blocks (its partners' ranks
+                                             // vary; longer groups cost accuracy where it is tightest)
 constexpr int kStagedEntries = 1024;         // list entries whose metadata a CTA keeps in shared memory
 
 // ------------------------------------------------------------------ PTX helpers
@@ -614,18 +618,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ Tc
       }
     }
   } else if (warp == 1) {
-    // ---- MMA issuer: main[b] = Ah*Xh over kDrainBlocks blocks, cross += Ah*Xl + Al*Xh
+    // ---- MMA issuer: main[b] = Ah*Xh over the blocks of a drain group, cross += Ah*Xl + Al*Xh
     if (lane == 0) {
       const uint32_t idesc = idesc_f16(kTcRows, a.n_t);
       const uint32_t cross = tmem + 256;
       const int nb = s_nb;  // blocks with data
-      int it = 0, blk = 0;
+      int it = 0, blk = 0, grp = 0, gch = 0, gbk = 0;  // k-chunks and blocks in the current drain group
       bool ok = true;
       for (int64_t e = e0; e < e1 && ok; ++e) {
         const int kc = ent_kc(e);
         if (kc == 0) continue;
-        const int grp = blk / kDrainBlocks, b = grp & 1, rb = grp >> 1;
-        const bool first_of_group = blk % kDrainBlocks == 0;
+        const int b = grp & 1, rb = grp >> 1;
+        const bool first_of_group = gbk == 0;
         if (first_of_group && rb > 0 && !mbar_wait(smem_u32(&mempty_bar[b]), (rb - 1) & 1, &abort_flag)) {
           fail();
           ok = false;
@@ -657,7 +661,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ Tc
         }
         if (!ok) break;
         ++blk;
-        if (blk % kDrainBlocks == 0 || blk == nb) mma_commit(smem_u32(&mfull_bar[b]));
+        gch += kc;
+        ++gbk;
+        if ((kFar ? gbk >= kDrainBlocksFar : gch >= kDrainChunks) || blk == nb) {
+          mma_commit(smem_u32(&mfull_bar[b]));
+          ++grp;
+          gch = 0;
+          gbk = 0;
+        }
       }
       if (ok && blk > 0) mma_commit(smem_u32(&cfull_bar));
       mma_commit(smem_u32(&done_bar));
@@ -680,8 +691,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ Tc
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) tmem_st16(comp + cc * 16, z);
     }
-    const int nb = s_nb;  // blocks with data, drained kDrainBlocks at a time
-    const int n_groups = (nb + kDrainBlocks - 1) / kDrainBlocks;
+    const int nb = s_nb;  // blocks with data
+    int n_groups = 0;     // drain groups, cut as the MMA issuer cuts them
+    {
+      int g = 0, gb = 0, bb = 0;
+      for (int64_t e = e0; e < e1; ++e) {
+        const int kc = ent_kc(e);
+        if (kc == 0) continue;
+        g += kc;
+        ++gb;
+        ++bb;
+        if ((kFar ? gb >= kDrainBlocksFar : g >= kDrainChunks) || bb == nb) {
+          ++n_groups;
+          g = 0;
+          gb = 0;
+        }
+      }
+    }
     int blk = 0;
     bool ok = true;
     for (int grp = 0; grp < n_groups; ++grp) {
@@ -704,7 +730,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const __grid_constant__ Tc
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&mempty_bar[b]));
-      blk += kDrainBlocks;
+      ++blk;  // drains done
     }
     bool have_cross = false;
     if (ok && blk > 0) {
