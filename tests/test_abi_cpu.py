@@ -68,3 +68,41 @@ def test_load_rejects_invalid_descriptions(mutate):
     elif mutate == "negative_rank":
         d["rank"][3] = -1
     _expect_einval(d)
+
+
+def test_null_and_out_of_range_arguments_are_rejected_before_any_device_work():
+    """Every entry point that takes a handle, batch or server refuses a null one with
+    HMAT_EINVAL (no CUDA call is made, so this runs without a GPU); the free calls accept
+    null as a no-op; the choice-taking calls refuse out-of-range choices."""
+    import ctypes
+    lib = hp.library()
+    V, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    null = V(0)
+    calls = {
+        "hmat_eval": ([V, V, V, I64, I32, V], (null, null, null, 4, hp.HMAT_MODE_FP64, null)),
+        "hmat_eval_typed": ([V, V, V, I64, I32, I32, V], (null, null, null, 4, hp.HMAT_MODE_MIXED, 1, null)),
+        "hmat_eval_host": ([V, V, V, I64, I32, V], (null, null, null, 4, hp.HMAT_MODE_FP64, null)),
+        "hmat_eval_noalloc": ([V, V, V, I64, V], (null, null, null, 4, null)),
+        "hmat_reserve": ([V, I64], (null, 4)),
+        "hmat_profile": ([V, I32], (null, 1)),
+        "hmat_tune_apply": ([V, V], (null, null)),
+        "hmat_autotune": ([V, I64, I32, V, V], (null, 4, hp.HMAT_MODE_FP64, null, null)),
+        "hmat_batch_info": ([V, V, I32], (null, null, 6)),
+        "hmat_batch_schedule": ([V, I32, I32, I32], (null, 0, 0, 0)),
+        "hmat_server_wait": ([V, I64, I32], (null, 0, 0)),
+        "hmat_server_stats": ([V, V, I32], (null, null, 4)),
+        "hmat_server_matrix_stats": ([V, I32, V, I32], (null, 0, null, 4)),
+        "hmat_selftest_timeout": ([V, I64, V], (null, 1000000, null)),
+        "hmat_selftest_chain_timeout": ([V, I64, I32, I64, V], (null, 4, hp.HMAT_MODE_MIXED, 1000000, null)),
+        "hmat_selftest_device_check": ([V, I64, I32, V], (null, 4, hp.HMAT_MODE_MIXED, null)),
+        "hmat_info": ([V, V, I32], (null, null, 4)),
+    }
+    for name, (argtypes, args) in calls.items():
+        fn = getattr(lib, name)
+        fn.argtypes, fn.restype = argtypes, ctypes.c_int
+        assert fn(*args) == hp.HMAT_EINVAL, name
+    for name in ("hmat_free", "hmat_batch_free", "hmat_server_free", "hmat_plan_free"):
+        fn = getattr(lib, name)
+        fn.argtypes, fn.restype = [V], ctypes.c_int
+        assert fn(null) == hp.HMAT_OK, name
+    assert hp.hmat_strerror(hp.HMAT_EBUSY) != "unknown status"
