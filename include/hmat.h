@@ -215,9 +215,10 @@ hmat_status hmat_structure(hmat_t h, int64_t* perm, int32_t* rank, int64_t* near
 
 /* Evaluation modes for hmat_eval. */
 #define HMAT_MODE_FP64 0            /* every block and every sum in FP64 (DFMA) */
-#define HMAT_MODE_MIXED 1           /* near field on the tensor cores (FP16 hi+lo splits of D and W,
-                                       FP32 accumulation drained per block into compensated sums),
-                                       far field in FP32; needs a handle loaded with HMAT_LOAD_MIXED */
+#define HMAT_MODE_MIXED 1           /* near field (and high-rank coupling) on the tensor cores (FP16
+                                       hi+lo splits of the blocks and of W, FP32 accumulation drained
+                                       every few blocks into compensated sums), far field in FP32;
+                                       needs a handle loaded with HMAT_LOAD_MIXED */
 
 /* Build flag (hmat_build, hmat_plan_build): the nested row IDs run on the GPU, one CTA
    per node of a tree level (same algorithm as on the host; sums in another order, so a
